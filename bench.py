@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the SP2 hot path on GB300.
+
+Workload (default): the ELLPACK X^2 SpGEMM case -- a 3D tight-binding Hamiltonian
+(sites uniform in a periodic cube at 0.1 per cubic Angstrom, hopping -exp(-r/1.5) for
+r < 4 Angstrom, onsite ~N(0, 0.5), Morton-ordered, seed 0), N = 262144, FP64 values and
+int32 indices, drop tolerance 1e-6; X = one SP2 step of H (built untimed, on the GPU).
+One step = one SP2 iteration on X through the C ABI (sp2_step): branch from tr X and
+||X||_F^2, the thresholded product with the fused update (X^2 or 2X - X^2), the FP64
+traces of the result and the host read of that 56-byte result.
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SP2 iters/s & ELLPACK X² SpGEMM HBM GB/s; mixed vs FP64 at ‖ΔD‖_F/√N≤1e-5"
+UNIT = "iter/s"
+# FP64 FMA units: 2 per SM per clock (1.25 TFLOP/s nominal = 152 SMs x 2 x 2 flop x 2.07 GHz)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=262144)
+    p.add_argument("--tau", type=float, default=1e-6)
+    p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-clocks", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+def workload_config(a, extra=None):
+    c = {"workload": "SP2 iteration on ELLPACK X^2 SpGEMM: 3D tight-binding N=%d, %s values, int32 indices, "
+                     "tau=%g, X = one SP2 step of H" % (a.n, a.dtype.upper(), a.tau),
+         "n": a.n, "tau": a.tau, "seed": a.seed,
+         "hamiltonian": "periodic cube, density 0.1/A^3, -exp(-r/1.5) for r<4 A, onsite N(0,0.5), Morton order"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------------ host-side helpers
+def fma_count(idx, nnz):
+    """sum over rows i of sum_{k in row i} nnz[k] (products of X*X)."""
+    n, w = idx.shape
+    mask = np.arange(w)[None, :] < nnz[:, None]
+    return int(np.where(mask, nnz[idx], 0).sum())
+
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id, enabled=True):
+        self.proc = None
+        self.dev_id = dev_id
+        if not enabled:
+            return
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(dev_id)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clocks not sampled"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out = self.proc.communicate(timeout=5)[0]
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_traffic(dtype):
+    """Per-launch DRAM bytes of the SpGEMM kernel from the committed ncu summary, or None
+    if the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "spgemm_traffic.json")
+    src = os.path.join(ROOT, "paper_2102_08505_gb300", "csrc", "spgemm.cu")
+    try:
+        rec = json.load(open(path))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        ent = rec.get(dtype)
+        if ent and ent.get("spgemm_cu_sha256") == sha:
+            return ent.get("dram_bytes_per_launch_full_size")
+    except Exception:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------ oracle timing (CPU)
+def oracle_prepare(a, threads):
+    """Oracle-side input of the timed iteration: X = one SP2 step of H, built by the oracle."""
+    from oracle import oracle as O
+    from paper_2102_08505_gb300 import inputs as I
+    O.set_threads(threads)
+    H = O.Ell(*I.tight_binding(a.n, seed=a.seed))
+    lo, hi = O.gershgorin(H)
+    X0 = O.x0(H, lo, hi, a.tau)
+    nocc = a.n / 2
+
+    def traces(X):
+        live = np.arange(X.w)[None, :] < X.nnz[:, None]
+        return O.trace(X), float(np.where(live, X.val, 0.0).__pow__(2).sum())
+
+    t0, t02 = traces(X0)
+    up = abs(2 * t0 - t02 - nocc) < abs(t02 - nocc)
+    X1 = O.spgemm(X0, X0, X0 if up else None, -1.0 if up else 1.0, 2.0 if up else 0.0, a.tau)
+    t1, t12 = traces(X1)
+    up = abs(2 * t1 - t12 - nocc) < abs(t12 - nocc)
+    O.set_threads(1)
+    return X1, up
+
+
+def oracle_iteration_rate(a, X1, up, sample_rows, threads, reps=1):
+    """Times the oracle's SP2 iteration (product with the update, then the trace) on a
+    row sample of X; returns (iterations/s scaled to all rows, median s, rows, times)."""
+    from oracle import oracle as O
+    O.set_threads(threads)
+    rng = np.random.default_rng(1234)
+    rows = np.sort(rng.choice(a.n, size=min(sample_rows, a.n), replace=False)).astype(np.int32)
+    times = []
+    for _ in range(reps):
+        t = time.perf_counter()
+        out = O.spgemm(X1, X1, X1 if up else None, -1.0 if up else 1.0, 2.0 if up else 0.0, a.tau, rows=rows)
+        _ = O.trace(out)
+        times.append(time.perf_counter() - t)
+    O.set_threads(1)
+    sec = float(np.median(times))
+    return 1.0 / (sec * a.n / len(rows)), sec, len(rows), times
+
+
+def cpu_baseline(a):
+    from oracle import oracle as O
+    threads = O.max_threads()
+    X1, up = oracle_prepare(a, threads)
+    # bounded sample: about 10 s of CPU work
+    _, sec0, rows0, _ = oracle_iteration_rate(a, X1, up, 4096, threads)
+    target = int(min(a.n, max(4096, rows0 * 10.0 / max(sec0, 1e-3))))
+    rate, sec, rows, _ = oracle_iteration_rate(a, X1, up, target, threads)
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d of %d product rows of one SP2 iteration (oracle SpGEMM + update + trace, %.1f s on %d "
+                      "threads), scaled to the whole iteration" % (rows, a.n, sec, threads)}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    threads = O.max_threads()
+    X1, up = oracle_prepare(a, threads)
+    # each step: a bounded row sample (1/16 of the rows), scaled to a whole iteration
+    sample = max(1, a.n // 16)
+    oracle_iteration_rate(a, X1, up, sample, threads, reps=max(1, a.warmup))
+    rate, sec, rows, times = oracle_iteration_rate(a, X1, up, sample, threads, reps=max(1, a.steps))
+    per_step_ms = 1000.0 * float(np.mean(times)) * a.n / rows
+    rate = 1000.0 / per_step_ms
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 0, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": per_step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(a),
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "%d of %d product rows per step (oracle SpGEMM + update + trace), "
+                                   "scaled to the whole iteration" % (rows, a.n)},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2102_08505_gb300 import inputs as I
+    from paper_2102_08505_gb300 import sp2ell as S
+
+    DT = S.SP2_F64 if a.dtype == "f64" else S.SP2_F32
+    esz = 8 if a.dtype == "f64" else 4
+    stream = torch.cuda.current_stream()
+    nocc = a.n / 2
+
+    # ---------------- setup (untimed): H -> X0 -> X (one SP2 step), all on the GPU
+    idx, val, nnz = I.tight_binding(a.n, seed=a.seed + rank)
+    H = S.Ellpack.from_numpy(idx, val, nnz)
+    X0 = S.Ellpack.empty(a.n, H.width + 32)
+    S.sp2_x0(H, X0, a.tau)
+    if DT == S.SP2_F32:
+        X0f = S.Ellpack.empty(a.n, X0.width, S.SP2_F32)
+        S.ellpack_copy(X0, X0f)
+        X0 = X0f
+    w1 = 4 * X0.width
+    while True:
+        X1 = S.Ellpack.empty(a.n, w1, DT)
+        rc, info = S.sp2_step(X0, X1, nocc, a.tau, raise_on_overflow=False)
+        if rc == 0:
+            break
+        w1 = ((info.required_width + 31) // 32) * 32
+    w1 = ((int(info.max_row_nnz) + 31) // 32) * 32
+    Xs = S.Ellpack.empty(a.n, w1, DT)
+    S.ellpack_copy(X1, Xs)
+    X1 = Xs
+    traces = (info.trXn, info.trXn2)
+    del X0, H
+    X2 = S.Ellpack.empty(a.n, 32, DT)
+    rc, info = S.sp2_step(X1, X2, nocc, a.tau, traces=traces, raise_on_overflow=False)
+    w2 = ((info.required_width + 31) // 32) * 32
+    X2 = S.Ellpack.empty(a.n, w2, DT)
+    info = S.sp2_step(X1, X2, nocc, a.tau, traces=traces)
+    torch.cuda.synchronize()
+    h_idx, h_val, h_nnz = [t.cpu().numpy() for t in (X1.idx, X1.val, X1.nnz)]
+    nnz_in = int(h_nnz.sum())
+    fmas = fma_count(h_idx, h_nnz)
+    nnz_out = int(info.nnz_total)
+    alg_bytes = (4 + esz) * (2 * nnz_in + nnz_out) + 12 * a.n  # A, B, C read/written once + 3 nnz arrays
+    in_bytes = X1.idx.numel() * 4 + X1.val.numel() * esz + a.n * 4
+
+    # ---------------- device-timed steps
+    for _ in range(a.warmup):
+        S.sp2_step(X1, X2, nocc, a.tau, traces=traces)
+    torch.cuda.synchronize()
+    clocks = Clocks(local, enabled=not a.no_clocks)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    S.sp2_profile_start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        S.sp2_step(X1, X2, nocc, a.tau, traces=traces)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = S.sp2_profile_stop()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+
+    cnt, tot = prof["spgemm"]
+    k_ms = tot / max(cnt, 1)
+    tflops = 2.0 * fmas / (k_ms * 1e-3) / 1e12
+    gbs = alg_bytes / (k_ms * 1e-3) / 1e9
+    pk = peaks()
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    alu_peak = FP64_PEAK_TFLOPS if a.dtype == "f64" else FP32_PEAK_TFLOPS
+    traffic = kernel_traffic(a.dtype)
+    roofline = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tflops / alu_peak,
+                "traffic": traffic,
+                "peak_source": "derived: 152 SMs x %s FMA/clk x 2 flop x 2.07 GHz" % ("2 FP64" if a.dtype == "f64" else "128 FP32"),
+                "kernel": "spgemm_hash_kernel", "kernel_ms": k_ms, "launches_timed": cnt,
+                "hbm_view": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                             "peak_source": "measured" if "fallback" not in pk else "fallback",
+                             "algorithmic_bytes_per_launch": alg_bytes}}
+
+    # ---------------- end to end through the C ABI with host buffers
+    e2e = None
+    if not a.no_e2e:
+        import torch as _t
+        hi = _t.from_numpy(h_idx).pin_memory()
+        hv = _t.from_numpy(h_val).pin_memory()
+        hn = _t.from_numpy(h_nnz).pin_memory()
+        oi = _t.empty((a.n, w2), dtype=_t.int32).pin_memory()
+        ov = _t.empty((a.n, w2), dtype=_t.float64 if DT == S.SP2_F64 else _t.float32).pin_memory()
+        on = _t.empty(a.n, dtype=_t.int32).pin_memory()
+        Xin = S.Ellpack.empty(a.n, w1, DT)
+
+        def e2e_step():
+            S._check(S.lib.ellpack_upload(S._d(Xin), hi.data_ptr(), hv.data_ptr(), hn.data_ptr(), S._stream(stream)))
+            S.sp2_step(Xin, X2, nocc, a.tau, traces=traces)
+            S._check(S.lib.ellpack_download(S._d(X2), oi.data_ptr(), ov.data_ptr(), on.data_ptr(), S._stream(stream)))
+
+        for _ in range(max(1, a.warmup)):
+            e2e_step()
+        ksteps = max(1, min(a.steps, 20))
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ksteps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1) / ksteps
+        if world > 1:
+            t = torch.tensor([ems], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        out_bytes = a.n * w2 * (4 + esz) + 4 * a.n
+        e2e = {"value": world * 1000.0 / ems, "unit": UNIT, "h2d_bytes_per_step": in_bytes,
+               "d2h_bytes_per_step": out_bytes, "ms_per_step": ems, "steps": ksteps,
+               "api": "ellpack_upload + sp2_step + ellpack_download (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(a)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": a.dtype, "data": "synthetic",
+            "config": workload_config(a, {
+                "width_in": w1, "width_out": w2, "nnz_per_row_in": nnz_in / a.n, "nnz_per_row_out": nnz_out / a.n,
+                "fma_per_row": fmas / a.n, "branch": "2X-X^2" if info.branch == 2 else "X^2",
+                "l2": "no flush: inputs %.2f GB > 129 MB L2" % (in_bytes / 1e9),
+                "parallelism": "replicas" if world > 1 else "single GPU"}),
+            "spgemm_gflops": tflops * 1e3, "spgemm_hbm_gbs": gbs,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(prof["launches"]),
+            "kernels_timed": {k: prof[k] for k in ("spgemm", "large_rows", "reduce", "other")},
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,272 @@
+/*
+ * sp2ell.h -- C ABI of the GB300 (sm_103a) library for SP2 density-matrix purification
+ * on thresholded ELLPACK sparse matrices.
+ *
+ * The method is the one the paper studies on multi-core CPUs: the SP2-Basic loop of the
+ * ExaSP2 proxy application, whose phases are the ELLPACK matrix-matrix multiply X*X
+ * ("SP2 Loop X2"), a norm ("SP2 Loop Norm") and the update ("SP2 Loop Misc")
+ * (Section "Performance Evaluation using an ExaSP2 Application"), on the ELLPACK storage
+ * of the allocation listing (arrays nnz[N], index[N*M], value[N*M]; Section
+ * "Micro-Kernel Performance Evaluation - NUMA Aware Data").  The SP2 recursion itself
+ * is the published one (Niklasson 2002, cited in the Introduction).
+ *
+ * Conventions
+ *   - Every function returns int: SP2_OK (0) or a negative SP2E_* code.  A failing call
+ *     leaves a message for sp2_last_error_string() (thread-local).
+ *   - Arguments are checked before any launch; no exception crosses the ABI.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Calls that return host scalars or a status that depends on device results
+ *     synchronise that stream; the others are asynchronous.
+ *   - All matrices are square, n x n, n >= 1.  Device arrays are row-major ELLPACK:
+ *       idx[i*width + s], val[i*width + s] for s < nnz[i] hold row i's entries;
+ *       slots s >= nnz[i] are never read and their contents are unspecified.
+ *     A row never holds the same column twice.  Rows written by the library are sorted
+ *     by ascending column.
+ *   - One handle must not be used from two streams at the same time.  The library uses
+ *     the current CUDA device; matrices must live on it.
+ */
+#ifndef SP2ELL_H
+#define SP2ELL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define SP2_OK 0
+#define SP2E_ARG (-1)        /* invalid argument (null pointer, bad size, aliasing, NaN/negative tau) */
+#define SP2E_OVERFLOW (-2)   /* an output row needs more slots than the output width */
+#define SP2E_NOMEM (-3)      /* device or pinned-host allocation failed */
+#define SP2E_CUDA (-4)       /* a CUDA runtime call or kernel launch failed */
+#define SP2E_NOTCONV (-5)    /* SP2 reached max_iter without meeting its stop rule */
+#define SP2E_NONFINITE (-6)  /* a NaN or Inf appeared in an input or a reduction */
+#define SP2E_TIMEOUT (-7)    /* a bounded device-side wait gave up */
+
+/* ---------------------------------------------------------------- value types */
+#define SP2_F64 0            /* double values */
+#define SP2_F32 1            /* float values */
+
+/*
+ * ELLPACK matrix descriptor (plain struct, passed by pointer).
+ *   n      rows (= columns)
+ *   width  slots per row (the paper's M); library-allocated widths are multiples of 32
+ *   dtype  SP2_F64 or SP2_F32: element type of val
+ *   owner  1 when ellpack_create allocated the arrays (ellpack_destroy frees them),
+ *          0 when they are borrowed from the caller (ellpack_wrap; never freed here)
+ *   idx    device int32[n*width]
+ *   val    device double[n*width] or float[n*width]
+ *   nnz    device int32[n]
+ */
+typedef struct ellpack_t {
+  int32_t n;
+  int32_t width;
+  int32_t dtype;
+  int32_t owner;
+  int32_t *idx;
+  void *val;
+  int32_t *nnz;
+} ellpack_t;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int sp2_version(void);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *sp2_last_error_string(void);
+
+/*
+ * Allocates an n x n ELLPACK matrix of the given width and dtype on the current device
+ * (stream-ordered allocation on `stream`) and sets every nnz[i] to 0.  width >= 1 is
+ * rounded up to a multiple of 32.  Errors: SP2E_ARG, SP2E_NOMEM, SP2E_CUDA.
+ */
+int ellpack_create(int32_t n, int32_t width, int32_t dtype, void *stream, ellpack_t *out);
+
+/* Fills `out` with caller-owned device arrays (borrowed: never freed by the library).
+ * width need not be a multiple of 32.  Errors: SP2E_ARG. */
+int ellpack_wrap(int32_t n, int32_t width, int32_t dtype, int32_t *idx, void *val, int32_t *nnz,
+                 ellpack_t *out);
+
+/* Frees the arrays of a library-owned matrix (stream-ordered) and zeroes the descriptor;
+ * a borrowed matrix is only zeroed.  Errors: SP2E_ARG, SP2E_CUDA. */
+int ellpack_destroy(ellpack_t *m, void *stream);
+
+/* Copies host arrays (same layout: idx[n*width], val[n*width], nnz[n]) to the device
+ * matrix, asynchronously; host buffers must stay valid until the stream reaches the
+ * copy (use pinned memory for overlap).  Errors: SP2E_ARG, SP2E_CUDA. */
+int ellpack_upload(ellpack_t *m, const int32_t *h_idx, const void *h_val, const int32_t *h_nnz,
+                   void *stream);
+
+/* Copies the device matrix to host arrays of the same layout and synchronises the
+ * stream.  Errors: SP2E_ARG, SP2E_CUDA. */
+int ellpack_download(const ellpack_t *m, int32_t *h_idx, void *h_val, int32_t *h_nnz, void *stream);
+
+/* Device-to-device copy of rows: dst row i <- src row i (values converted when the
+ * dtypes differ), asynchronous.  Same n; dst->width >= src->width.  dst must not share
+ * arrays with src.  Errors: SP2E_ARG, SP2E_CUDA. */
+int ellpack_copy(const ellpack_t *src, ellpack_t *dst, void *stream);
+
+/*
+ * Thresholded ELLPACK matrix-matrix multiply (the paper's "ELLPACK X2" operation,
+ * Section "Performance Evaluation using System Matrices"), BLAS gemm convention:
+ *
+ *     C <- drop_tau(alpha * A * B + beta * C)
+ *
+ *   pattern(C_i) = union over k in cols(A_i) of cols(B_k), plus the old cols(C_i) when
+ *   beta != 0; an entry is kept iff |v| > tau (tau == 0 keeps every structural entry,
+ *   exact zeros included); rows of C come out sorted by column.  The comparison with
+ *   tau is made in the matrices' own precision.
+ *   A, B, C must share n and dtype.  A and B may be the same matrix; C must not alias A
+ *   or B (SP2E_ARG).  tau must be >= 0 and finite.
+ *   required_width (optional, host): receives the largest post-threshold row length.
+ *   Returns SP2E_OVERFLOW if some row needs more than C->width slots; C's contents are
+ *   then unspecified and *required_width tells the width to allocate.  Synchronises
+ *   `stream` (the status depends on device results).
+ *   Errors: SP2E_ARG, SP2E_OVERFLOW, SP2E_NOMEM, SP2E_CUDA.
+ */
+int ellpack_multiply(const ellpack_t *A, const ellpack_t *B, ellpack_t *C, double alpha, double beta,
+                     double tau, void *stream, int32_t *required_width);
+
+/*
+ * A <- drop_tau(alpha * A + beta * B) (the "SP2 Loop Misc" update, Section "Performance
+ * Evaluation using an ExaSP2 Application"): pattern is the union of the two rows, keep
+ * rule as in ellpack_multiply, rows sorted.  A and B share n and dtype and must not be
+ * the same matrix.  Returns SP2E_OVERFLOW (A unspecified, *required_width set) if a
+ * row does not fit A->width.  Synchronises `stream`.
+ */
+int ellpack_add(ellpack_t *A, const ellpack_t *B, double alpha, double beta, double tau, void *stream,
+                int32_t *required_width);
+
+/* tr A = sum_i A_ii, accumulated in FP64 in a fixed order (the "SP2 Loop Norm"
+ * quantity).  Synchronises `stream`.  Errors: SP2E_ARG, SP2E_CUDA, SP2E_NONFINITE. */
+int ellpack_trace(const ellpack_t *A, double *out, void *stream);
+
+/* Squared Frobenius norm sum_ij A_ij^2 in FP64 (equal to tr A^2 for symmetric A).
+ * Synchronises `stream`. */
+int ellpack_frobenius2(const ellpack_t *A, double *out, void *stream);
+
+/* Gershgorin bounds of H: e_min = min_i (H_ii - sum_{j!=i} |H_ij|),
+ * e_max = max_i (H_ii + sum_{j!=i} |H_ij|), FP64.  Synchronises `stream`. */
+int ellpack_gershgorin(const ellpack_t *H, double *emin, double *emax, void *stream);
+
+/* ---------------------------------------------------------------- profiling */
+/* Kernel classes timed by the profiler. */
+#define SP2_PROF_SPGEMM 0   /* the per-row hash SpGEMM kernel (dominant) */
+#define SP2_PROF_LARGE 1    /* the large-row (dense global row) SpGEMM kernel */
+#define SP2_PROF_REDUCE 2   /* ordered trace/norm reductions */
+#define SP2_PROF_OTHER 3    /* everything else (X0, conversions, add, Gershgorin) */
+#define SP2_PROF_CLASSES 4
+
+typedef struct sp2_profile {
+  int64_t launches;                   /* kernels launched by the library while enabled */
+  int32_t count[SP2_PROF_CLASSES];    /* timed launches per class */
+  double total_ms[SP2_PROF_CLASSES];  /* summed CUDA-event durations per class */
+} sp2_profile;
+
+/* Starts (and resets) the profiler of the calling process: from now on every kernel
+ * launch is counted and the launches of the classes above are bracketed by CUDA events
+ * recorded on the launching stream.  Errors: SP2E_CUDA. */
+int sp2_profile_start(void);
+
+/* Stops the profiler, waits for the recorded events and fills *out (may be NULL).
+ * Errors: SP2E_CUDA. */
+int sp2_profile_stop(sp2_profile *out);
+
+/* ---------------------------------------------------------------- SP2 */
+
+#define SP2_PREC_F64 0      /* every step in FP64 */
+#define SP2_PREC_MIXED 1    /* FP32 products and updates; FP64 traces, branch, stop test,
+                               then n_fp64_tail FP64 iterations */
+
+#define SP2_STATS_CAP 256   /* per-iteration records kept in sp2_stats */
+
+typedef struct sp2_options {
+  int32_t precision;    /* SP2_PREC_F64 or SP2_PREC_MIXED */
+  int32_t max_iter;     /* cap on updates (default 100) */
+  int32_t stall_rule;   /* 1: stop once |trX - trX2| < 0.1 has been seen and err_n >= err_{n-2} */
+  int32_t n_fp64_tail;  /* MIXED: FP64 iterations after the FP32 loop stops (default 2) */
+  int32_t max_width;    /* cap on the working width (0 = n); SP2E_OVERFLOW beyond it */
+  int32_t table_log2;   /* per-row hash-table size hint for the SpGEMM (0 = automatic) */
+  double tau;           /* drop tolerance (default 1e-5) */
+} sp2_options;
+
+typedef struct sp2_stats {
+  int32_t iterations;                   /* updates applied */
+  int32_t status;                       /* 0 err < tol, 1 stall rule, 2 max_iter */
+  int32_t fp32_iterations;              /* MIXED: updates made in FP32 */
+  int32_t regrows;                      /* multiplies repeated after a width overflow */
+  double emin, emax;                    /* Gershgorin bounds */
+  double time_ms;                       /* wall time of the call */
+  double trX[SP2_STATS_CAP];            /* per visited X_n (n = 0..iterations) */
+  double trX2[SP2_STATS_CAP];           /* tr X_n^2, taken as ||X_n||_F^2 */
+  double err[SP2_STATS_CAP];            /* |trX - trX2| / n */
+  int32_t branch[SP2_STATS_CAP];        /* per update: 1 = X^2, 2 = 2X - X^2 */
+  int64_t nnz_total[SP2_STATS_CAP];     /* per visited X_n */
+  int32_t max_row_nnz[SP2_STATS_CAP];   /* per visited X_n */
+} sp2_stats;
+
+/*
+ * SP2 initial guess (the "Init Misc" phase, Section "Performance Evaluation using an
+ * ExaSP2 Application"): Gershgorin bounds of H, then
+ *   X0 = drop_tau((e_max I - H) / (e_max - e_min)).
+ * H F64.  X0 F64, X0->n == H->n, X0->width >= H->width + 1.  Row order of X0: the kept
+ * entries of H's row left of the diagonal, the diagonal (always present unless it falls
+ * below tau), then those right of it (sorted whenever H's row is sorted).  emin/emax
+ * (optional, host) receive the bounds.  Synchronises `stream`.
+ * Errors: SP2E_ARG (also e_max <= e_min), SP2E_NONFINITE, SP2E_CUDA.
+ */
+int sp2_x0(const ellpack_t *H, double tau, ellpack_t *X0, double *emin, double *emax, void *stream);
+
+/* One SP2 iteration: in/out record of sp2_step. */
+typedef struct sp2_step_info {
+  double trX, trX2;        /* in when have_traces == 1 (else computed): tr X, ||X||_F^2 */
+  int32_t have_traces;     /* in */
+  int32_t branch;          /* out: 1 = X^2, 2 = 2X - X^2 */
+  double err;              /* out: |trX - trX2| / n of the input X */
+  double trXn, trXn2;      /* out: tr X', ||X'||_F^2 of the result */
+  int64_t nnz_total;       /* out: stored entries of X' */
+  int32_t max_row_nnz;     /* out: longest row of X' */
+  int32_t required_width;  /* out: longest post-threshold row (valid on overflow too) */
+  int32_t table_log2;      /* in: hash-table size hint (0 = automatic) */
+  int32_t pad;
+} sp2_step_info;
+
+/*
+ * One SP2 iteration on X (the "SP2 Loop X2 / Norm / Misc" phases): with
+ *   trX = tr X, trX2 = ||X||_F^2 (= tr X^2 for symmetric X),
+ *   X' = drop_tau(2X - X*X) if |2 trX - trX2 - nocc| < |trX2 - nocc|, else drop_tau(X*X),
+ * computed in one fused pass whose epilogue also yields tr X' and ||X'||_F^2 (FP64).
+ * X and X' share n and dtype and must not share arrays.  Returns SP2E_OVERFLOW when a
+ * row of X' needs more than Xn->width slots (info->required_width tells how many).
+ * Synchronises `stream`.  Errors: SP2E_ARG, SP2E_OVERFLOW, SP2E_NONFINITE, SP2E_CUDA.
+ */
+int sp2_step(const ellpack_t *X, ellpack_t *Xn, double nocc, double tau, sp2_step_info *info, void *stream);
+
+/* Fills *opt with the defaults (F64, max_iter 100, stall rule on, tail 2, tau 1e-5). */
+void sp2_options_default(sp2_options *opt);
+
+/*
+ * SP2 purification (SP2-Basic, Section "Performance Evaluation using an ExaSP2
+ * Application"; recursion of Niklasson 2002):
+ *   e_min, e_max = Gershgorin bounds of H
+ *   X_0 = drop_tau((e_max I - H) / (e_max - e_min))  (diagonal always in the pattern)
+ *   for n = 0, 1, ...:  trX = tr X_n, trX2 = ||X_n||_F^2,  err_n = |trX - trX2| / N
+ *       stop if err_n < tol, or (stall_rule) |trX - trX2| < 0.1 has been seen and
+ *       err_n >= err_{n-2}, or n == max_iter
+ *       X_{n+1} = drop_tau(2X_n - X_n^2) if |2 trX - trX2 - nocc| < |trX2 - nocc|,
+ *                 else drop_tau(X_n^2)
+ * H: symmetric, F64 (an F32 H is accepted and promoted).  nocc in (0, n).  tol > 0.
+ * opt may be NULL (defaults).  On success *D receives a new library-owned F64 matrix
+ * (release with ellpack_destroy) and *stats (optional) the per-iteration record.
+ * Returns SP2_OK, or SP2E_NOTCONV with D still set when max_iter was reached.
+ * Errors: SP2E_ARG, SP2E_NOMEM, SP2E_CUDA, SP2E_OVERFLOW (max_width too small),
+ * SP2E_NONFINITE.  Synchronises `stream`.
+ */
+int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2_options *opt, ellpack_t *D,
+               sp2_stats *stats, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SP2ELL_H */

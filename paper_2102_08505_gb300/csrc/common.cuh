@@ -1,0 +1,143 @@
+// common.cuh -- internal declarations shared by the translation units of libsp2ell.
+//
+// Storage: row-major ELLPACK (the allocation listing of Section "Micro-Kernel Performance
+// Evaluation - NUMA Aware Data": nnz[N], index[N*M], value[N*M]).  Row i's entries are
+// slots i*w .. i*w+nnz[i]-1; padding slots are never read.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+
+#include "sp2ell.h"
+
+namespace sp2 {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char *fmt, ...);
+int fail(int code, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define SP2_CUDA(call)                                                             \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) return ::sp2::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define SP2_TRY(call)          \
+  do {                         \
+    int rc_ = (call);          \
+    if (rc_ != SP2_OK) return rc_; \
+  } while (0)
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int num_sms();
+inline int round_up(int x, int m) { return ((x + m - 1) / m) * m; }
+
+// ------------------------------------------------------------------ profiling
+// note_launch() after every kernel launch; prof_begin/prof_end bracket one launch of a
+// class with CUDA events when the profiler is on (no-ops otherwise).
+void note_launch();
+void prof_begin(int cls, cudaStream_t s);
+void prof_end(int cls, cudaStream_t s);
+
+// ------------------------------------------------------------------ views
+template <typename T>
+struct EllView {  // read-only view
+  int n, w;
+  const int *__restrict__ idx;
+  const T *__restrict__ val;
+  const int *__restrict__ nnz;
+};
+
+template <typename T>
+struct EllOut {  // writable view
+  int n, w;
+  int *idx;
+  T *val;
+  int *nnz;
+};
+
+template <typename T>
+inline EllView<T> view(const ellpack_t *m) {
+  return EllView<T>{m->n, m->width, m->idx, static_cast<const T *>(m->val), m->nnz};
+}
+template <typename T>
+inline EllOut<T> outview(const ellpack_t *m) {
+  return EllOut<T>{m->n, m->width, m->idx, static_cast<T *>(m->val), m->nnz};
+}
+
+int check_matrix(const ellpack_t *m, const char *name);
+inline size_t dtype_size(int dt) { return dt == SP2_F64 ? sizeof(double) : sizeof(float); }
+
+// ------------------------------------------------------------------ device memory
+// Stream-ordered allocation helpers (cudaMallocAsync pool of the current device).
+int dev_alloc(void **p, size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+
+// Grow-only scratch kept per device for the large-row fallback of the multiply:
+// `slots` dense rows of n accumulators (T) and n marks (int, initialised to -1).
+int fallback_scratch(int n, int dtype, int slots, void **acc, int **mark, cudaStream_t s);
+
+// ------------------------------------------------------------------ per-step reductions
+// Result of one multiply / trace pass, reduced in a fixed order (deterministic).
+struct StepResult {
+  double tr;           // sum of diagonal entries of the output
+  double fro;          // sum of squares of the output entries
+  long long nnz_total; // stored entries
+  int max_nnz;         // longest row
+  int overflow_rows;   // rows that did not fit the output width
+  int max_count;       // longest post-threshold row, fitted or not
+  int n_fallback;      // rows handled by the large-row kernel
+  int nonfinite;       // 1 if tr or fro is not finite
+  int table_fail;      // rows where the large-row kernel could not run (internal)
+};
+
+// Device control block of one multiply launch.
+struct SpgemmCtl {
+  int overflow_rows;
+  int max_count;
+  int n_fallback;
+  int table_fail;
+};
+
+// rowstat[r] = {diagonal value, sum of squares} of output row r (post-threshold).
+// Reduces rowstat and out.nnz over n rows, copies ctl counters, into *res (device).
+void launch_reduce_rows(const double2 *rowstat, const int *nnz, int n, const SpgemmCtl *ctl,
+                        StepResult *res, cudaStream_t s);
+
+// ------------------------------------------------------------------ kernels (host launchers)
+// Multiply driver: out = drop_tau(alpha * A*B + beta * Add); Add may be null (beta ignored),
+// may equal A (SP2 update 2X - X^2), or equal out (in-place BLAS form).
+// Writes rowstat (n entries) and fills ctl; does not synchronise.
+struct MultiplyArgs {
+  const ellpack_t *A, *B, *Add;
+  ellpack_t *Out;
+  double alpha, beta, tau;
+  int table_log2;  // 0 = automatic
+};
+int multiply_async(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStream_t s);
+
+// A <- drop_tau(alpha*A + beta*B), rowstat/ctl as above.
+int add_async(ellpack_t *A, const ellpack_t *B, double alpha, double beta, double tau, double2 *rowstat,
+              SpgemmCtl *ctl, cudaStream_t s);
+
+// rowstat of an existing matrix (diag, sum of squares).
+int rowstat_async(const ellpack_t *A, double2 *rowstat, cudaStream_t s);
+
+// Gershgorin bounds into dev_bounds[0..1] = {emin, emax}.
+int gershgorin_async(const ellpack_t *H, double *dev_bounds, cudaStream_t s);
+
+// X0 = drop_tau((emax I - H)/(emax - emin)), bounds read from dev_bounds on the device.
+// X->width >= H->width + 1, X->dtype == SP2_F64, H F64.
+int x0_async(const ellpack_t *H, const double *dev_bounds, double tau, ellpack_t *X, cudaStream_t s);
+
+// Element-type conversion (same n; dst->width >= max row length of src).
+int convert_async(const ellpack_t *src, ellpack_t *dst, cudaStream_t s);
+
+// Copies src into dst (same dtype; dst->width >= src row lengths; rows copied as is).
+int copy_async(const ellpack_t *src, ellpack_t *dst, cudaStream_t s);
+
+}  // namespace sp2

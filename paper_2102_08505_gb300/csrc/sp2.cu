@@ -1,0 +1,324 @@
+// sp2.cu -- host-stepped SP2 purification (SP2-Basic of the ExaSP2 proxy, Section
+// "Performance Evaluation using an ExaSP2 Application"; recursion of Niklasson 2002).
+//
+// Per iteration the device does one fused pass: X' = drop_tau(alpha X*X + beta X) with
+// (alpha, beta) = (1, 0) for X^2 and (-1, 2) for 2X - X^2, whose epilogue also leaves
+// each row's diagonal value and sum of squares; one CTA reduces those in a fixed order
+// to tr X' and ||X'||_F^2 = tr X'^2 (X' symmetric).  The host reads that 56-byte result
+// once per iteration (the stop test and the branch of the next step need it) and
+// launches the next step.  Mixed precision runs the same loop on FP32 values with FP64
+// reductions, then converts X to FP64 and runs the FP64 tail iterations.
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+
+#include "common.cuh"
+
+namespace sp2 {
+namespace {
+
+struct Buffers {
+  cudaStream_t s;
+  double2 *rowstat = nullptr;
+  SpgemmCtl *ctl = nullptr;
+  StepResult *dres = nullptr;
+  double *bounds = nullptr;
+  ellpack_t X{}, Y{}, Hf{};
+  bool hf_owned = false;
+  ~Buffers() {
+    dev_free(rowstat, s);
+    dev_free(ctl, s);
+    dev_free(dres, s);
+    dev_free(bounds, s);
+    if (X.owner) ellpack_destroy(&X, s);
+    if (Y.owner) ellpack_destroy(&Y, s);
+    if (hf_owned) ellpack_destroy(&Hf, s);
+  }
+};
+
+int read_result(Buffers &b, StepResult *h) {
+  SP2_CUDA(cudaMemcpyAsync(h, b.dres, sizeof(StepResult), cudaMemcpyDeviceToHost, b.s));
+  SP2_CUDA(cudaStreamSynchronize(b.s));
+  return SP2_OK;
+}
+
+// (Re)allocates m with at least `width` slots and the given dtype; contents undefined.
+int ensure(ellpack_t *m, int n, int width, int dtype, cudaStream_t s) {
+  if (m->owner && m->width >= width && m->dtype == dtype) return SP2_OK;
+  if (m->owner) SP2_TRY(ellpack_destroy(m, s));
+  return ellpack_create(n, width, dtype, s, m);
+}
+
+int pick_table_log2(int expected_count, int hint) {
+  if (hint) return hint;
+  for (int lg = 9; lg <= 11; ++lg)
+    if ((1 << lg) / 2 >= expected_count) return lg;
+  return 11;
+}
+
+}  // namespace
+}  // namespace sp2
+
+using namespace sp2;
+
+extern "C" void sp2_options_default(sp2_options *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = SP2_PREC_F64;
+  o->max_iter = 100;
+  o->stall_rule = 1;
+  o->n_fp64_tail = 2;
+  o->max_width = 0;
+  o->table_log2 = 0;
+  o->tau = 1e-5;
+}
+
+extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2_options *opt_in, ellpack_t *D,
+                          sp2_stats *stats, void *stream) {
+  auto t0 = std::chrono::steady_clock::now();
+  SP2_TRY(check_matrix(H, "sp2_purify: H"));
+  if (!D) return fail(SP2E_ARG, "sp2_purify: D is NULL");
+  memset(D, 0, sizeof(*D));
+  sp2_options opt;
+  if (opt_in) opt = *opt_in; else sp2_options_default(&opt);
+  const int n = H->n;
+  if (!(nocc > 0.0) || !(nocc < (double)n)) return fail(SP2E_ARG, "sp2_purify: nocc=%g must lie in (0, %d)", nocc, n);
+  if (!(tol > 0.0) || !isfinite(tol)) return fail(SP2E_ARG, "sp2_purify: tol must be finite and > 0");
+  if (!(opt.tau >= 0.0) || !isfinite(opt.tau)) return fail(SP2E_ARG, "sp2_purify: tau must be finite and >= 0");
+  if (opt.precision != SP2_PREC_F64 && opt.precision != SP2_PREC_MIXED)
+    return fail(SP2E_ARG, "sp2_purify: unknown precision %d", opt.precision);
+  if (opt.max_iter < 0 || opt.max_iter + opt.n_fp64_tail >= SP2_STATS_CAP)
+    return fail(SP2E_ARG, "sp2_purify: max_iter + n_fp64_tail must be < %d", SP2_STATS_CAP);
+  if (opt.n_fp64_tail < 0) return fail(SP2E_ARG, "sp2_purify: n_fp64_tail < 0");
+  if (opt.table_log2 != 0 && (opt.table_log2 < 9 || opt.table_log2 > 11))
+    return fail(SP2E_ARG, "sp2_purify: table_log2 must be 0 or 9..11");
+  const int max_w = (opt.max_width > 0 && opt.max_width < n) ? opt.max_width : n;
+
+  Buffers b;
+  b.s = as_stream(stream);
+  cudaStream_t s = b.s;
+  sp2_stats st;
+  memset(&st, 0, sizeof(st));
+
+  SP2_TRY(dev_alloc((void **)&b.rowstat, sizeof(double2) * (size_t)n, s));
+  SP2_TRY(dev_alloc((void **)&b.ctl, sizeof(SpgemmCtl), s));
+  SP2_TRY(dev_alloc((void **)&b.dres, sizeof(StepResult), s));
+  SP2_TRY(dev_alloc((void **)&b.bounds, 2 * sizeof(double), s));
+
+  // F64 copy of H if needed
+  const ellpack_t *H64 = H;
+  if (H->dtype != SP2_F64) {
+    SP2_TRY(ellpack_create(n, H->width, SP2_F64, s, &b.Hf));
+    b.hf_owned = true;
+    SP2_TRY(convert_async(H, &b.Hf, s));
+    H64 = &b.Hf;
+  }
+
+  // a1: Gershgorin bounds (read back once: validated and reported)
+  SP2_TRY(gershgorin_async(H64, b.bounds, s));
+  double hb[2];
+  SP2_CUDA(cudaMemcpyAsync(hb, b.bounds, sizeof(hb), cudaMemcpyDeviceToHost, s));
+  SP2_CUDA(cudaStreamSynchronize(s));
+  st.emin = hb[0];
+  st.emax = hb[1];
+  if (!isfinite(hb[0]) || !isfinite(hb[1])) return fail(SP2E_NONFINITE, "sp2_purify: H holds a NaN or Inf");
+  if (!(hb[1] > hb[0])) return fail(SP2E_ARG, "sp2_purify: degenerate spectral bounds (e_max <= e_min)");
+
+  // a2: X0 in FP64
+  SP2_TRY(ellpack_create(n, H64->width + 1, SP2_F64, s, &b.X));
+  SP2_TRY(x0_async(H64, b.bounds, opt.tau, &b.X, s));
+
+  const bool mixed = opt.precision == SP2_PREC_MIXED;
+  if (mixed) {
+    SP2_TRY(ellpack_create(n, b.X.width, SP2_F32, s, &b.Y));
+    SP2_TRY(convert_async(&b.X, &b.Y, s));
+    ellpack_t t = b.X; b.X = b.Y; b.Y = t;  // X <- F32 copy, Y <- spare F64 buffer
+  }
+
+  // a3 for X0: traces from a pass over the stored matrix
+  SP2_TRY(rowstat_async(&b.X, b.rowstat, s));
+  launch_reduce_rows(b.rowstat, b.X.nnz, n, nullptr, b.dres, s);
+  SP2_CUDA(cudaGetLastError());
+  StepResult res;
+  SP2_TRY(read_result(b, &res));
+
+  enum Phase { MAIN, TAIL } phase = MAIN;
+  bool fp32 = mixed;
+  int tail_left = opt.n_fp64_tail;
+  bool armed = false;
+  int it = 0;
+  int status = 2;
+  int last_count = res.max_nnz;
+  for (;;) {
+    if (res.nonfinite) return fail(SP2E_NONFINITE, "sp2_purify: non-finite trace at iteration %d", it);
+    const double trX = res.tr, trX2 = res.fro;
+    const double err = fabs(trX - trX2) / (double)n;
+    if (it < SP2_STATS_CAP) {
+      st.trX[it] = trX;
+      st.trX2[it] = trX2;
+      st.err[it] = err;
+      st.nnz_total[it] = res.nnz_total;
+      st.max_row_nnz[it] = res.max_nnz;
+    }
+    // a7: stop rules
+    bool stop = false;
+    if (phase == MAIN) {
+      bool main_done = false;
+      if (err < tol) { main_done = true; status = 0; }
+      if (!main_done && (opt.stall_rule || fp32)) {
+        if (fabs(trX - trX2) < 0.1) armed = true;
+        if (armed && it >= 2 && err >= st.err[it - 2]) { main_done = true; status = 1; }
+      }
+      if (!main_done && it >= opt.max_iter) { main_done = true; status = 2; }
+      if (main_done) {
+        if (fp32 && status != 0 && tail_left > 0) {
+          // a8: promote to FP64 and refine
+          SP2_TRY(ensure(&b.Y, n, b.X.width, SP2_F64, s));
+          SP2_TRY(convert_async(&b.X, &b.Y, s));
+          ellpack_t t = b.X; b.X = b.Y; b.Y = t;
+          fp32 = false;
+          phase = TAIL;
+          st.fp32_iterations = it;
+        } else {
+          stop = true;
+        }
+      }
+    } else {  // TAIL
+      if (err < tol) { status = 0; stop = true; }
+      else if (tail_left == 0) { status = 1; stop = true; }
+    }
+    if (stop) break;
+
+    // a4: branch
+    const bool up = fabs(2.0 * trX - trX2 - nocc) < fabs(trX2 - nocc);
+    const double alpha = up ? -1.0 : 1.0, beta = up ? 2.0 : 0.0;
+    if (it < SP2_STATS_CAP) st.branch[it] = up ? 2 : 1;
+
+    // a5/a6: sized output, multiply with fused update and trace partials
+    long long guess = (long long)4 * res.max_nnz;
+    if (guess < (long long)(1.25 * last_count)) guess = (long long)(1.25 * last_count);
+    if (guess < 64) guess = 64;
+    int width = round_up((int)(guess < max_w ? guess : max_w), 32);
+    if (width > n) width = n;
+    const int lg = pick_table_log2((int)(1.5 * (last_count > res.max_nnz ? last_count : res.max_nnz)) + 32,
+                                   opt.table_log2);
+    for (;;) {
+      SP2_TRY(ensure(&b.Y, n, width, b.X.dtype, s));
+      MultiplyArgs a{&b.X, &b.X, beta != 0.0 ? &b.X : nullptr, &b.Y, alpha, beta, opt.tau, lg};
+      SP2_TRY(multiply_async(a, b.rowstat, b.ctl, s));
+      launch_reduce_rows(b.rowstat, b.Y.nnz, n, b.ctl, b.dres, s);
+      SP2_CUDA(cudaGetLastError());
+      SP2_TRY(read_result(b, &res));
+      if (res.overflow_rows == 0) break;
+      if (res.max_count > max_w)
+        return fail(SP2E_OVERFLOW, "sp2_purify: a row needs %d slots, above the width cap %d", res.max_count, max_w);
+      width = round_up((int)(1.25 * res.max_count) + 1, 32);
+      if (width > max_w) width = round_up(max_w, 32) > n ? n : round_up(max_w, 32);
+      if (width < res.max_count) width = res.max_count;
+      st.regrows++;
+    }
+    last_count = res.max_count;
+    ellpack_t t = b.X; b.X = b.Y; b.Y = t;
+    ++it;
+    if (phase == TAIL) --tail_left;
+  }
+  if (mixed && st.fp32_iterations == 0 && fp32) st.fp32_iterations = it;
+
+  // result: an F64 matrix owned by the caller
+  if (b.X.dtype != SP2_F64) {
+    SP2_TRY(ensure(&b.Y, n, b.X.width, SP2_F64, s));
+    SP2_TRY(convert_async(&b.X, &b.Y, s));
+    ellpack_t t = b.X; b.X = b.Y; b.Y = t;
+  }
+  *D = b.X;
+  memset(&b.X, 0, sizeof(b.X));
+  SP2_CUDA(cudaStreamSynchronize(s));
+  st.iterations = it;
+  st.status = status;
+  st.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = st;
+  if (status == 2) return fail(SP2E_NOTCONV, "sp2_purify: max_iter=%d reached (err %.3e)", opt.max_iter, st.err[it < SP2_STATS_CAP ? it : SP2_STATS_CAP - 1]);
+  return SP2_OK;
+}
+
+extern "C" int sp2_x0(const ellpack_t *H, double tau, ellpack_t *X0, double *emin, double *emax, void *stream) {
+  SP2_TRY(check_matrix(H, "sp2_x0: H"));
+  SP2_TRY(check_matrix(X0, "sp2_x0: X0"));
+  if (H->n != X0->n) return fail(SP2E_ARG, "sp2_x0: sizes differ");
+  if (H->dtype != SP2_F64 || X0->dtype != SP2_F64) return fail(SP2E_ARG, "sp2_x0: F64 matrices expected");
+  if (X0->width < H->width + 1) return fail(SP2E_ARG, "sp2_x0: X0 width %d < H width + 1", X0->width);
+  if (X0->idx == H->idx || X0->val == H->val || X0->nnz == H->nnz) return fail(SP2E_ARG, "sp2_x0: X0 aliases H");
+  if (!(tau >= 0.0) || !isfinite(tau)) return fail(SP2E_ARG, "sp2_x0: tau must be finite and >= 0");
+  cudaStream_t s = as_stream(stream);
+  double *db = nullptr;
+  SP2_TRY(dev_alloc((void **)&db, 2 * sizeof(double), s));
+  int rc = gershgorin_async(H, db, s);
+  double hb[2] = {0, 0};
+  if (rc == SP2_OK) {
+    cudaError_t e = cudaMemcpyAsync(hb, db, sizeof(hb), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "sp2_x0 bounds", __FILE__, __LINE__);
+  }
+  if (rc == SP2_OK && (!isfinite(hb[0]) || !isfinite(hb[1]))) rc = fail(SP2E_NONFINITE, "sp2_x0: H holds a NaN or Inf");
+  if (rc == SP2_OK && !(hb[1] > hb[0])) rc = fail(SP2E_ARG, "sp2_x0: degenerate spectral bounds");
+  if (rc == SP2_OK) rc = x0_async(H, db, tau, X0, s);
+  if (rc == SP2_OK) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "sp2_x0", __FILE__, __LINE__);
+  }
+  dev_free(db, s);
+  SP2_TRY(rc);
+  if (emin) *emin = hb[0];
+  if (emax) *emax = hb[1];
+  return SP2_OK;
+}
+
+extern "C" int sp2_step(const ellpack_t *X, ellpack_t *Xn, double nocc, double tau, sp2_step_info *info,
+                        void *stream) {
+  SP2_TRY(check_matrix(X, "sp2_step: X"));
+  SP2_TRY(check_matrix(Xn, "sp2_step: Xn"));
+  if (!info) return fail(SP2E_ARG, "sp2_step: info is NULL");
+  if (X->n != Xn->n || X->dtype != Xn->dtype) return fail(SP2E_ARG, "sp2_step: X and Xn differ in n or dtype");
+  if (X->idx == Xn->idx || X->val == Xn->val || X->nnz == Xn->nnz) return fail(SP2E_ARG, "sp2_step: Xn aliases X");
+  if (!(tau >= 0.0) || !isfinite(tau)) return fail(SP2E_ARG, "sp2_step: tau must be finite and >= 0");
+  if (!isfinite(nocc)) return fail(SP2E_ARG, "sp2_step: nocc not finite");
+  if (info->table_log2 != 0 && (info->table_log2 < 9 || info->table_log2 > 11))
+    return fail(SP2E_ARG, "sp2_step: table_log2 must be 0 or 9..11");
+  const int n = X->n;
+  Buffers b;
+  b.s = as_stream(stream);
+  cudaStream_t s = b.s;
+  SP2_TRY(dev_alloc((void **)&b.rowstat, sizeof(double2) * (size_t)n, s));
+  SP2_TRY(dev_alloc((void **)&b.ctl, sizeof(SpgemmCtl), s));
+  SP2_TRY(dev_alloc((void **)&b.dres, sizeof(StepResult), s));
+  StepResult res;
+  if (!info->have_traces) {
+    SP2_TRY(rowstat_async(X, b.rowstat, s));
+    launch_reduce_rows(b.rowstat, X->nnz, n, nullptr, b.dres, s);
+    SP2_CUDA(cudaGetLastError());
+    SP2_TRY(read_result(b, &res));
+    if (res.nonfinite) return fail(SP2E_NONFINITE, "sp2_step: non-finite trace of X");
+    info->trX = res.tr;
+    info->trX2 = res.fro;
+  }
+  const double trX = info->trX, trX2 = info->trX2;
+  info->err = fabs(trX - trX2) / (double)n;
+  const bool up = fabs(2.0 * trX - trX2 - nocc) < fabs(trX2 - nocc);
+  info->branch = up ? 2 : 1;
+  MultiplyArgs a{X, X, up ? X : nullptr, Xn, up ? -1.0 : 1.0, up ? 2.0 : 0.0, tau, info->table_log2};
+  SP2_TRY(multiply_async(a, b.rowstat, b.ctl, s));
+  launch_reduce_rows(b.rowstat, Xn->nnz, n, b.ctl, b.dres, s);
+  SP2_CUDA(cudaGetLastError());
+  SP2_TRY(read_result(b, &res));
+  info->trXn = res.tr;
+  info->trXn2 = res.fro;
+  info->nnz_total = res.nnz_total;
+  info->max_row_nnz = res.max_nnz;
+  info->required_width = res.max_count;
+  if (res.overflow_rows > 0)
+    return fail(SP2E_OVERFLOW, "sp2_step: %d row(s) need %d slots, Xn width is %d", res.overflow_rows, res.max_count,
+                Xn->width);
+  if (res.nonfinite) return fail(SP2E_NONFINITE, "sp2_step: non-finite trace of the result");
+  return SP2_OK;
+}

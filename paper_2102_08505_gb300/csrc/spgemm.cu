@@ -1,0 +1,741 @@
+// spgemm.cu -- thresholded ELLPACK matrix-matrix multiply and add.
+//
+// C = drop_tau(alpha * A*B + beta * Add): the "ELLPACK X2" operation of Section
+// "Performance Evaluation using System Matrices" with the "SP2 Loop Misc" update fused
+// into its epilogue (Section "Performance Evaluation using an ExaSP2 Application").
+//
+// Design (GB300): one warp per output row.  The warp walks row i of A; for every k it
+// streams row k of B (coalesced 32-wide loads, prefetched one k ahead into registers)
+// and accumulates a_ik * b_kj into a warp-private open-addressing hash table in shared
+// memory.  Within one k the columns j are distinct, so lanes never update the same slot
+// concurrently; a __syncwarp between k steps orders the steps, and the accumulation is a
+// plain load-FMA-store (one FMA per product, no floating-point atomics).  The slot of
+// column j keeps j's low bits and rotates each aligned block of 2^LOG2T columns by a
+// multiplicative hash of the block number, so consecutive columns -- the common case for
+// Morton-ordered sites -- land in consecutive slots and therefore distinct banks.
+// The epilogue compacts the table in place (drop rule), sorts the survivors by column
+// with a bitonic network, writes the row, and records the row's diagonal value and sum
+// of squares for the FP64 traces of the next SP2 iteration.
+// Rows whose pattern outgrows half the table are deferred to a second kernel that
+// accumulates into a dense global-memory row (one CTA per row), so no row size fails.
+#include <limits.h>
+#include <math.h>
+
+#include "common.cuh"
+
+namespace sp2 {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kEmpty = -1;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ double absval(double x) { return fabs(x); }
+__device__ __forceinline__ float absval(float x) { return fabsf(x); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <typename T>
+__device__ __forceinline__ bool keep_value(T v, T tau) {
+  return tau == T(0) || absval(v) > tau;
+}
+
+template <int LOG2T>
+__device__ __forceinline__ int hslot(int j) {
+  const unsigned blk = (unsigned)j >> LOG2T;
+  const unsigned rot = (blk * 0x9E3779B1u) >> (32 - LOG2T);
+  return (int)(((unsigned)j + rot) & ((1u << LOG2T) - 1u));
+}
+
+// Slot holding column j, inserting it (value 0) if absent; -1 if the table is full.
+template <int LOG2T, typename T>
+__device__ __forceinline__ int find_or_insert(int *keys, T *vals, int j, int &ins) {
+  constexpr int TS = 1 << LOG2T;
+  int h = hslot<LOG2T>(j);
+#pragma unroll 1
+  for (int p = 0; p < TS; ++p) {
+    const int cur = ((volatile int *)keys)[h];
+    if (cur == j) return h;
+    if (cur == kEmpty) {
+      const int old = atomicCAS(keys + h, kEmpty, j);
+      if (old == kEmpty) {
+        vals[h] = T(0);
+        ++ins;
+        return h;
+      }
+      if (old == j) return h;
+    }
+    h = (h + 1) & (TS - 1);
+  }
+  return -1;
+}
+
+template <typename T, int QM>
+__device__ __forceinline__ void load_brow(const EllView<T> &B, int k, int nb, int lane, int (&jr)[QM], T (&vr)[QM]) {
+  const int *bi = B.idx + (size_t)k * B.w;
+  const T *bv = B.val + (size_t)k * B.w;
+#pragma unroll
+  for (int u = 0; u < QM; ++u) {
+    const int q = lane + 32 * u;
+    if (q < nb) {
+      jr[u] = __ldg(bi + q);
+      vr[u] = __ldg(bv + q);
+    } else {
+      jr[u] = kEmpty;
+      vr[u] = T(0);
+    }
+  }
+}
+
+// In-place compaction of the occupied, kept slots to the front of the table; returns
+// the kept count and accumulates the row's diagonal value and sum of squares.
+template <typename T, int TS>
+__device__ __forceinline__ int compact_table(int *keys, T *vals, int row, T tau, int lane, double &dsum,
+                                             double &fsum) {
+  const unsigned lt = lanemask_lt();
+  int nk = 0;
+  for (int c = 0; c < TS; c += 32) {
+    const int key = keys[c + lane];
+    const T v = vals[c + lane];
+    const bool keep = key != kEmpty && keep_value(v, tau);
+    const unsigned m = __ballot_sync(kFull, keep);
+    __syncwarp();
+    if (keep) {
+      const int pos = nk + __popc(m & lt);
+      keys[pos] = key;
+      vals[pos] = v;
+      const double dv = (double)v;
+      if (key == row) dsum += dv;
+      fsum += dv * dv;
+    }
+    nk += __popc(m);
+  }
+  __syncwarp();
+  return nk;
+}
+
+// Bitonic sort of (keys, vals)[0..nk) by key inside the warp's table (capacity >= P).
+template <typename T>
+__device__ __forceinline__ void sort_prefix(int *keys, T *vals, int nk, int lane) {
+  int P = 32;
+  while (P < nk) P <<= 1;
+  for (int s = nk + lane; s < P; s += 32) keys[s] = INT_MAX;
+  __syncwarp();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int e = lane; e < (P >> 1); e += 32) {
+        const int i = ((e & ~(j - 1)) << 1) | (e & (j - 1));
+        const int ixj = i + j;
+        const int ki = keys[i], kj = keys[ixj];
+        const bool up = (i & k) == 0;
+        if ((ki > kj) == up) {
+          keys[i] = kj;
+          keys[ixj] = ki;
+          const T t = vals[i];
+          vals[i] = vals[ixj];
+          vals[ixj] = t;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+template <typename T, int LOG2T>
+struct HashCfg {
+  static constexpr int TS = 1 << LOG2T;
+  static constexpr int LIMIT = TS / 2;
+  static constexpr int BYTES_PER_WARP = TS * (int)(sizeof(int) + sizeof(T));
+  static constexpr int WARPS_RAW = (196608 / BYTES_PER_WARP);
+  static constexpr int WARPS = WARPS_RAW > 16 ? 16 : (WARPS_RAW < 1 ? 1 : WARPS_RAW);
+  static constexpr int SMEM = WARPS * BYTES_PER_WARP;
+};
+
+template <typename T, int LOG2T, int QM>
+__global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32)
+    spgemm_hash_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
+                       int use_add, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
+                       int *__restrict__ fb_list) {
+  using Cfg = HashCfg<T, LOG2T>;
+  constexpr int TS = Cfg::TS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int *keys = reinterpret_cast<int *>(smem + (size_t)wid * Cfg::BYTES_PER_WARP);
+  T *vals = reinterpret_cast<T *>(keys + TS);
+  const int nw = gridDim.x * Cfg::WARPS;
+  const int ncol = Out.n;
+  int wmax = 0, wover = 0;
+
+  for (int r = blockIdx.x * Cfg::WARPS + wid; r < A.n; r += nw) {
+    for (int s = lane * 4; s < TS; s += 128) *reinterpret_cast<int4 *>(keys + s) = make_int4(-1, -1, -1, -1);
+    __syncwarp();
+    int ins = 0;
+    int bad = 0;
+    if (use_add) {
+      const int nc = min(Add.nnz[r], Add.w);
+      for (int s = lane; s < nc; s += 32) {
+        const int j = Add.idx[(size_t)r * Add.w + s];
+        if ((unsigned)j >= (unsigned)ncol) continue;  // invalid column: ignored, never dereferenced
+        const T c = Add.val[(size_t)r * Add.w + s];
+        const int h = find_or_insert<LOG2T>(keys, vals, j, ins);
+        if (h >= 0) vals[h] = beta * c; else bad = 1;
+      }
+      __syncwarp();
+    }
+    bool aborted = __reduce_add_sync(kFull, ins + (bad << 20)) > Cfg::LIMIT;
+
+    const int na = min(A.nnz[r], A.w);
+    const int *ai = A.idx + (size_t)r * A.w;
+    const T *avp = A.val + (size_t)r * A.w;
+    for (int base = 0; base < na && !aborted; base += 32) {
+      const int s = base + lane;
+      int kk = 0, nbk = 0;
+      T av = T(0);
+      if (s < na) {
+        kk = __ldg(ai + s);
+        if ((unsigned)kk < (unsigned)B.n) {
+          av = alpha * __ldg(avp + s);
+          nbk = min(__ldg(B.nnz + kk), B.w);
+        } else {
+          kk = 0;  // invalid column of A: contributes nothing
+        }
+      }
+      const int cnt = min(32, na - base);
+      int jr[QM];
+      T vr[QM];
+      load_brow<T, QM>(B, __shfl_sync(kFull, kk, 0), __shfl_sync(kFull, nbk, 0), lane, jr, vr);
+      for (int t = 0; t < cnt; ++t) {
+        const T a = __shfl_sync(kFull, av, t);
+        const int k = __shfl_sync(kFull, kk, t);
+        const int nb = __shfl_sync(kFull, nbk, t);
+        const int tn = t + 1 < cnt ? t + 1 : t;
+        const int k1 = __shfl_sync(kFull, kk, tn);
+        const int nb1 = (t + 1 < cnt) ? __shfl_sync(kFull, nbk, tn) : 0;
+        int jn[QM];
+        T vn[QM];
+        load_brow<T, QM>(B, k1, nb1, lane, jn, vn);
+#pragma unroll
+        for (int u = 0; u < QM; ++u) {
+          if ((unsigned)jr[u] < (unsigned)ncol) {
+            const int h = find_or_insert<LOG2T>(keys, vals, jr[u], ins);
+            if (h >= 0) vals[h] = fmadd(a, vr[u], vals[h]); else bad = 1;
+          }
+        }
+        for (int q = lane + 32 * QM; q < nb; q += 32) {  // rows longer than 32*QM
+          const int j = __ldg(B.idx + (size_t)k * B.w + q);
+          if ((unsigned)j >= (unsigned)ncol) continue;
+          const T v = __ldg(B.val + (size_t)k * B.w + q);
+          const int h = find_or_insert<LOG2T>(keys, vals, j, ins);
+          if (h >= 0) vals[h] = fmadd(a, v, vals[h]); else bad = 1;
+        }
+        __syncwarp();
+        if (__reduce_add_sync(kFull, ins + (bad << 20)) > Cfg::LIMIT) {
+          aborted = true;
+          break;
+        }
+#pragma unroll
+        for (int u = 0; u < QM; ++u) {
+          jr[u] = jn[u];
+          vr[u] = vn[u];
+        }
+      }
+    }
+    if (aborted) {
+      if (lane == 0) {
+        const int p = atomicAdd(&ctl->n_fallback, 1);
+        fb_list[p] = r;
+      }
+      continue;
+    }
+    double dsum = 0.0, fsum = 0.0;
+    const int nk = compact_table<T, TS>(keys, vals, r, tau, lane, dsum, fsum);
+    dsum = warp_sum(dsum);
+    fsum = warp_sum(fsum);
+    wmax = max(wmax, nk);
+    if (lane == 0) rowstat[r] = make_double2(dsum, fsum);
+    if (nk > Out.w) {
+      ++wover;
+      continue;
+    }
+    sort_prefix<T>(keys, vals, nk, lane);
+    int *oi = Out.idx + (size_t)r * Out.w;
+    T *ov = Out.val + (size_t)r * Out.w;
+    for (int s = lane; s < nk; s += 32) {
+      oi[s] = keys[s];
+      ov[s] = vals[s];
+    }
+    if (lane == 0) Out.nnz[r] = nk;
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (wmax) atomicMax(&ctl->max_count, wmax);
+    if (wover) atomicAdd(&ctl->overflow_rows, wover);
+  }
+}
+
+// ------------------------------------------------------------------ large rows
+// One CTA per deferred row: accumulate into a dense row of n values in global memory
+// (per-CTA slot; marks start at -1 and accumulators at 0 and are restored after use),
+// then scan the columns in ascending order, so the output comes out sorted.
+constexpr int kDenseThreads = 512;
+
+template <typename T>
+__device__ __forceinline__ int block_exclusive_scan_ballot(bool flag, int *s_warp, int &total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned m = __ballot_sync(kFull, flag);
+  if (lane == 0) s_warp[wid] = __popc(m);
+  __syncthreads();
+  int before = 0;
+  total = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    const int c = s_warp[w];
+    if (w < wid) before += c;
+    total += c;
+  }
+  const int pos = before + __popc(m & lanemask_lt());
+  __syncthreads();
+  return pos;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kDenseThreads)
+    spgemm_dense_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
+                        int use_add, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
+                        const int *__restrict__ fb_list, T *__restrict__ acc_all, int *__restrict__ mark_all) {
+  __shared__ int s_warp[kDenseThreads / 32];
+  __shared__ double s_d[kDenseThreads / 32], s_f[kDenseThreads / 32];
+  const int n = A.n;
+  const int nfb = *((volatile int *)&ctl->n_fallback);
+  T *acc = acc_all + (size_t)blockIdx.x * n;
+  int *mark = mark_all + (size_t)blockIdx.x * n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  int lmax = 0, lover = 0;
+  for (int q = blockIdx.x; q < nfb; q += gridDim.x) {
+    const int r = fb_list[q];
+    if (use_add) {
+      const int nc = min(Add.nnz[r], Add.w);
+      for (int s = threadIdx.x; s < nc; s += blockDim.x) {
+        const int j = Add.idx[(size_t)r * Add.w + s];
+        if ((unsigned)j >= (unsigned)n) continue;
+        mark[j] = 1;
+        acc[j] += beta * Add.val[(size_t)r * Add.w + s];
+      }
+    }
+    __syncthreads();
+    const int na = min(A.nnz[r], A.w);
+    for (int t = wid; t < na; t += nwarp) {
+      const int k = A.idx[(size_t)r * A.w + t];
+      if ((unsigned)k >= (unsigned)B.n) continue;
+      const T a = alpha * A.val[(size_t)r * A.w + t];
+      const int nb = min(B.nnz[k], B.w);
+      for (int s = lane; s < nb; s += 32) {
+        const int j = B.idx[(size_t)k * B.w + s];
+        if ((unsigned)j >= (unsigned)n) continue;
+        mark[j] = 1;
+        atomicAdd(acc + j, a * B.val[(size_t)k * B.w + s]);
+      }
+    }
+    __syncthreads();
+    int base = 0;
+    double d = 0.0, f = 0.0;
+    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+      const int j = c0 + threadIdx.x;
+      bool keep = false;
+      T v = T(0);
+      if (j < n && mark[j] != -1) {
+        v = acc[j];
+        keep = keep_value(v, tau);
+        mark[j] = -1;
+        acc[j] = T(0);
+      }
+      int total;
+      const int pos = base + block_exclusive_scan_ballot<T>(keep, s_warp, total);
+      if (keep) {
+        if (pos < Out.w) {
+          Out.idx[(size_t)r * Out.w + pos] = j;
+          Out.val[(size_t)r * Out.w + pos] = v;
+        }
+        const double dv = (double)v;
+        if (j == r) d += dv;
+        f += dv * dv;
+      }
+      base += total;
+    }
+    d = warp_sum(d);
+    f = warp_sum(f);
+    if (lane == 0) { s_d[wid] = d; s_f[wid] = f; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double dd = 0.0, ff = 0.0;
+      for (int w = 0; w < nwarp; ++w) { dd += s_d[w]; ff += s_f[w]; }
+      rowstat[r] = make_double2(dd, ff);
+      lmax = max(lmax, base);
+      if (base > Out.w) ++lover; else Out.nnz[r] = base;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (lmax) atomicMax(&ctl->max_count, lmax);
+    if (lover) atomicAdd(&ctl->overflow_rows, lover);
+  }
+}
+
+// ------------------------------------------------------------------ add
+// A <- drop_tau(alpha*A + beta*B), warp per row, table of 2^11 slots.
+template <typename T>
+__global__ void __launch_bounds__(HashCfg<T, 11>::WARPS * 32)
+    add_hash_kernel(EllOut<T> A, EllView<T> B, T alpha, T beta, T tau, double2 *__restrict__ rowstat,
+                    SpgemmCtl *__restrict__ ctl, int *__restrict__ fb_list) {
+  using Cfg = HashCfg<T, 11>;
+  constexpr int TS = Cfg::TS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int *keys = reinterpret_cast<int *>(smem + (size_t)wid * Cfg::BYTES_PER_WARP);
+  T *vals = reinterpret_cast<T *>(keys + TS);
+  const int nw = gridDim.x * Cfg::WARPS;
+  int wmax = 0, wover = 0;
+  for (int r = blockIdx.x * Cfg::WARPS + wid; r < A.n; r += nw) {
+    const int na = min(A.nnz[r], A.w), nb = min(B.nnz[r], B.w);
+    if (na + nb > Cfg::LIMIT) {
+      if (lane == 0) {
+        const int p = atomicAdd(&ctl->n_fallback, 1);
+        fb_list[p] = r;
+      }
+      continue;
+    }
+    for (int s = lane * 4; s < TS; s += 128) *reinterpret_cast<int4 *>(keys + s) = make_int4(-1, -1, -1, -1);
+    __syncwarp();
+    int ins = 0;
+    for (int s = lane; s < na; s += 32) {
+      const int j = A.idx[(size_t)r * A.w + s];
+      if ((unsigned)j >= (unsigned)A.n) continue;
+      const int h = find_or_insert<11>(keys, vals, j, ins);
+      if (h >= 0) vals[h] = alpha * A.val[(size_t)r * A.w + s];
+    }
+    __syncwarp();
+    for (int s = lane; s < nb; s += 32) {
+      const int j = B.idx[(size_t)r * B.w + s];
+      if ((unsigned)j >= (unsigned)A.n) continue;
+      const int h = find_or_insert<11>(keys, vals, j, ins);
+      if (h >= 0) vals[h] = fmadd(beta, B.val[(size_t)r * B.w + s], vals[h]);
+    }
+    __syncwarp();
+    double dsum = 0.0, fsum = 0.0;
+    const int nk = compact_table<T, TS>(keys, vals, r, tau, lane, dsum, fsum);
+    dsum = warp_sum(dsum);
+    fsum = warp_sum(fsum);
+    wmax = max(wmax, nk);
+    if (lane == 0) rowstat[r] = make_double2(dsum, fsum);
+    if (nk > A.w) {
+      ++wover;
+      continue;
+    }
+    sort_prefix<T>(keys, vals, nk, lane);
+    for (int s = lane; s < nk; s += 32) {
+      A.idx[(size_t)r * A.w + s] = keys[s];
+      A.val[(size_t)r * A.w + s] = vals[s];
+    }
+    if (lane == 0) A.nnz[r] = nk;
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (wmax) atomicMax(&ctl->max_count, wmax);
+    if (wover) atomicAdd(&ctl->overflow_rows, wover);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kDenseThreads)
+    add_dense_kernel(EllOut<T> A, EllView<T> B, T alpha, T beta, T tau, double2 *__restrict__ rowstat,
+                     SpgemmCtl *__restrict__ ctl, const int *__restrict__ fb_list, T *__restrict__ acc_all,
+                     int *__restrict__ mark_all) {
+  __shared__ int s_warp[kDenseThreads / 32];
+  __shared__ double s_d[kDenseThreads / 32], s_f[kDenseThreads / 32];
+  const int n = A.n;
+  const int nfb = *((volatile int *)&ctl->n_fallback);
+  T *acc = acc_all + (size_t)blockIdx.x * n;
+  int *mark = mark_all + (size_t)blockIdx.x * n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  int lmax = 0, lover = 0;
+  for (int q = blockIdx.x; q < nfb; q += gridDim.x) {
+    const int r = fb_list[q];
+    const int na = min(A.nnz[r], A.w), nb = min(B.nnz[r], B.w);
+    for (int s = threadIdx.x; s < na; s += blockDim.x) {
+      const int j = A.idx[(size_t)r * A.w + s];
+      if ((unsigned)j >= (unsigned)n) continue;
+      mark[j] = 1;
+      acc[j] = alpha * A.val[(size_t)r * A.w + s];
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < nb; s += blockDim.x) {
+      const int j = B.idx[(size_t)r * B.w + s];
+      if ((unsigned)j >= (unsigned)n) continue;
+      mark[j] = 1;
+      acc[j] = fmadd(beta, B.val[(size_t)r * B.w + s], acc[j]);
+    }
+    __syncthreads();
+    int base = 0;
+    double d = 0.0, f = 0.0;
+    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+      const int j = c0 + threadIdx.x;
+      bool keep = false;
+      T v = T(0);
+      if (j < n && mark[j] != -1) {
+        v = acc[j];
+        keep = keep_value(v, tau);
+        mark[j] = -1;
+        acc[j] = T(0);
+      }
+      int total;
+      const int pos = base + block_exclusive_scan_ballot<T>(keep, s_warp, total);
+      if (keep) {
+        if (pos < A.w) {
+          A.idx[(size_t)r * A.w + pos] = j;
+          A.val[(size_t)r * A.w + pos] = v;
+        }
+        const double dv = (double)v;
+        if (j == r) d += dv;
+        f += dv * dv;
+      }
+      base += total;
+    }
+    d = warp_sum(d);
+    f = warp_sum(f);
+    if (lane == 0) { s_d[wid] = d; s_f[wid] = f; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double dd = 0.0, ff = 0.0;
+      for (int w = 0; w < nwarp; ++w) { dd += s_d[w]; ff += s_f[w]; }
+      rowstat[r] = make_double2(dd, ff);
+      lmax = max(lmax, base);
+      if (base > A.w) ++lover; else A.nnz[r] = base;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (lmax) atomicMax(&ctl->max_count, lmax);
+    if (lover) atomicAdd(&ctl->overflow_rows, lover);
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+namespace {
+
+constexpr int kFallbackSlots = 64;
+
+template <typename K>
+int set_smem(K kernel, int bytes) {
+  SP2_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  return SP2_OK;
+}
+
+template <typename T, int LOG2T, int QM>
+int launch_hash(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, cudaStream_t s) {
+  using Cfg = HashCfg<T, LOG2T>;
+  auto kern = spgemm_hash_kernel<T, LOG2T, QM>;
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    SP2_TRY(set_smem(kern, Cfg::SMEM));
+    attr_set[dev] = true;
+  }
+  const int n = a.A->n;
+  long long blocks = ((long long)n + Cfg::WARPS - 1) / Cfg::WARPS;
+  int occ = 0;
+  SP2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Cfg::WARPS * 32, Cfg::SMEM));
+  if (occ < 1) occ = 1;
+  long long cap = (long long)num_sms() * occ;
+  int grid = (int)(blocks < cap ? blocks : cap);
+  if (grid < 1) grid = 1;
+  const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
+  prof_begin(SP2_PROF_SPGEMM, s);
+  kern<<<grid, Cfg::WARPS * 32, Cfg::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
+                                               (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, rowstat,
+                                               ctl, fb);
+  note_launch();
+  prof_end(SP2_PROF_SPGEMM, s);
+  SP2_CUDA(cudaGetLastError());
+  return SP2_OK;
+}
+
+template <typename T>
+int multiply_t(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStream_t s) {
+  const int n = a.A->n;
+  int *fb = nullptr;
+  SP2_TRY(dev_alloc((void **)&fb, sizeof(int) * (size_t)n, s));
+  int qm_need = (a.B->width + 31) / 32;
+  int lg = a.table_log2;
+  if (lg == 0) lg = 10;
+  if (lg < 9) lg = 9;
+  if (lg > 11) lg = 11;
+  int rc;
+  if (qm_need <= 4) {
+    rc = lg == 9 ? launch_hash<T, 9, 4>(a, rowstat, ctl, fb, s)
+                 : lg == 10 ? launch_hash<T, 10, 4>(a, rowstat, ctl, fb, s) : launch_hash<T, 11, 4>(a, rowstat, ctl, fb, s);
+  } else {
+    rc = lg == 9 ? launch_hash<T, 9, 8>(a, rowstat, ctl, fb, s)
+                 : lg == 10 ? launch_hash<T, 10, 8>(a, rowstat, ctl, fb, s) : launch_hash<T, 11, 8>(a, rowstat, ctl, fb, s);
+  }
+  if (rc == SP2_OK) {
+    void *acc = nullptr;
+    int *mark = nullptr;
+    int slots = kFallbackSlots;
+    if (slots > n) slots = n;
+    rc = fallback_scratch(n, a.A->dtype, slots, &acc, &mark, s);
+    if (rc == SP2_OK) {
+      const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
+      prof_begin(SP2_PROF_LARGE, s);
+      spgemm_dense_kernel<T><<<slots, kDenseThreads, 0, s>>>(
+          view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha, (T)a.beta, (T)a.tau,
+          a.Add != nullptr && a.beta != 0.0, rowstat, ctl, fb, (T *)acc, mark);
+      note_launch();
+      prof_end(SP2_PROF_LARGE, s);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) rc = cuda_fail(e, "spgemm_dense_kernel", __FILE__, __LINE__);
+    }
+  }
+  dev_free(fb, s);
+  return rc;
+}
+
+template <typename T>
+int add_t(ellpack_t *A, const ellpack_t *B, double alpha, double beta, double tau, double2 *rowstat,
+          SpgemmCtl *ctl, cudaStream_t s) {
+  using Cfg = HashCfg<T, 11>;
+  const int n = A->n;
+  int *fb = nullptr;
+  SP2_TRY(dev_alloc((void **)&fb, sizeof(int) * (size_t)n, s));
+  int rc = set_smem(add_hash_kernel<T>, Cfg::SMEM);
+  if (rc == SP2_OK) {
+    long long blocks = ((long long)n + Cfg::WARPS - 1) / Cfg::WARPS;
+    long long cap = (long long)num_sms() * 2;
+    int grid = (int)(blocks < cap ? blocks : cap);
+    add_hash_kernel<T><<<grid, Cfg::WARPS * 32, Cfg::SMEM, s>>>(outview<T>(A), view<T>(B), (T)alpha, (T)beta,
+                                                               (T)tau, rowstat, ctl, fb);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) rc = cuda_fail(e, "add_hash_kernel", __FILE__, __LINE__);
+  }
+  if (rc == SP2_OK) {
+    void *acc = nullptr;
+    int *mark = nullptr;
+    int slots = kFallbackSlots < n ? kFallbackSlots : n;
+    rc = fallback_scratch(n, A->dtype, slots, &acc, &mark, s);
+    if (rc == SP2_OK) {
+      add_dense_kernel<T><<<slots, kDenseThreads, 0, s>>>(outview<T>(A), view<T>(B), (T)alpha, (T)beta, (T)tau,
+                                                          rowstat, ctl, fb, (T *)acc, mark);
+      note_launch();
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) rc = cuda_fail(e, "add_dense_kernel", __FILE__, __LINE__);
+    }
+  }
+  dev_free(fb, s);
+  return rc;
+}
+
+}  // namespace
+
+int multiply_async(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStream_t s) {
+  SP2_CUDA(cudaMemsetAsync(ctl, 0, sizeof(SpgemmCtl), s));
+  if (a.A->dtype == SP2_F64) return multiply_t<double>(a, rowstat, ctl, s);
+  return multiply_t<float>(a, rowstat, ctl, s);
+}
+
+int add_async(ellpack_t *A, const ellpack_t *B, double alpha, double beta, double tau, double2 *rowstat,
+              SpgemmCtl *ctl, cudaStream_t s) {
+  SP2_CUDA(cudaMemsetAsync(ctl, 0, sizeof(SpgemmCtl), s));
+  if (A->dtype == SP2_F64) return add_t<double>(A, B, alpha, beta, tau, rowstat, ctl, s);
+  return add_t<float>(A, B, alpha, beta, tau, rowstat, ctl, s);
+}
+
+}  // namespace sp2
+
+// ==================================================================== C ABI
+using namespace sp2;
+
+namespace {
+bool same_arrays(const ellpack_t *x, const ellpack_t *y) {
+  return x->idx == y->idx || x->val == y->val || x->nnz == y->nnz;
+}
+
+int check_tau(double tau, const char *who) {
+  if (!(tau >= 0.0) || !isfinite(tau)) return fail(SP2E_ARG, "%s: tau must be finite and >= 0", who);
+  return SP2_OK;
+}
+
+int finish_step(SpgemmCtl *ctl, double2 *rowstat, const ellpack_t *out, cudaStream_t s, int32_t *required_width,
+                const char *who) {
+  StepResult *dres = nullptr;
+  SP2_TRY(dev_alloc((void **)&dres, sizeof(StepResult), s));
+  launch_reduce_rows(rowstat, out->nnz, out->n, ctl, dres, s);
+  StepResult h;
+  cudaError_t e = cudaMemcpyAsync(&h, dres, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dev_free(dres, s);
+  if (e != cudaSuccess) return cuda_fail(e, who, __FILE__, __LINE__);
+  if (required_width) *required_width = h.max_count;
+  if (h.overflow_rows > 0)
+    return fail(SP2E_OVERFLOW, "%s: %d row(s) need %d slots, output width is %d", who, h.overflow_rows, h.max_count,
+                out->width);
+  return SP2_OK;
+}
+}  // namespace
+
+extern "C" int ellpack_multiply(const ellpack_t *A, const ellpack_t *B, ellpack_t *C, double alpha, double beta,
+                                double tau, void *stream, int32_t *required_width) {
+  SP2_TRY(check_matrix(A, "ellpack_multiply: A"));
+  SP2_TRY(check_matrix(B, "ellpack_multiply: B"));
+  SP2_TRY(check_matrix(C, "ellpack_multiply: C"));
+  SP2_TRY(check_tau(tau, "ellpack_multiply"));
+  if (A->n != B->n || A->n != C->n) return fail(SP2E_ARG, "ellpack_multiply: sizes differ (%d, %d, %d)", A->n, B->n, C->n);
+  if (A->dtype != B->dtype || A->dtype != C->dtype) return fail(SP2E_ARG, "ellpack_multiply: dtypes differ");
+  if (same_arrays(C, A) || same_arrays(C, B)) return fail(SP2E_ARG, "ellpack_multiply: C aliases A or B");
+  if (!isfinite(alpha) || !isfinite(beta)) return fail(SP2E_ARG, "ellpack_multiply: alpha/beta not finite");
+  cudaStream_t s = as_stream(stream);
+  double2 *rowstat = nullptr;
+  SpgemmCtl *ctl = nullptr;
+  SP2_TRY(dev_alloc((void **)&rowstat, sizeof(double2) * (size_t)A->n, s));
+  int rc = dev_alloc((void **)&ctl, sizeof(SpgemmCtl), s);
+  if (rc == SP2_OK) {
+    MultiplyArgs a{A, B, beta != 0.0 ? C : nullptr, C, alpha, beta, tau, 0};
+    rc = multiply_async(a, rowstat, ctl, s);
+    if (rc == SP2_OK) rc = finish_step(ctl, rowstat, C, s, required_width, "ellpack_multiply");
+  }
+  dev_free(rowstat, s);
+  dev_free(ctl, s);
+  return rc;
+}
+
+extern "C" int ellpack_add(ellpack_t *A, const ellpack_t *B, double alpha, double beta, double tau, void *stream,
+                           int32_t *required_width) {
+  SP2_TRY(check_matrix(A, "ellpack_add: A"));
+  SP2_TRY(check_matrix(B, "ellpack_add: B"));
+  SP2_TRY(check_tau(tau, "ellpack_add"));
+  if (A->n != B->n) return fail(SP2E_ARG, "ellpack_add: sizes differ");
+  if (A->dtype != B->dtype) return fail(SP2E_ARG, "ellpack_add: dtypes differ");
+  if (same_arrays(A, B)) return fail(SP2E_ARG, "ellpack_add: A and B alias");
+  if (!isfinite(alpha) || !isfinite(beta)) return fail(SP2E_ARG, "ellpack_add: alpha/beta not finite");
+  cudaStream_t s = as_stream(stream);
+  double2 *rowstat = nullptr;
+  SpgemmCtl *ctl = nullptr;
+  SP2_TRY(dev_alloc((void **)&rowstat, sizeof(double2) * (size_t)A->n, s));
+  int rc = dev_alloc((void **)&ctl, sizeof(SpgemmCtl), s);
+  if (rc == SP2_OK) {
+    rc = add_async(A, B, alpha, beta, tau, rowstat, ctl, s);
+    if (rc == SP2_OK) rc = finish_step(ctl, rowstat, A, s, required_width, "ellpack_add");
+  }
+  dev_free(rowstat, s);
+  dev_free(ctl, s);
+  return rc;
+}

@@ -1,0 +1,347 @@
+"""Thin ctypes binding of libsp2ell.so (C ABI in include/sp2ell.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA library.
+Device memory comes from torch tensors (wrapped, borrowed by the library) or from the
+library itself (matrices returned by sp2_purify, released when their Python owner is
+garbage-collected).  If the library is missing the import of this module raises; there
+is no other code path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsp2ell.so")
+
+SP2_OK = 0
+SP2E_ARG, SP2E_OVERFLOW, SP2E_NOMEM, SP2E_CUDA, SP2E_NOTCONV, SP2E_NONFINITE, SP2E_TIMEOUT = -1, -2, -3, -4, -5, -6, -7
+SP2_F64, SP2_F32 = 0, 1
+SP2_PREC_F64, SP2_PREC_MIXED = 0, 1
+SP2_STATS_CAP = 256
+_CODES = {0: "SP2_OK", -1: "SP2E_ARG", -2: "SP2E_OVERFLOW", -3: "SP2E_NOMEM", -4: "SP2E_CUDA",
+          -5: "SP2E_NOTCONV", -6: "SP2E_NONFINITE", -7: "SP2E_TIMEOUT"}
+
+
+class Sp2Error(RuntimeError):
+    def __init__(self, code, message):
+        super().__init__("%s: %s" % (_CODES.get(code, code), message))
+        self.code = code
+
+
+class ellpack_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("width", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("owner", ctypes.c_int32), ("idx", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("nnz", ctypes.c_void_p)]
+
+
+class sp2_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("stall_rule", ctypes.c_int32),
+                ("n_fp64_tail", ctypes.c_int32), ("max_width", ctypes.c_int32), ("table_log2", ctypes.c_int32),
+                ("tau", ctypes.c_double)]
+
+
+class sp2_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("status", ctypes.c_int32), ("fp32_iterations", ctypes.c_int32),
+                ("regrows", ctypes.c_int32), ("emin", ctypes.c_double), ("emax", ctypes.c_double),
+                ("time_ms", ctypes.c_double),
+                ("trX", ctypes.c_double * SP2_STATS_CAP), ("trX2", ctypes.c_double * SP2_STATS_CAP),
+                ("err", ctypes.c_double * SP2_STATS_CAP), ("branch", ctypes.c_int32 * SP2_STATS_CAP),
+                ("nnz_total", ctypes.c_int64 * SP2_STATS_CAP), ("max_row_nnz", ctypes.c_int32 * SP2_STATS_CAP)]
+
+
+class sp2_step_info(ctypes.Structure):
+    _fields_ = [("trX", ctypes.c_double), ("trX2", ctypes.c_double), ("have_traces", ctypes.c_int32),
+                ("branch", ctypes.c_int32), ("err", ctypes.c_double), ("trXn", ctypes.c_double),
+                ("trXn2", ctypes.c_double), ("nnz_total", ctypes.c_int64), ("max_row_nnz", ctypes.c_int32),
+                ("required_width", ctypes.c_int32), ("table_log2", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+SP2_PROF_CLASSES = 4
+PROF_NAMES = ("spgemm", "large_rows", "reduce", "other")
+
+
+class sp2_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("count", ctypes.c_int32 * SP2_PROF_CLASSES),
+                ("total_ms", ctypes.c_double * SP2_PROF_CLASSES)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libsp2ell.so is not built (run __graft_entry__.build() or "
+                          "python paper_2102_08505_gb300/build.py)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, V, I, D = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    E = P(ellpack_t)
+    sig = {
+        "sp2_version": ([], ctypes.c_int),
+        "sp2_last_error_string": ([], ctypes.c_char_p),
+        "ellpack_create": ([I, I, I, V, E], ctypes.c_int),
+        "ellpack_wrap": ([I, I, I, V, V, V, E], ctypes.c_int),
+        "ellpack_destroy": ([E, V], ctypes.c_int),
+        "ellpack_upload": ([E, V, V, V, V], ctypes.c_int),
+        "ellpack_download": ([E, V, V, V, V], ctypes.c_int),
+        "ellpack_copy": ([E, E, V], ctypes.c_int),
+        "ellpack_multiply": ([E, E, E, D, D, D, V, P(I)], ctypes.c_int),
+        "ellpack_add": ([E, E, D, D, D, V, P(I)], ctypes.c_int),
+        "ellpack_trace": ([E, P(D), V], ctypes.c_int),
+        "ellpack_frobenius2": ([E, P(D), V], ctypes.c_int),
+        "ellpack_gershgorin": ([E, P(D), P(D), V], ctypes.c_int),
+        "sp2_options_default": ([P(sp2_options)], None),
+        "sp2_purify": ([E, D, D, P(sp2_options), E, P(sp2_stats), V], ctypes.c_int),
+        "sp2_x0": ([E, D, E, P(D), P(D), V], ctypes.c_int),
+        "sp2_profile_start": ([], ctypes.c_int),
+        "sp2_profile_stop": ([P(sp2_profile)], ctypes.c_int),
+        "sp2_step": ([E, E, D, D, P(sp2_step_info), V], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+lib = _load()
+
+
+def _check(rc):
+    if rc != SP2_OK:
+        raise Sp2Error(rc, lib.sp2_last_error_string().decode())
+    return rc
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _torch_dtype(dt):
+    import torch
+    return torch.float64 if dt == SP2_F64 else torch.float32
+
+
+class Ellpack:
+    """ELLPACK matrix on the GPU: torch tensors idx int32[n, w], val f64/f32[n, w], nnz int32[n],
+    exposed to the library through a borrowed ellpack_t descriptor."""
+
+    def __init__(self, idx, val, nnz):
+        import torch
+        assert idx.is_cuda and val.is_cuda and nnz.is_cuda
+        assert idx.dtype == torch.int32 and nnz.dtype == torch.int32
+        assert val.dtype in (torch.float64, torch.float32)
+        assert idx.shape == val.shape and idx.dim() == 2 and nnz.shape == (idx.shape[0],)
+        self.idx, self.val, self.nnz = idx.contiguous(), val.contiguous(), nnz.contiguous()
+        self.dtype = SP2_F64 if val.dtype == torch.float64 else SP2_F32
+        self.desc = ellpack_t()
+        _check(lib.ellpack_wrap(self.n, self.width, self.dtype, self.idx.data_ptr(), self.val.data_ptr(),
+                                self.nnz.data_ptr(), ctypes.byref(self.desc)))
+
+    @property
+    def n(self):
+        return self.idx.shape[0]
+
+    @property
+    def width(self):
+        return self.idx.shape[1]
+
+    @classmethod
+    def empty(cls, n, width, dtype=SP2_F64, device="cuda"):
+        import torch
+        return cls(torch.zeros((n, width), dtype=torch.int32, device=device),
+                   torch.zeros((n, width), dtype=_torch_dtype(dtype), device=device),
+                   torch.zeros(n, dtype=torch.int32, device=device))
+
+    @classmethod
+    def from_numpy(cls, idx, val, nnz, dtype=SP2_F64, device="cuda"):
+        import torch
+        return cls(torch.as_tensor(np.ascontiguousarray(idx, np.int32), device=device),
+                   torch.as_tensor(np.ascontiguousarray(val), device=device).to(_torch_dtype(dtype)),
+                   torch.as_tensor(np.ascontiguousarray(nnz, np.int32), device=device))
+
+    def to_numpy(self):
+        return self.idx.cpu().numpy(), self.val.double().cpu().numpy(), self.nnz.cpu().numpy()
+
+
+class OwnedEllpack:
+    """A matrix allocated by the library (e.g. the density matrix of sp2_purify)."""
+
+    def __init__(self, desc):
+        self.desc = desc
+
+    @property
+    def n(self):
+        return self.desc.n
+
+    @property
+    def width(self):
+        return self.desc.width
+
+    @property
+    def dtype(self):
+        return self.desc.dtype
+
+    def to_torch(self, stream=None):
+        """Copy into a new torch-backed Ellpack (same width and dtype)."""
+        out = Ellpack.empty(self.n, self.width, self.dtype)
+        _check(lib.ellpack_copy(ctypes.byref(self.desc), ctypes.byref(out.desc), _stream(stream)))
+        return out
+
+    def to_numpy(self, stream=None):
+        n, w = self.n, self.width
+        idx = np.empty((n, w), np.int32)
+        val = np.empty((n, w), np.float64 if self.dtype == SP2_F64 else np.float32)
+        nnz = np.empty(n, np.int32)
+        _check(lib.ellpack_download(ctypes.byref(self.desc), idx.ctypes.data, val.ctypes.data, nnz.ctypes.data,
+                                    _stream(stream)))
+        return idx, val.astype(np.float64), nnz
+
+    def release(self, stream=None):
+        if self.desc is not None and self.desc.owner:
+            lib.ellpack_destroy(ctypes.byref(self.desc), _stream(stream) if stream is not None else None)
+        self.desc = None
+
+    def __del__(self):
+        try:
+            if self.desc is not None and self.desc.owner:
+                lib.ellpack_destroy(ctypes.byref(self.desc), None)
+        except Exception:
+            pass
+
+
+def _d(m):
+    return ctypes.byref(m.desc)
+
+
+def ellpack_create(n, width, dtype=SP2_F64, stream=None):
+    d = ellpack_t()
+    _check(lib.ellpack_create(n, width, dtype, _stream(stream), ctypes.byref(d)))
+    return OwnedEllpack(d)
+
+
+def ellpack_upload(m, idx, val, nnz, stream=None):
+    """Host numpy arrays -> device matrix (asynchronous; arrays must outlive the copy)."""
+    _check(lib.ellpack_upload(_d(m), idx.ctypes.data, val.ctypes.data, nnz.ctypes.data, _stream(stream)))
+
+
+def ellpack_download(m, idx, val, nnz, stream=None):
+    _check(lib.ellpack_download(_d(m), idx.ctypes.data, val.ctypes.data, nnz.ctypes.data, _stream(stream)))
+
+
+def ellpack_copy(src, dst, stream=None):
+    _check(lib.ellpack_copy(_d(src), _d(dst), _stream(stream)))
+
+
+def ellpack_multiply(A, B, C, alpha=1.0, beta=0.0, tau=0.0, stream=None, raise_on_overflow=True):
+    """C <- drop_tau(alpha*A*B + beta*C).  Returns the largest post-threshold row length;
+    raises Sp2Error(SP2E_OVERFLOW) if C is too narrow (unless raise_on_overflow=False,
+    then returns (status, required_width))."""
+    req = ctypes.c_int32(0)
+    rc = lib.ellpack_multiply(_d(A), _d(B), _d(C), float(alpha), float(beta), float(tau), _stream(stream),
+                              ctypes.byref(req))
+    if not raise_on_overflow:
+        if rc not in (SP2_OK, SP2E_OVERFLOW):
+            _check(rc)
+        return rc, req.value
+    _check(rc)
+    return req.value
+
+
+def ellpack_add(A, B, alpha=1.0, beta=1.0, tau=0.0, stream=None):
+    req = ctypes.c_int32(0)
+    _check(lib.ellpack_add(_d(A), _d(B), float(alpha), float(beta), float(tau), _stream(stream), ctypes.byref(req)))
+    return req.value
+
+
+def ellpack_trace(A, stream=None):
+    out = ctypes.c_double()
+    _check(lib.ellpack_trace(_d(A), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def ellpack_frobenius2(A, stream=None):
+    out = ctypes.c_double()
+    _check(lib.ellpack_frobenius2(_d(A), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def ellpack_gershgorin(H, stream=None):
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(lib.ellpack_gershgorin(_d(H), ctypes.byref(lo), ctypes.byref(hi), _stream(stream)))
+    return lo.value, hi.value
+
+
+def sp2_options_default(**kw):
+    o = sp2_options()
+    lib.sp2_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError("unknown sp2 option %r" % k)
+        setattr(o, k, v)
+    return o
+
+
+def stats_dict(st):
+    it = st.iterations
+    m = min(it + 1, SP2_STATS_CAP)
+    return {
+        "iterations": it, "status": {0: "converged", 1: "stalled", 2: "max_iter"}.get(st.status, st.status),
+        "fp32_iterations": st.fp32_iterations, "regrows": st.regrows, "emin": st.emin, "emax": st.emax,
+        "time_ms": st.time_ms,
+        "trX": np.array(st.trX[:m]), "trX2": np.array(st.trX2[:m]), "err": np.array(st.err[:m]),
+        "branch": ["X2" if b == 1 else "2X-X2" for b in st.branch[:min(it, SP2_STATS_CAP)]],
+        "nnz_total": np.array(st.nnz_total[:m]), "max_row_nnz": np.array(st.max_row_nnz[:m]),
+    }
+
+
+def sp2_purify(H, nocc, tol, options=None, stream=None, allow_notconv=False):
+    """SP2 purification of H; returns (D as OwnedEllpack, stats dict)."""
+    opt = options if options is not None else sp2_options_default()
+    D = ellpack_t()
+    st = sp2_stats()
+    rc = lib.sp2_purify(_d(H), float(nocc), float(tol), ctypes.byref(opt), ctypes.byref(D), ctypes.byref(st),
+                        _stream(stream))
+    out = OwnedEllpack(D)  # owns D even when an error is raised below (freed with it)
+    if rc == SP2E_NOTCONV and allow_notconv:
+        return out, stats_dict(st)
+    _check(rc)
+    return out, stats_dict(st)
+
+
+def sp2_x0(H, X0, tau, stream=None):
+    """X0 = drop_tau((e_max I - H)/(e_max - e_min)) into X0; returns (e_min, e_max)."""
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(lib.sp2_x0(_d(H), float(tau), _d(X0), ctypes.byref(lo), ctypes.byref(hi), _stream(stream)))
+    return lo.value, hi.value
+
+
+def sp2_step(X, Xn, nocc, tau, traces=None, table_log2=0, stream=None, raise_on_overflow=True):
+    """One SP2 iteration X -> Xn.  traces = (trX, trX2) of X if known.  Returns the
+    sp2_step_info record (and the status when raise_on_overflow=False)."""
+    info = sp2_step_info()
+    if traces is not None:
+        info.trX, info.trX2 = traces
+        info.have_traces = 1
+    info.table_log2 = table_log2
+    rc = lib.sp2_step(_d(X), _d(Xn), float(nocc), float(tau), ctypes.byref(info), _stream(stream))
+    if not raise_on_overflow:
+        if rc not in (SP2_OK, SP2E_OVERFLOW):
+            _check(rc)
+        return rc, info
+    _check(rc)
+    return info
+
+
+def sp2_profile_start():
+    _check(lib.sp2_profile_start())
+
+
+def sp2_profile_stop():
+    """Returns {"launches": L, "<class>": (count, total_ms), ...}."""
+    p = sp2_profile()
+    _check(lib.sp2_profile_stop(ctypes.byref(p)))
+    out = {"launches": int(p.launches)}
+    for i, name in enumerate(PROF_NAMES):
+        out[name] = (int(p.count[i]), float(p.total_ms[i]))
+    return out

@@ -1,0 +1,120 @@
+"""SP2 purification on the GPU against the CPU oracle and the exact projector (GPU)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2102_08505_gb300 import inputs as I
+from parity import compare_spgemm, dense_of
+
+pytestmark = pytest.mark.gpu
+
+
+def ell(t):
+    return O.Ell(*t)
+
+
+def dev(S, E, dtype=None):
+    return S.Ellpack.from_numpy(E.idx, E.val, E.nnz, S.SP2_F64 if dtype is None else dtype)
+
+
+def dense_D(D):
+    idx, val, nnz = D.to_numpy()
+    return dense_of(idx, val, nnz, D.n)
+
+
+def test_sp2_tau0_matches_eigen_projector(gpu):
+    S = gpu
+    n = 512
+    H = ell(I.banded(n, band=16, seed=1, delta=10.0))
+    D, st = S.sp2_purify(dev(S, H), n // 2, 1e-12, S.sp2_options_default(tau=0.0))
+    c = O.checks(H.to_dense(), dense_D(D), n // 2)
+    assert st["status"] == "converged"
+    assert c["proj_err"] < 1e-10 and c["trace_err"] < 1e-8 and c["idem_err"] < 1e-8 and c["comm_err"] < 1e-8
+
+
+@pytest.mark.parametrize("delta", [10.0, 0.0])
+def test_sp2_banded_f64_matches_oracle(gpu, delta):
+    """The banded Hamiltonian (n=1024, |i-j| <= 16, tau 1e-5, tol 1e-10), gapped (A/B
+    splitting 10) and as written (gapless)."""
+    S = gpu
+    n, nocc, tau, tol = 1024, 512, 1e-5, 1e-10
+    H = ell(I.banded(n, band=16, seed=1, delta=delta))
+    Do, so = O.sp2(H, nocc, tol, tau, max_iter=100)
+    D, sg = S.sp2_purify(dev(S, H), nocc, tol, S.sp2_options_default(tau=tau), allow_notconv=True)
+    assert sg["emin"] == pytest.approx(so["emin"], rel=1e-14) and sg["emax"] == pytest.approx(so["emax"], rel=1e-14)
+    assert sg["iterations"] == so["iterations"]
+    assert sg["branch"] == so["branch"]
+    assert sg["status"] == so["status"]
+    assert np.allclose(sg["trX"], so["trX"], rtol=1e-11, atol=1e-9)
+    assert np.allclose(sg["trX2"], so["trX2"], rtol=1e-11, atol=1e-9)
+    Dg, Dr = dense_D(D), Do.to_dense()
+    assert np.linalg.norm(Dg - Dr) / np.sqrt(n) < 1e-10
+    assert np.abs(Dg - Dr).max() < 1e-8
+
+
+def test_sp2_3d_gapped_f64_and_mixed(gpu):
+    """3D tight-binding with A/B splitting (n=4096, tau 1e-5): FP64 matches the oracle;
+    mixed precision (FP32 loop + 2 FP64 iterations) is within 1e-5 of it (Frobenius/sqrt(n))."""
+    S = gpu
+    n, tau, tol = 4096, 1e-5, 1e-10
+    H = ell(I.tight_binding(n, seed=11, delta=10.0))
+    O.set_threads(O.max_threads())
+    try:
+        Do, so = O.sp2(H, n // 2, tol, tau)
+    finally:
+        O.set_threads(1)
+    Dr = Do.to_dense()
+    D64, s64 = S.sp2_purify(dev(S, H), n // 2, tol, S.sp2_options_default(tau=tau))
+    assert s64["iterations"] == so["iterations"] and s64["branch"] == so["branch"]
+    assert np.linalg.norm(dense_D(D64) - Dr) / np.sqrt(n) < 1e-10
+    Dm, sm = S.sp2_purify(dev(S, H), n // 2, tol, S.sp2_options_default(tau=tau, precision=S.SP2_PREC_MIXED))
+    Dmd = dense_D(Dm)
+    assert np.linalg.norm(Dmd - Dr) / np.sqrt(n) <= 1e-5
+    assert sm["fp32_iterations"] >= 1 and sm["iterations"] - sm["fp32_iterations"] <= 2
+    assert abs(np.trace(Dmd) - n // 2) < 1e-3
+
+
+def test_sp2_step_matches_oracle_product(gpu):
+    S = gpu
+    n = 3000
+    H = ell(I.tight_binding(n, seed=2, delta=10.0))
+    lo, hi = O.gershgorin(H)
+    X0 = O.x0(H, lo, hi, 1e-5)
+    nocc = n / 2
+    tr, tr2 = O.trace(X0), float(sum((X0.row(i)[1] ** 2).sum() for i in range(n)))
+    up = abs(2 * tr - tr2 - nocc) < abs(tr2 - nocc)
+    alpha, beta = (-1.0, 2.0) if up else (1.0, 0.0)
+    ref = O.spgemm(X0, X0, X0, alpha, beta, 1e-5)
+    w = ((int(ref.nnz.max()) + 31) // 32) * 32
+    dX = dev(S, X0)
+    out = S.Ellpack.empty(n, w)
+    info = S.sp2_step(dX, out, nocc, 1e-5)
+    assert info.branch == (2 if up else 1)
+    assert info.trX == pytest.approx(tr, rel=1e-13) and info.trX2 == pytest.approx(tr2, rel=1e-13)
+    compare_spgemm(out.to_numpy(), X0, X0, X0, alpha, beta, 1e-5)
+    assert info.trXn == pytest.approx(O.trace(ref), rel=1e-12)
+    assert info.nnz_total == int(ref.nnz.sum())
+    assert info.max_row_nnz == int(ref.nnz.max())
+
+
+def test_sp2_errors(gpu):
+    S = gpu
+    n = 64
+    H = ell(I.banded(n, band=3, seed=1, delta=10.0))
+    with pytest.raises(S.Sp2Error) as e:
+        S.sp2_purify(dev(S, H), 0.0, 1e-10)
+    assert e.value.code == S.SP2E_ARG
+    with pytest.raises(S.Sp2Error) as e:
+        S.sp2_purify(dev(S, H), n / 2, -1.0)
+    assert e.value.code == S.SP2E_ARG
+    bad = H.val.copy()
+    bad[3, 0] = np.nan
+    with pytest.raises(S.Sp2Error) as e:
+        S.sp2_purify(S.Ellpack.from_numpy(H.idx, bad, H.nnz), n / 2, 1e-10)
+    assert e.value.code == S.SP2E_NONFINITE
+    D, st = S.sp2_purify(dev(S, H), n / 2, 1e-14, S.sp2_options_default(max_iter=3, stall_rule=0),
+                         allow_notconv=True)
+    assert st["status"] == "max_iter" and st["iterations"] == 3 and D.n == n
+    with pytest.raises(S.Sp2Error) as e:
+        S.sp2_purify(dev(S, H), n / 2, 1e-14, S.sp2_options_default(max_iter=3, stall_rule=0))
+    assert e.value.code == S.SP2E_NOTCONV

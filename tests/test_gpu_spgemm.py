@@ -1,0 +1,246 @@
+"""CUDA thresholded ELLPACK SpGEMM / add / reductions against the CPU oracle (GPU)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2102_08505_gb300 import inputs as I
+from parity import compare_spgemm, dense_of, sorted_rows_ok
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(S, E, dtype=None, width=None):
+    dt = S.SP2_F64 if dtype is None else dtype
+    idx, val, nnz = E.idx, E.val, E.nnz
+    if width is not None and width > idx.shape[1]:
+        pad = width - idx.shape[1]
+        idx = np.pad(idx, ((0, 0), (0, pad)))
+        val = np.pad(val, ((0, 0), (0, pad)), constant_values=np.nan)
+    return S.Ellpack.from_numpy(idx, val, nnz, dt)
+
+
+def ell(t):
+    return O.Ell(*t)
+
+
+def f32_input(E):
+    """The oracle's input for an FP32 run: the FP64 values rounded to FP32."""
+    return O.Ell(E.idx, E.val.astype(np.float32).astype(np.float64), E.nnz)
+
+
+RANDOM_CASES = [
+    # n, seed, min, max nnz, full rows, empty rows
+    (1, 0, 0, 1, (), ()),
+    (37, 1, 0, 9, (4,), (0, 5)),
+    (700, 2, 0, 40, (10,), (3, 699)),
+    (3000, 3, 20, 160, (7, 2999), (100,)),   # B rows above 128 entries: register tail path
+]
+
+
+@pytest.mark.parametrize("case", RANDOM_CASES)
+@pytest.mark.parametrize("ab", [(1.0, 0.0), (-1.0, 2.0), (0.5, -1.5)])
+@pytest.mark.parametrize("tau", [0.0, 2e-3])
+def test_multiply_f64_random(gpu, case, ab, tau):
+    S = gpu
+    n, seed, lo, hi, full, empty = case
+    alpha, beta = ab
+    A = ell(I.random_sparse(n, seed=seed, min_nnz=lo, max_nnz=hi, full_rows=full, empty_rows=empty,
+                            value_scale=0.2))
+    B = ell(I.random_sparse(n, seed=seed + 7, min_nnz=lo, max_nnz=hi, full_rows=full[:1], value_scale=0.2))
+    C = ell(I.random_sparse(n, seed=seed + 9, min_nnz=0, max_nnz=max(1, hi // 4)))
+    ref = O.spgemm(A, B, C if beta else None, alpha, beta, tau)
+    width = max(32, ((int(ref.nnz.max()) + 31) // 32) * 32)
+    dA, dB = dev(S, A), dev(S, B)
+    dC = dev(S, C, width=width)
+    S.ellpack_multiply(dA, dB, dC, alpha, beta, tau)
+    compare_spgemm(dC.to_numpy(), A, B, C, alpha, beta, tau)
+
+
+@pytest.mark.parametrize("case", RANDOM_CASES[1:])
+@pytest.mark.parametrize("tau", [0.0, 2e-3])
+def test_multiply_f32_random(gpu, case, tau):
+    S = gpu
+    n, seed, lo, hi, full, empty = case
+    A = f32_input(ell(I.random_sparse(n, seed=seed, min_nnz=lo, max_nnz=hi, full_rows=full, empty_rows=empty,
+                                      value_scale=0.2)))
+    C = f32_input(ell(I.random_sparse(n, seed=seed + 9, min_nnz=0, max_nnz=max(1, hi // 4))))
+    ref = O.spgemm(A, A, C, -1.0, 2.0, tau)
+    width = max(32, ((int(ref.nnz.max()) + 31) // 32) * 32)
+    dA = dev(S, A, S.SP2_F32)
+    dC = dev(S, C, S.SP2_F32, width=width)
+    S.ellpack_multiply(dA, dA, dC, -1.0, 2.0, tau)
+    compare_spgemm(dC.to_numpy(), A, A, C, -1.0, 2.0, tau, fp32=True)
+
+
+def test_multiply_long_rows_use_large_row_kernel(gpu):
+    """Rows with more than half a hash table of distinct columns go to the dense
+    global-memory kernel; results must be the same."""
+    S = gpu
+    n = 2500
+    A = ell(I.random_sparse(n, seed=51, min_nnz=5, max_nnz=60, full_rows=tuple(range(0, n, 97)), value_scale=0.3))
+    ref = O.spgemm(A, A, None, 1.0, 0.0, 1e-4)
+    assert ref.nnz.max() > 600  # some rows exceed the default table's limit
+    width = ((int(ref.nnz.max()) + 31) // 32) * 32
+    dA = dev(S, A)
+    dC = S.Ellpack.empty(n, width)
+    S.ellpack_multiply(dA, dA, dC, 1.0, 0.0, 1e-4)
+    compare_spgemm(dC.to_numpy(), A, A, None, 1.0, 0.0, 1e-4)
+
+
+def test_multiply_tight_binding_product(gpu):
+    """Realistic pattern: X0^2 of a Morton-ordered 3D tight-binding Hamiltonian."""
+    S = gpu
+    n = 6000
+    H = ell(I.tight_binding(n, seed=3))
+    lo, hi = O.gershgorin(H)
+    X0 = O.x0(H, lo, hi, 1e-6)
+    X1 = O.spgemm(X0, X0, None, 1.0, 0.0, 1e-6)
+    ref = O.spgemm(X1, X1, X1, -1.0, 2.0, 1e-6)
+    w = ((int(ref.nnz.max()) + 31) // 32) * 32
+    d1 = dev(S, X1)
+    out = S.Ellpack.empty(n, w)
+    S.ellpack_multiply(d1, d1, out, 1.0, 0.0, 1e-6)
+    compare_spgemm(out.to_numpy(), X1, X1, None, 1.0, 0.0, 1e-6)
+    # fused update as in an SP2 step: 2X - X^2 (C holds X beforehand)
+    out2 = dev(S, X1, width=w)
+    S.ellpack_multiply(d1, d1, out2, -1.0, 2.0, 1e-6)
+    compare_spgemm(out2.to_numpy(), X1, X1, X1, -1.0, 2.0, 1e-6)
+
+
+def test_multiply_is_deterministic(gpu):
+    S = gpu
+    n = 3000
+    A = ell(I.random_sparse(n, seed=61, min_nnz=10, max_nnz=80, value_scale=0.2))
+    dA = dev(S, A)
+    outs = []
+    for _ in range(2):
+        C = S.Ellpack.empty(n, 1024)
+        S.ellpack_multiply(dA, dA, C, 1.0, 0.0, 1e-5)
+        outs.append(C.to_numpy())
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(np.nan_to_num(a), np.nan_to_num(b))
+
+
+def test_multiply_overflow_status_and_retry(gpu):
+    S = gpu
+    n = 500
+    A = ell(I.random_sparse(n, seed=71, min_nnz=5, max_nnz=20))
+    ref = O.spgemm(A, A, None, 1.0, 0.0, 0.0)
+    need = int(ref.nnz.max())
+    dA = dev(S, A)
+    small = S.Ellpack.empty(n, 32)
+    rc, req = S.ellpack_multiply(dA, dA, small, raise_on_overflow=False)
+    assert rc == S.SP2E_OVERFLOW and req == need
+    big = S.Ellpack.empty(n, ((need + 31) // 32) * 32)
+    assert S.ellpack_multiply(dA, dA, big) == need
+    compare_spgemm(big.to_numpy(), A, A, None, 1.0, 0.0, 0.0)
+
+
+def test_multiply_argument_errors(gpu):
+    S = gpu
+    A = dev(S, ell(I.random_sparse(10, seed=1, max_nnz=3)))
+    B = dev(S, ell(I.random_sparse(11, seed=2, max_nnz=3)))
+    with pytest.raises(S.Sp2Error) as e:
+        S.ellpack_multiply(A, A, A)  # C aliases A
+    assert e.value.code == S.SP2E_ARG
+    with pytest.raises(S.Sp2Error) as e:
+        S.ellpack_multiply(A, B, S.Ellpack.empty(10, 32))
+    assert e.value.code == S.SP2E_ARG
+    with pytest.raises(S.Sp2Error) as e:
+        S.ellpack_multiply(A, A, S.Ellpack.empty(10, 32), tau=-1.0)
+    assert e.value.code == S.SP2E_ARG
+    with pytest.raises(S.Sp2Error) as e:
+        S.ellpack_multiply(A, A, S.Ellpack.empty(10, 32, S.SP2_F32))
+    assert e.value.code == S.SP2E_ARG
+
+
+@pytest.mark.parametrize("ab", [(1.0, 1.0), (2.0, -1.0), (-0.5, 0.25)])
+@pytest.mark.parametrize("tau", [0.0, 0.05])
+def test_add(gpu, ab, tau):
+    S = gpu
+    alpha, beta = ab
+    n = 900
+    A = ell(I.random_sparse(n, seed=81, min_nnz=0, max_nnz=30, empty_rows=(0,)))
+    B = ell(I.random_sparse(n, seed=82, min_nnz=0, max_nnz=30, empty_rows=(0, 1)))
+    ref = O.add(A, B, alpha, beta, tau)
+    dA = dev(S, A, width=64)
+    dB = dev(S, B)
+    S.ellpack_add(dA, dB, alpha, beta, tau)
+    gi, gv, gn = dA.to_numpy()
+    assert sorted_rows_ok(gi, gn)
+    G = dense_of(gi, gv, gn, n)
+    R = ref.to_dense()
+    scale = abs(alpha) * np.abs(A.to_dense()) + abs(beta) * np.abs(B.to_dense())
+    bound = 1e-15 * scale + 1e-300
+    pg = np.zeros((n, n), bool)
+    pr = np.zeros((n, n), bool)
+    for i in range(n):
+        pg[i, gi[i, :gn[i]]] = True
+        pr[i, ref.row(i)[0]] = True
+    if tau == 0.0:
+        assert np.array_equal(pg, pr)
+    both = pg & pr
+    assert np.all(np.abs(G - R)[both] <= bound[both])
+    flip = pg ^ pr
+    exact = alpha * A.to_dense() + beta * B.to_dense()
+    assert np.all(np.abs(np.abs(exact[flip]) - tau) <= bound[flip])
+
+
+def test_add_long_rows(gpu):
+    S = gpu
+    n = 3000
+    A = ell(I.random_sparse(n, seed=91, min_nnz=0, max_nnz=700, width=704))
+    B = ell(I.random_sparse(n, seed=92, min_nnz=0, max_nnz=700))
+    ref = O.add(A, B, 1.0, -1.0, 0.0)
+    w = ((int(ref.nnz.max()) + 31) // 32) * 32
+    dA = dev(S, A, width=w)
+    S.ellpack_add(dA, dev(S, B), 1.0, -1.0, 0.0)
+    gi, gv, gn = dA.to_numpy()
+    assert np.array_equal(gn, ref.nnz)
+    for i in range(0, n, 37):
+        assert np.array_equal(gi[i, :gn[i]], ref.row(i)[0])
+        assert np.allclose(gv[i, :gn[i]], ref.row(i)[1], rtol=0, atol=1e-15)
+
+
+def test_trace_frobenius_gershgorin(gpu):
+    S = gpu
+    H = ell(I.tight_binding(5000, seed=5))
+    dH = dev(S, H)
+    tr = S.ellpack_trace(dH)
+    assert tr == pytest.approx(O.trace(H), rel=1e-13, abs=1e-12)
+    fro = S.ellpack_frobenius2(dH)
+    want = float(sum((H.row(i)[1] ** 2).sum() for i in range(H.n)))
+    assert fro == pytest.approx(want, rel=1e-13)
+    lo, hi = S.ellpack_gershgorin(dH)
+    olo, ohi = O.gershgorin(H)
+    assert lo == pytest.approx(olo, rel=1e-13) and hi == pytest.approx(ohi, rel=1e-13)
+    dF = dev(S, H, S.SP2_F32)
+    assert S.ellpack_trace(dF) == pytest.approx(O.trace(H), rel=1e-6)
+
+
+@pytest.mark.parametrize("tau", [0.0, 1e-2])
+def test_x0(gpu, tau):
+    S = gpu
+    n = 2000
+    H = ell(I.banded(n, band=12, seed=4))
+    # knock out a few diagonal entries so that the insertion path runs
+    Hd_idx, Hd_val, Hd_nnz = H.idx.copy(), H.val.copy(), H.nnz.copy()
+    for i in (0, 5, 1999):
+        k = Hd_nnz[i]
+        cols = Hd_idx[i, :k]
+        keep = cols != i
+        m = int(keep.sum())
+        Hd_idx[i, :m], Hd_val[i, :m] = cols[keep], Hd_val[i, :k][keep]
+        Hd_nnz[i] = m
+    H = O.Ell(Hd_idx, Hd_val, Hd_nnz)
+    lo, hi = O.gershgorin(H)
+    ref = O.x0(H, lo, hi, tau)
+    dH = dev(S, H)
+    X = S.Ellpack.empty(n, H.w + 32)
+    glo, ghi = S.sp2_x0(dH, X, tau)
+    assert glo == pytest.approx(lo, rel=1e-14) and ghi == pytest.approx(hi, rel=1e-14)
+    gi, gv, gn = X.to_numpy()
+    assert np.array_equal(gn, ref.nnz)
+    for i in range(n):
+        assert np.array_equal(gi[i, :gn[i]], ref.row(i)[0])
+        assert np.allclose(gv[i, :gn[i]], ref.row(i)[1], rtol=5e-16, atol=1e-300)

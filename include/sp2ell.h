@@ -102,8 +102,9 @@ int ellpack_upload(ellpack_t *m, const int32_t *h_idx, const void *h_val, const 
 int ellpack_download(const ellpack_t *m, int32_t *h_idx, void *h_val, int32_t *h_nnz, void *stream);
 
 /* Device-to-device copy of rows: dst row i <- src row i (values converted when the
- * dtypes differ), asynchronous.  Same n; dst->width >= src->width.  dst must not share
- * arrays with src.  Errors: SP2E_ARG, SP2E_CUDA. */
+ * dtypes differ).  Same n; dst must not share arrays with src; dst->width may be smaller
+ * than src->width as long as every row fits, else SP2E_OVERFLOW (those rows are left
+ * unwritten).  Synchronises `stream`.  Errors: SP2E_ARG, SP2E_OVERFLOW, SP2E_CUDA. */
 int ellpack_copy(const ellpack_t *src, ellpack_t *dst, void *stream);
 
 /*
@@ -175,8 +176,10 @@ int sp2_profile_stop(sp2_profile *out);
 /* ---------------------------------------------------------------- SP2 */
 
 #define SP2_PREC_F64 0      /* every step in FP64 */
-#define SP2_PREC_MIXED 1    /* FP32 products and updates; FP64 traces, branch, stop test,
-                               then n_fp64_tail FP64 iterations */
+#define SP2_PREC_MIXED 1    /* FP32 products and updates with FP64 traces, branch and tests
+                               until err_n < switch_tol (or the FP32 loop stalls); then X is
+                               promoted to FP64 and at least n_fp64_tail FP64 iterations run,
+                               continuing until the FP64 stop rule holds */
 
 #define SP2_STATS_CAP 256   /* per-iteration records kept in sp2_stats */
 
@@ -184,10 +187,12 @@ typedef struct sp2_options {
   int32_t precision;    /* SP2_PREC_F64 or SP2_PREC_MIXED */
   int32_t max_iter;     /* cap on updates (default 100) */
   int32_t stall_rule;   /* 1: stop once |trX - trX2| < 0.1 has been seen and err_n >= err_{n-2} */
-  int32_t n_fp64_tail;  /* MIXED: FP64 iterations after the FP32 loop stops (default 2) */
+  int32_t n_fp64_tail;  /* MIXED: minimum FP64 iterations after the switch (default 2) */
   int32_t max_width;    /* cap on the working width (0 = n); SP2E_OVERFLOW beyond it */
   int32_t table_log2;   /* per-row hash-table size hint for the SpGEMM (0 = automatic) */
   double tau;           /* drop tolerance (default 1e-5) */
+  double switch_tol;    /* MIXED: leave the FP32 loop once err_n < switch_tol (0 = automatic:
+                           max(tol, 1e-6)); the FP32 stall rule also ends it */
 } sp2_options;
 
 typedef struct sp2_stats {

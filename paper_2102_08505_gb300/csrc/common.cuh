@@ -134,8 +134,9 @@ int gershgorin_async(const ellpack_t *H, double *dev_bounds, cudaStream_t s);
 // X->width >= H->width + 1, X->dtype == SP2_F64, H F64.
 int x0_async(const ellpack_t *H, const double *dev_bounds, double tau, ellpack_t *X, cudaStream_t s);
 
-// Element-type conversion (same n; dst->width >= max row length of src).
-int convert_async(const ellpack_t *src, ellpack_t *dst, cudaStream_t s);
+// Element-type conversion (same n).  Rows longer than dst->width are left unwritten and
+// counted in *overflow (device int, may be null).
+int convert_async(const ellpack_t *src, ellpack_t *dst, cudaStream_t s, int *overflow = nullptr);
 
 // Copies src into dst (same dtype; dst->width >= src row lengths; rows copied as is).
 int copy_async(const ellpack_t *src, ellpack_t *dst, cudaStream_t s);

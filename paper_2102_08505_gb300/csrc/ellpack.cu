@@ -233,13 +233,17 @@ __global__ void gershgorin_rows_kernel(EllView<T> H, double2 *__restrict__ part)
       d += __shfl_xor_sync(0xffffffffu, d, o);
       rad += __shfl_xor_sync(0xffffffffu, rad, o);
     }
-    lo = fmin(lo, d - rad);
-    hi = fmax(hi, d + rad);
+    const double l = d - rad, h = d + rad;
+    lo = (isnan(l) || isnan(lo)) ? NAN : fmin(lo, l);  // fmin/fmax would drop a NaN
+    hi = (isnan(h) || isnan(hi)) ? NAN : fmax(hi, h);
   }
   if (lane == 0) { s_lo[wid] = lo; s_hi[wid] = hi; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { lo = fmin(lo, s_lo[w]); hi = fmax(hi, s_hi[w]); }
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      lo = (isnan(lo) || isnan(s_lo[w])) ? NAN : fmin(lo, s_lo[w]);
+      hi = (isnan(hi) || isnan(s_hi[w])) ? NAN : fmax(hi, s_hi[w]);
+    }
     part[blockIdx.x] = make_double2(lo, hi);
   }
 }
@@ -368,11 +372,16 @@ int x0_async(const ellpack_t *H, const double *dev_bounds, double tau, ellpack_t
 
 // ------------------------------------------------------------------ conversion / copy
 template <typename S, typename D>
-__global__ void convert_kernel(EllView<S> a, EllOut<D> b) {
+__global__ void convert_kernel(EllView<S> a, EllOut<D> b, int *__restrict__ overflow) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < a.n; r += warps) {
-    const int k = min(a.nnz[r], min(a.w, b.w));
+    const int k0 = min(a.nnz[r], a.w);
+    if (k0 > b.w) {  // row does not fit: counted, left unwritten
+      if (lane == 0 && overflow) atomicAdd(overflow, 1);
+      continue;
+    }
+    const int k = k0;
     for (int s = lane; s < k; s += 32) {
       b.idx[(size_t)r * b.w + s] = a.idx[(size_t)r * a.w + s];
       b.val[(size_t)r * b.w + s] = (D)a.val[(size_t)r * a.w + s];
@@ -381,21 +390,21 @@ __global__ void convert_kernel(EllView<S> a, EllOut<D> b) {
   }
 }
 
-int convert_async(const ellpack_t *src, ellpack_t *dst, cudaStream_t s) {
+int convert_async(const ellpack_t *src, ellpack_t *dst, cudaStream_t s, int *overflow) {
   int grid = grid_for_rows(src->n, 8);
   if (src->dtype == SP2_F64 && dst->dtype == SP2_F32)
-    { convert_kernel<double, float><<<grid, 256, 0, s>>>(view<double>(src), outview<float>(dst)); note_launch(); }
+    { convert_kernel<double, float><<<grid, 256, 0, s>>>(view<double>(src), outview<float>(dst), overflow); note_launch(); }
   else if (src->dtype == SP2_F32 && dst->dtype == SP2_F64)
-    { convert_kernel<float, double><<<grid, 256, 0, s>>>(view<float>(src), outview<double>(dst)); note_launch(); }
+    { convert_kernel<float, double><<<grid, 256, 0, s>>>(view<float>(src), outview<double>(dst), overflow); note_launch(); }
   else if (src->dtype == SP2_F64)
-    { convert_kernel<double, double><<<grid, 256, 0, s>>>(view<double>(src), outview<double>(dst)); note_launch(); }
+    { convert_kernel<double, double><<<grid, 256, 0, s>>>(view<double>(src), outview<double>(dst), overflow); note_launch(); }
   else
-    { convert_kernel<float, float><<<grid, 256, 0, s>>>(view<float>(src), outview<float>(dst)); note_launch(); }
+    { convert_kernel<float, float><<<grid, 256, 0, s>>>(view<float>(src), outview<float>(dst), overflow); note_launch(); }
   SP2_CUDA(cudaGetLastError());
   return SP2_OK;
 }
 
-int copy_async(const ellpack_t *src, ellpack_t *dst, cudaStream_t s) { return convert_async(src, dst, s); }
+int copy_async(const ellpack_t *src, ellpack_t *dst, cudaStream_t s) { return convert_async(src, dst, s, nullptr); }
 
 }  // namespace sp2
 
@@ -551,8 +560,21 @@ extern "C" int ellpack_copy(const ellpack_t *src, ellpack_t *dst, void *stream) 
   SP2_TRY(check_matrix(src, "ellpack_copy: src"));
   SP2_TRY(check_matrix(dst, "ellpack_copy: dst"));
   if (src->n != dst->n) return fail(SP2E_ARG, "ellpack_copy: sizes differ");
-  if (dst->width < src->width) return fail(SP2E_ARG, "ellpack_copy: dst width %d < src width %d", dst->width, src->width);
   if (src->idx == dst->idx || src->val == dst->val || src->nnz == dst->nnz)
     return fail(SP2E_ARG, "ellpack_copy: src and dst share arrays");
-  return convert_async(src, dst, as_stream(stream));
+  cudaStream_t s = as_stream(stream);
+  int *dov = nullptr;
+  SP2_TRY(dev_alloc((void **)&dov, sizeof(int), s));
+  int hov = 0;
+  cudaError_t e = cudaMemsetAsync(dov, 0, sizeof(int), s);
+  int rc = e == cudaSuccess ? convert_async(src, dst, s, dov) : cuda_fail(e, "ellpack_copy", __FILE__, __LINE__);
+  if (rc == SP2_OK) {
+    e = cudaMemcpyAsync(&hov, dov, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "ellpack_copy", __FILE__, __LINE__);
+  }
+  dev_free(dov, s);
+  SP2_TRY(rc);
+  if (hov > 0) return fail(SP2E_OVERFLOW, "ellpack_copy: %d row(s) longer than dst width %d", hov, dst->width);
+  return SP2_OK;
 }

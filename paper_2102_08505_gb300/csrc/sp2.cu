@@ -72,6 +72,7 @@ extern "C" void sp2_options_default(sp2_options *o) {
   o->max_width = 0;
   o->table_log2 = 0;
   o->tau = 1e-5;
+  o->switch_tol = 0.0;
 }
 
 extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2_options *opt_in, ellpack_t *D,
@@ -94,6 +95,8 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   if (opt.table_log2 != 0 && (opt.table_log2 < 9 || opt.table_log2 > 11))
     return fail(SP2E_ARG, "sp2_purify: table_log2 must be 0 or 9..11");
   const int max_w = (opt.max_width > 0 && opt.max_width < n) ? opt.max_width : n;
+  if (!(opt.switch_tol >= 0.0) || !isfinite(opt.switch_tol)) return fail(SP2E_ARG, "sp2_purify: bad switch_tol");
+  const double switch_tol = opt.switch_tol > 0.0 ? opt.switch_tol : (tol > 1e-6 ? tol : 1e-6);
 
   Buffers b;
   b.s = as_stream(stream);
@@ -163,16 +166,23 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
     }
     // a7: stop rules
     bool stop = false;
+    const bool stalled = [&] {
+      if (fabs(trX - trX2) < 0.1) armed = true;
+      return armed && it >= 2 && err >= st.err[it - 2];
+    }();
     if (phase == MAIN) {
       bool main_done = false;
-      if (err < tol) { main_done = true; status = 0; }
-      if (!main_done && (opt.stall_rule || fp32)) {
-        if (fabs(trX - trX2) < 0.1) armed = true;
-        if (armed && it >= 2 && err >= st.err[it - 2]) { main_done = true; status = 1; }
+      if (fp32) {
+        // FP32 loop: leave at switch_tol, at an FP32 stall, or at max_iter
+        if (err < switch_tol || stalled || it >= opt.max_iter) main_done = true;
+        if (it >= opt.max_iter) status = 2;
+      } else {
+        if (err < tol) { main_done = true; status = 0; }
+        else if (opt.stall_rule && stalled) { main_done = true; status = 1; }
+        else if (it >= opt.max_iter) { main_done = true; status = 2; }
       }
-      if (!main_done && it >= opt.max_iter) { main_done = true; status = 2; }
       if (main_done) {
-        if (fp32 && status != 0 && tail_left > 0) {
+        if (fp32 && tail_left > 0 && status != 2) {
           // a8: promote to FP64 and refine
           SP2_TRY(ensure(&b.Y, n, b.X.width, SP2_F64, s));
           SP2_TRY(convert_async(&b.X, &b.Y, s));
@@ -181,12 +191,17 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
           phase = TAIL;
           st.fp32_iterations = it;
         } else {
+          if (fp32 && status != 2) status = err < tol ? 0 : 1;
           stop = true;
         }
       }
-    } else {  // TAIL
-      if (err < tol) { status = 0; stop = true; }
-      else if (tail_left == 0) { status = 1; stop = true; }
+    } else {  // TAIL: at least n_fp64_tail FP64 iterations, then the FP64 stop rule
+      const int done = it - st.fp32_iterations;
+      if (done >= opt.n_fp64_tail) {
+        if (err < tol) { status = 0; stop = true; }
+        else if (stalled) { status = 1; stop = true; }
+      }
+      if (!stop && it >= opt.max_iter + opt.n_fp64_tail) { status = 2; stop = true; }
     }
     if (stop) break;
 
@@ -221,7 +236,6 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
     last_count = res.max_count;
     ellpack_t t = b.X; b.X = b.Y; b.Y = t;
     ++it;
-    if (phase == TAIL) --tail_left;
   }
   if (mixed && st.fp32_iterations == 0 && fp32) st.fp32_iterations = it;
 

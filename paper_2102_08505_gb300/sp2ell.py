@@ -38,7 +38,7 @@ class ellpack_t(ctypes.Structure):
 class sp2_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("stall_rule", ctypes.c_int32),
                 ("n_fp64_tail", ctypes.c_int32), ("max_width", ctypes.c_int32), ("table_log2", ctypes.c_int32),
-                ("tau", ctypes.c_double)]
+                ("tau", ctypes.c_double), ("switch_tol", ctypes.c_double)]
 
 
 class sp2_stats(ctypes.Structure):

@@ -54,7 +54,8 @@ def test_sp2_banded_f64_matches_oracle(gpu, delta):
 
 def test_sp2_3d_gapped_f64_and_mixed(gpu):
     """3D tight-binding with A/B splitting (n=4096, tau 1e-5): FP64 matches the oracle;
-    mixed precision (FP32 loop + 2 FP64 iterations) is within 1e-5 of it (Frobenius/sqrt(n))."""
+    mixed precision (FP32 loop to err < 1e-6, then >= 2 FP64 iterations) is within 1e-5
+    of it (Frobenius / sqrt(n))."""
     S = gpu
     n, tau, tol = 4096, 1e-5, 1e-10
     H = ell(I.tight_binding(n, seed=11, delta=10.0))
@@ -69,8 +70,13 @@ def test_sp2_3d_gapped_f64_and_mixed(gpu):
     assert np.linalg.norm(dense_D(D64) - Dr) / np.sqrt(n) < 1e-10
     Dm, sm = S.sp2_purify(dev(S, H), n // 2, tol, S.sp2_options_default(tau=tau, precision=S.SP2_PREC_MIXED))
     Dmd = dense_D(Dm)
-    assert np.linalg.norm(Dmd - Dr) / np.sqrt(n) <= 1e-5
-    assert sm["fp32_iterations"] >= 1 and sm["iterations"] - sm["fp32_iterations"] <= 2
+    dD = np.linalg.norm(Dmd - Dr) / np.sqrt(n)
+    print("mixed: iterations %d (fp32 %d) status %s dD %.3e err %s; fp64: %d iterations, branches %s / %s" % (
+        sm["iterations"], sm["fp32_iterations"], sm["status"], dD, ["%.2e" % e for e in sm["err"]],
+        so["iterations"], "".join("2" if b == "2X-X2" else "1" for b in sm["branch"]),
+        "".join("2" if b == "2X-X2" else "1" for b in so["branch"])))
+    assert dD <= 1e-5
+    assert sm["fp32_iterations"] >= 1 and sm["iterations"] - sm["fp32_iterations"] >= 2
     assert abs(np.trace(Dmd) - n // 2) < 1e-3
 
 

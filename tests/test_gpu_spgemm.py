@@ -112,9 +112,10 @@ def test_multiply_is_deterministic(gpu):
     n = 3000
     A = ell(I.random_sparse(n, seed=61, min_nnz=10, max_nnz=80, value_scale=0.2))
     dA = dev(S, A)
+    need = S.ellpack_multiply(dA, dA, S.Ellpack.empty(n, 32), 1.0, 0.0, 1e-5, raise_on_overflow=False)[1]
     outs = []
     for _ in range(2):
-        C = S.Ellpack.empty(n, 1024)
+        C = S.Ellpack.empty(n, ((need + 31) // 32) * 32)
         S.ellpack_multiply(dA, dA, C, 1.0, 0.0, 1e-5)
         outs.append(C.to_numpy())
     for a, b in zip(outs[0], outs[1]):

@@ -90,17 +90,17 @@ struct StepResult {
   int max_nnz;         // longest row
   int overflow_rows;   // rows that did not fit the output width
   int max_count;       // longest post-threshold row, fitted or not
-  int n_fallback;      // rows handled by the large-row kernel
+  int n_fallback;      // rows deferred from the per-warp tables to the 2^14-slot table
   int nonfinite;       // 1 if tr or fro is not finite
-  int table_fail;      // rows where the large-row kernel could not run (internal)
+  int n_fallback2;     // rows deferred further to the dense global-row kernel
 };
 
 // Device control block of one multiply launch.
 struct SpgemmCtl {
   int overflow_rows;
   int max_count;
-  int n_fallback;
-  int table_fail;
+  int n_fallback;   // count of the first deferred-row list
+  int n_fallback2;  // count of the second deferred-row list
 };
 
 // rowstat[r] = {diagonal value, sum of squares} of output row r (post-threshold).
@@ -116,7 +116,7 @@ struct MultiplyArgs {
   const ellpack_t *A, *B, *Add;
   ellpack_t *Out;
   double alpha, beta, tau;
-  int table_log2;  // 0 = automatic
+  int table_log2;  // per-warp table size of the first pass: 10, 11 or 12 (0 = 11)
 };
 int multiply_async(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStream_t s);
 

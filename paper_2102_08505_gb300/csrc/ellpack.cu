@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_rows_kernel(const doubl
     o.overflow_rows = ctl ? ctl->overflow_rows : 0;
     o.max_count = ctl ? ctl->max_count : s_max[0];
     o.n_fallback = ctl ? ctl->n_fallback : 0;
-    o.table_fail = ctl ? ctl->table_fail : 0;
+    o.n_fallback2 = ctl ? ctl->n_fallback2 : 0;
     o.nonfinite = (isfinite(o.tr) && isfinite(o.fro)) ? 0 : 1;
     *res = o;
   }

@@ -50,12 +50,6 @@ int ensure(ellpack_t *m, int n, int width, int dtype, cudaStream_t s) {
   return ellpack_create(n, width, dtype, s, m);
 }
 
-int pick_table_log2(int expected_count, int hint) {
-  if (hint) return hint;
-  for (int lg = 9; lg <= 11; ++lg)
-    if ((1 << lg) / 2 >= expected_count) return lg;
-  return 11;
-}
 
 }  // namespace
 }  // namespace sp2
@@ -92,8 +86,8 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   if (opt.max_iter < 0 || opt.max_iter + opt.n_fp64_tail >= SP2_STATS_CAP)
     return fail(SP2E_ARG, "sp2_purify: max_iter + n_fp64_tail must be < %d", SP2_STATS_CAP);
   if (opt.n_fp64_tail < 0) return fail(SP2E_ARG, "sp2_purify: n_fp64_tail < 0");
-  if (opt.table_log2 != 0 && (opt.table_log2 < 9 || opt.table_log2 > 11))
-    return fail(SP2E_ARG, "sp2_purify: table_log2 must be 0 or 9..11");
+  if (opt.table_log2 != 0 && (opt.table_log2 < 10 || opt.table_log2 > 12))
+    return fail(SP2E_ARG, "sp2_purify: table_log2 must be 0 or 10..12");
   const int max_w = (opt.max_width > 0 && opt.max_width < n) ? opt.max_width : n;
   if (!(opt.switch_tol >= 0.0) || !isfinite(opt.switch_tol)) return fail(SP2E_ARG, "sp2_purify: bad switch_tol");
   const double switch_tol = opt.switch_tol > 0.0 ? opt.switch_tol : (tol > 1e-6 ? tol : 1e-6);
@@ -216,8 +210,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
     if (guess < 64) guess = 64;
     int width = round_up((int)(guess < max_w ? guess : max_w), 32);
     if (width > n) width = n;
-    const int lg = pick_table_log2((int)(1.5 * (last_count > res.max_nnz ? last_count : res.max_nnz)) + 32,
-                                   opt.table_log2);
+    const int lg = opt.table_log2;
     for (;;) {
       SP2_TRY(ensure(&b.Y, n, width, b.X.dtype, s));
       MultiplyArgs a{&b.X, &b.X, beta != 0.0 ? &b.X : nullptr, &b.Y, alpha, beta, opt.tau, lg};
@@ -297,8 +290,8 @@ extern "C" int sp2_step(const ellpack_t *X, ellpack_t *Xn, double nocc, double t
   if (X->idx == Xn->idx || X->val == Xn->val || X->nnz == Xn->nnz) return fail(SP2E_ARG, "sp2_step: Xn aliases X");
   if (!(tau >= 0.0) || !isfinite(tau)) return fail(SP2E_ARG, "sp2_step: tau must be finite and >= 0");
   if (!isfinite(nocc)) return fail(SP2E_ARG, "sp2_step: nocc not finite");
-  if (info->table_log2 != 0 && (info->table_log2 < 9 || info->table_log2 > 11))
-    return fail(SP2E_ARG, "sp2_step: table_log2 must be 0 or 9..11");
+  if (info->table_log2 != 0 && (info->table_log2 < 10 || info->table_log2 > 12))
+    return fail(SP2E_ARG, "sp2_step: table_log2 must be 0 or 10..12");
   const int n = X->n;
   Buffers b;
   b.s = as_stream(stream);

@@ -44,18 +44,31 @@ __device__ __forceinline__ bool keep_value(T v, T tau) {
   return tau == T(0) || absval(v) > tau;
 }
 
+// Slot layout: columns are taken in groups of 32 (j >> 5).  A group g owns the aligned
+// block base(g) = 32 * h1(g) and column j first tries slot base(g) + (j & 31), so the
+// first probe of column j always falls in shared-memory bank j mod 32: 32 lanes holding
+// 32 different values of j mod 32 (any run of consecutive columns) never conflict.  A
+// collision moves the key by an odd, group-dependent stride (double hashing), which
+// visits every slot of the power-of-two table and keeps colliding groups from forming
+// long primary clusters.
 template <int LOG2T>
-__device__ __forceinline__ int hslot(int j) {
-  const unsigned blk = (unsigned)j >> LOG2T;
-  const unsigned rot = (blk * 0x9E3779B1u) >> (32 - LOG2T);
-  return (int)(((unsigned)j + rot) & ((1u << LOG2T) - 1u));
+__device__ __forceinline__ int hslot0(int j) {
+  const unsigned g = (unsigned)j >> 5;
+  const unsigned blk = (g * 0x9E3779B1u) >> (32 - (LOG2T - 5));
+  return (int)((blk << 5) | ((unsigned)j & 31u));
+}
+template <int LOG2T>
+__device__ __forceinline__ int hstride(int j) {
+  const unsigned g = (unsigned)j >> 5;
+  return (int)((((g * 0x85EBCA6Bu) >> (32 - (LOG2T - 1))) << 1) | 1u);
 }
 
 // Slot holding column j, inserting it (value 0) if absent; -1 if the table is full.
 template <int LOG2T, typename T>
 __device__ __forceinline__ int find_or_insert(int *keys, T *vals, int j, int &ins) {
   constexpr int TS = 1 << LOG2T;
-  int h = hslot<LOG2T>(j);
+  int h = hslot0<LOG2T>(j);
+  const int step = hstride<LOG2T>(j);
 #pragma unroll 1
   for (int p = 0; p < TS; ++p) {
     const int cur = ((volatile int *)keys)[h];
@@ -69,7 +82,7 @@ __device__ __forceinline__ int find_or_insert(int *keys, T *vals, int j, int &in
       }
       if (old == j) return h;
     }
-    h = (h + 1) & (TS - 1);
+    h = (h + step) & (TS - 1);
   }
   return -1;
 }
@@ -151,21 +164,25 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Table geometry: 2^LOG2T slots of (int key, T value) per warp; a row is deferred to a
+// larger table once more than LIMIT = 7/8 of the slots hold keys.  As many warps per
+// CTA as fit in 224 KB of shared memory (at most 16).
 template <typename T, int LOG2T>
 struct HashCfg {
   static constexpr int TS = 1 << LOG2T;
-  static constexpr int LIMIT = TS / 2;
+  static constexpr int LIMIT = TS - TS / 8;
   static constexpr int BYTES_PER_WARP = TS * (int)(sizeof(int) + sizeof(T));
-  static constexpr int WARPS_RAW = (196608 / BYTES_PER_WARP);
+  static constexpr int WARPS_RAW = (229376 / BYTES_PER_WARP);
   static constexpr int WARPS = WARPS_RAW > 16 ? 16 : (WARPS_RAW < 1 ? 1 : WARPS_RAW);
   static constexpr int SMEM = WARPS * BYTES_PER_WARP;
 };
 
 template <typename T, int LOG2T, int QM>
-__global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32)
+__global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32, 1)
     spgemm_hash_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
                        int use_add, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
-                       int *__restrict__ fb_list) {
+                       const int *__restrict__ row_list, const int *__restrict__ row_count,
+                       int *__restrict__ fb_list, int *__restrict__ fb_count) {
   using Cfg = HashCfg<T, LOG2T>;
   constexpr int TS = Cfg::TS;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -174,9 +191,12 @@ __global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32)
   T *vals = reinterpret_cast<T *>(keys + TS);
   const int nw = gridDim.x * Cfg::WARPS;
   const int ncol = Out.n;
+  // rows: all of them, or the list left by a smaller-table pass (count on the device)
+  const int nrows = row_list ? *((volatile const int *)row_count) : A.n;
   int wmax = 0, wover = 0;
 
-  for (int r = blockIdx.x * Cfg::WARPS + wid; r < A.n; r += nw) {
+  for (int q = blockIdx.x * Cfg::WARPS + wid; q < nrows; q += nw) {
+    const int r = row_list ? row_list[q] : q;
     for (int s = lane * 4; s < TS; s += 128) *reinterpret_cast<int4 *>(keys + s) = make_int4(-1, -1, -1, -1);
     __syncwarp();
     int ins = 0;
@@ -224,13 +244,28 @@ __global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32)
         int jn[QM];
         T vn[QM];
         load_brow<T, QM>(B, k1, nb1, lane, jn, vn);
+        // The QM columns a lane holds in this step are distinct, so their slots are too:
+        // probe all keys, resolve misses, load all values, then FMA and store -- QM
+        // independent chains instead of one serial chain.
+        int hs[QM], cur[QM];
 #pragma unroll
         for (int u = 0; u < QM; ++u) {
-          if ((unsigned)jr[u] < (unsigned)ncol) {
-            const int h = find_or_insert<LOG2T>(keys, vals, jr[u], ins);
-            if (h >= 0) vals[h] = fmadd(a, vr[u], vals[h]); else bad = 1;
+          hs[u] = (unsigned)jr[u] < (unsigned)ncol ? hslot0<LOG2T>(jr[u]) : -1;
+          cur[u] = hs[u] >= 0 ? (int)((volatile int *)keys)[hs[u]] : (int)kEmpty;
+        }
+#pragma unroll
+        for (int u = 0; u < QM; ++u) {
+          if (hs[u] >= 0 && cur[u] != jr[u]) {
+            hs[u] = find_or_insert<LOG2T>(keys, vals, jr[u], ins);
+            if (hs[u] < 0) bad = 1;
           }
         }
+        T old[QM];
+#pragma unroll
+        for (int u = 0; u < QM; ++u) old[u] = hs[u] >= 0 ? vals[hs[u]] : T(0);
+#pragma unroll
+        for (int u = 0; u < QM; ++u)
+          if (hs[u] >= 0) vals[hs[u]] = fmadd(a, vr[u], old[u]);
         for (int q = lane + 32 * QM; q < nb; q += 32) {  // rows longer than 32*QM
           const int j = __ldg(B.idx + (size_t)k * B.w + q);
           if ((unsigned)j >= (unsigned)ncol) continue;
@@ -252,7 +287,7 @@ __global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32)
     }
     if (aborted) {
       if (lane == 0) {
-        const int p = atomicAdd(&ctl->n_fallback, 1);
+        const int p = atomicAdd(fb_count, 1);
         fb_list[p] = r;
       }
       continue;
@@ -311,11 +346,12 @@ template <typename T>
 __global__ void __launch_bounds__(kDenseThreads)
     spgemm_dense_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
                         int use_add, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
-                        const int *__restrict__ fb_list, T *__restrict__ acc_all, int *__restrict__ mark_all) {
+                        const int *__restrict__ fb_list, const int *__restrict__ fb_count, T *__restrict__ acc_all,
+                        int *__restrict__ mark_all) {
   __shared__ int s_warp[kDenseThreads / 32];
   __shared__ double s_d[kDenseThreads / 32], s_f[kDenseThreads / 32];
   const int n = A.n;
-  const int nfb = *((volatile int *)&ctl->n_fallback);
+  const int nfb = *((volatile const int *)fb_count);
   T *acc = acc_all + (size_t)blockIdx.x * n;
   int *mark = mark_all + (size_t)blockIdx.x * n;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -332,20 +368,23 @@ __global__ void __launch_bounds__(kDenseThreads)
       }
     }
     __syncthreads();
+    // one k at a time in A's row order: the columns of B_k are distinct, so the CTA's
+    // threads update distinct accumulators; the barrier orders the steps (deterministic)
     const int na = min(A.nnz[r], A.w);
-    for (int t = wid; t < na; t += nwarp) {
+    for (int t = 0; t < na; ++t) {
       const int k = A.idx[(size_t)r * A.w + t];
-      if ((unsigned)k >= (unsigned)B.n) continue;
-      const T a = alpha * A.val[(size_t)r * A.w + t];
-      const int nb = min(B.nnz[k], B.w);
-      for (int s = lane; s < nb; s += 32) {
-        const int j = B.idx[(size_t)k * B.w + s];
-        if ((unsigned)j >= (unsigned)n) continue;
-        mark[j] = 1;
-        atomicAdd(acc + j, a * B.val[(size_t)k * B.w + s]);
+      if ((unsigned)k < (unsigned)B.n) {
+        const T a = alpha * A.val[(size_t)r * A.w + t];
+        const int nb = min(B.nnz[k], B.w);
+        for (int s = threadIdx.x; s < nb; s += blockDim.x) {
+          const int j = B.idx[(size_t)k * B.w + s];
+          if ((unsigned)j >= (unsigned)n) continue;
+          mark[j] = 1;
+          acc[j] = fmadd(a, B.val[(size_t)k * B.w + s], acc[j]);
+        }
       }
+      __syncthreads();
     }
-    __syncthreads();
     int base = 0;
     double d = 0.0, f = 0.0;
     for (int c0 = 0; c0 < n; c0 += blockDim.x) {
@@ -539,55 +578,64 @@ int set_smem(K kernel, int bytes) {
   return SP2_OK;
 }
 
+// Launches the hash kernel over all rows (row_list == nullptr) or over a device-side list.
 template <typename T, int LOG2T, int QM>
-int launch_hash(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, cudaStream_t s) {
+int launch_hash(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, const int *row_list, const int *row_count,
+                int *fb, int *fb_count, cudaStream_t s) {
   using Cfg = HashCfg<T, LOG2T>;
   auto kern = spgemm_hash_kernel<T, LOG2T, QM>;
   static bool attr_set[64] = {false};
+  static int occ_cache[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!attr_set[dev]) {
     SP2_TRY(set_smem(kern, Cfg::SMEM));
+    int occ = 0;
+    SP2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Cfg::WARPS * 32, Cfg::SMEM));
+    occ_cache[dev] = occ < 1 ? 1 : occ;
     attr_set[dev] = true;
   }
-  const int n = a.A->n;
-  long long blocks = ((long long)n + Cfg::WARPS - 1) / Cfg::WARPS;
-  int occ = 0;
-  SP2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Cfg::WARPS * 32, Cfg::SMEM));
-  if (occ < 1) occ = 1;
-  long long cap = (long long)num_sms() * occ;
+  const long long cap = (long long)num_sms() * occ_cache[dev];
+  long long blocks = row_list ? cap : ((long long)a.A->n + Cfg::WARPS - 1) / Cfg::WARPS;
   int grid = (int)(blocks < cap ? blocks : cap);
   if (grid < 1) grid = 1;
   const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
-  prof_begin(SP2_PROF_SPGEMM, s);
+  const int cls = row_list ? SP2_PROF_LARGE : SP2_PROF_SPGEMM;
+  prof_begin(cls, s);
   kern<<<grid, Cfg::WARPS * 32, Cfg::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
                                                (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, rowstat,
-                                               ctl, fb);
+                                               ctl, row_list, row_count, fb, fb_count);
   note_launch();
-  prof_end(SP2_PROF_SPGEMM, s);
+  prof_end(cls, s);
   SP2_CUDA(cudaGetLastError());
   return SP2_OK;
+}
+
+template <typename T, int QM>
+int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb1, int *fb2, int lg, cudaStream_t s) {
+  // bin 0: every row, warp-private table of 2^lg slots
+  int rc = lg == 10 ? launch_hash<T, 10, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s)
+         : lg == 12 ? launch_hash<T, 12, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s)
+                    : launch_hash<T, 11, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s);
+  // bin 1: the deferred rows, one warp per CTA with a 2^14-slot table
+  if (rc == SP2_OK)
+    rc = launch_hash<T, 14, QM>(a, rowstat, ctl, fb1, &ctl->n_fallback, fb2, &ctl->n_fallback2, s);
+  return rc;
 }
 
 template <typename T>
 int multiply_t(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStream_t s) {
   const int n = a.A->n;
   int *fb = nullptr;
-  SP2_TRY(dev_alloc((void **)&fb, sizeof(int) * (size_t)n, s));
-  int qm_need = (a.B->width + 31) / 32;
-  int lg = a.table_log2;
-  if (lg == 0) lg = 10;
-  if (lg < 9) lg = 9;
-  if (lg > 11) lg = 11;
-  int rc;
-  if (qm_need <= 4) {
-    rc = lg == 9 ? launch_hash<T, 9, 4>(a, rowstat, ctl, fb, s)
-                 : lg == 10 ? launch_hash<T, 10, 4>(a, rowstat, ctl, fb, s) : launch_hash<T, 11, 4>(a, rowstat, ctl, fb, s);
-  } else {
-    rc = lg == 9 ? launch_hash<T, 9, 8>(a, rowstat, ctl, fb, s)
-                 : lg == 10 ? launch_hash<T, 10, 8>(a, rowstat, ctl, fb, s) : launch_hash<T, 11, 8>(a, rowstat, ctl, fb, s);
-  }
+  SP2_TRY(dev_alloc((void **)&fb, 2 * sizeof(int) * (size_t)n, s));
+  int *fb1 = fb, *fb2 = fb + n;
+  const int qm_need = (a.B->width + 31) / 32;
+  const int lg = a.table_log2 == 0 ? 11 : a.table_log2;
+  int rc = qm_need <= 4 ? launch_bins<T, 4>(a, rowstat, ctl, fb1, fb2, lg, s)
+                        : launch_bins<T, 8>(a, rowstat, ctl, fb1, fb2, lg, s);
   if (rc == SP2_OK) {
+    // bin 2: rows beyond the largest table, dense global-memory rows
     void *acc = nullptr;
     int *mark = nullptr;
     int slots = kFallbackSlots;
@@ -595,12 +643,10 @@ int multiply_t(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStre
     rc = fallback_scratch(n, a.A->dtype, slots, &acc, &mark, s);
     if (rc == SP2_OK) {
       const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
-      prof_begin(SP2_PROF_LARGE, s);
       spgemm_dense_kernel<T><<<slots, kDenseThreads, 0, s>>>(
           view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha, (T)a.beta, (T)a.tau,
-          a.Add != nullptr && a.beta != 0.0, rowstat, ctl, fb, (T *)acc, mark);
+          a.Add != nullptr && a.beta != 0.0, rowstat, ctl, fb2, &ctl->n_fallback2, (T *)acc, mark);
       note_launch();
-      prof_end(SP2_PROF_LARGE, s);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) rc = cuda_fail(e, "spgemm_dense_kernel", __FILE__, __LINE__);
     }

@@ -145,7 +145,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   int tail_left = opt.n_fp64_tail;
   bool armed = false;
   int it = 0;
-  int status = 2;
+  int status = 0;  // set when the loop stops: 0 err < tol, 1 stall rule, 2 max_iter
   int last_count = res.max_nnz;
   for (;;) {
     if (res.nonfinite) return fail(SP2E_NONFINITE, "sp2_purify: non-finite trace at iteration %d", it);
@@ -168,8 +168,8 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
       bool main_done = false;
       if (fp32) {
         // FP32 loop: leave at switch_tol, at an FP32 stall, or at max_iter
-        if (err < switch_tol || stalled || it >= opt.max_iter) main_done = true;
-        if (it >= opt.max_iter) status = 2;
+        if (err < switch_tol || stalled) main_done = true;
+        else if (it >= opt.max_iter) { main_done = true; status = 2; }
       } else {
         if (err < tol) { main_done = true; status = 0; }
         else if (opt.stall_rule && stalled) { main_done = true; status = 1; }

@@ -39,10 +39,6 @@ __device__ __forceinline__ float absval(float x) { return fabsf(x); }
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
 
-template <typename T>
-__device__ __forceinline__ bool keep_value(T v, T tau) {
-  return tau == T(0) || absval(v) > tau;
-}
 
 // Slot layout: columns are taken in groups of 32 (j >> 5).  A group g owns the aligned
 // block base(g) = 32 * h1(g) and column j first tries slot base(g) + (j & 31), so the
@@ -104,26 +100,36 @@ __device__ __forceinline__ void load_brow(const EllView<T> &B, int k, int nb, in
   }
 }
 
+// Drop rule |v| > tau evaluated on the bit patterns: for IEEE values with the sign bit
+// cleared the integer order is the numeric order, so the test runs on the integer pipe
+// (the FP64 pipe of this GPU is narrow).  A NaN compares above tau and is kept, so it
+// reaches the traces and is reported instead of vanishing.
+__device__ __forceinline__ long long mag_bits(double v) { return __double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFLL; }
+__device__ __forceinline__ int mag_bits(float v) { return __float_as_int(v) & 0x7FFFFFFF; }
+
+template <typename T>
+__device__ __forceinline__ bool keep_value(T v, T tau) {
+  return tau == T(0) || mag_bits(v) > mag_bits(tau);
+}
+
 // In-place compaction of the occupied, kept slots to the front of the table; returns
-// the kept count and accumulates the row's diagonal value and sum of squares.
+// the kept count.
 template <typename T, int TS>
-__device__ __forceinline__ int compact_table(int *keys, T *vals, int row, T tau, int lane, double &dsum,
-                                             double &fsum) {
+__device__ __forceinline__ int compact_table(int *keys, T *vals, T tau, int lane) {
   const unsigned lt = lanemask_lt();
+  const auto tb = mag_bits(tau);
+  const bool keep_all = tau == T(0);
   int nk = 0;
   for (int c = 0; c < TS; c += 32) {
     const int key = keys[c + lane];
     const T v = vals[c + lane];
-    const bool keep = key != kEmpty && keep_value(v, tau);
+    const bool keep = key != kEmpty && (keep_all || mag_bits(v) > tb);
     const unsigned m = __ballot_sync(kFull, keep);
     __syncwarp();
     if (keep) {
       const int pos = nk + __popc(m & lt);
       keys[pos] = key;
       vals[pos] = v;
-      const double dv = (double)v;
-      if (key == row) dsum += dv;
-      fsum += dv * dv;
     }
     nk += __popc(m);
   }
@@ -238,34 +244,48 @@ __global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32, 1)
         const T a = __shfl_sync(kFull, av, t);
         const int k = __shfl_sync(kFull, kk, t);
         const int nb = __shfl_sync(kFull, nbk, t);
+        const int nu = (nb + 31) >> 5;  // warp-uniform: register slots in use this step
         const int tn = t + 1 < cnt ? t + 1 : t;
         const int k1 = __shfl_sync(kFull, kk, tn);
         const int nb1 = (t + 1 < cnt) ? __shfl_sync(kFull, nbk, tn) : 0;
         int jn[QM];
         T vn[QM];
         load_brow<T, QM>(B, k1, nb1, lane, jn, vn);
-        // The QM columns a lane holds in this step are distinct, so their slots are too:
-        // probe all keys, resolve misses, load all values, then FMA and store -- QM
-        // independent chains instead of one serial chain.
-        int hs[QM], cur[QM];
+        // The QM columns a lane holds in this step are distinct, so their slots are too.
+        // Phase 1 probes every home slot; phase 2 accumulates the hits (loads first,
+        // then FMAs and stores: QM independent chains); phase 3 resolves the misses
+        // (inserts, displaced keys) of all slots in one loop instead of one per slot.
+        int hs[QM];
+        unsigned miss = 0;
 #pragma unroll
         for (int u = 0; u < QM; ++u) {
-          hs[u] = (unsigned)jr[u] < (unsigned)ncol ? hslot0<LOG2T>(jr[u]) : -1;
-          cur[u] = hs[u] >= 0 ? (int)((volatile int *)keys)[hs[u]] : (int)kEmpty;
-        }
-#pragma unroll
-        for (int u = 0; u < QM; ++u) {
-          if (hs[u] >= 0 && cur[u] != jr[u]) {
-            hs[u] = find_or_insert<LOG2T>(keys, vals, jr[u], ins);
-            if (hs[u] < 0) bad = 1;
+          hs[u] = -1;
+          if (u < nu) {
+            const bool valid = (unsigned)jr[u] < (unsigned)ncol;
+            const int h = hslot0<LOG2T>(jr[u]);
+            const int cur = valid ? (int)((volatile int *)keys)[h] : (int)kEmpty;
+            if (valid && cur == jr[u]) hs[u] = h;
+            if (valid && cur != jr[u]) miss |= 1u << u;
           }
         }
         T old[QM];
 #pragma unroll
-        for (int u = 0; u < QM; ++u) old[u] = hs[u] >= 0 ? vals[hs[u]] : T(0);
+        for (int u = 0; u < QM; ++u)
+          if (u < nu) old[u] = hs[u] >= 0 ? vals[hs[u]] : T(0);
 #pragma unroll
         for (int u = 0; u < QM; ++u)
-          if (hs[u] >= 0) vals[hs[u]] = fmadd(a, vr[u], old[u]);
+          if (u < nu && hs[u] >= 0) vals[hs[u]] = fmadd(a, vr[u], old[u]);
+        while (miss) {
+          const int u = __ffs(miss) - 1;
+          miss &= miss - 1;
+          int jj = jr[0];
+          T vv = vr[0];
+#pragma unroll
+          for (int w = 1; w < QM; ++w)
+            if (u == w) { jj = jr[w]; vv = vr[w]; }
+          const int h = find_or_insert<LOG2T>(keys, vals, jj, ins);
+          if (h >= 0) vals[h] = fmadd(a, vv, vals[h]); else bad = 1;
+        }
         for (int q = lane + 32 * QM; q < nb; q += 32) {  // rows longer than 32*QM
           const int j = __ldg(B.idx + (size_t)k * B.w + q);
           if ((unsigned)j >= (unsigned)ncol) continue;
@@ -292,24 +312,32 @@ __global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32, 1)
       }
       continue;
     }
-    double dsum = 0.0, fsum = 0.0;
-    const int nk = compact_table<T, TS>(keys, vals, r, tau, lane, dsum, fsum);
-    dsum = warp_sum(dsum);
-    fsum = warp_sum(fsum);
+    const int nk = compact_table<T, TS>(keys, vals, tau, lane);
     wmax = max(wmax, nk);
-    if (lane == 0) rowstat[r] = make_double2(dsum, fsum);
     if (nk > Out.w) {
       ++wover;
+      if (lane == 0) rowstat[r] = make_double2(0.0, 0.0);
       continue;
     }
     sort_prefix<T>(keys, vals, nk, lane);
     int *oi = Out.idx + (size_t)r * Out.w;
     T *ov = Out.val + (size_t)r * Out.w;
+    double dsum = 0.0, fsum = 0.0;
     for (int s = lane; s < nk; s += 32) {
-      oi[s] = keys[s];
-      ov[s] = vals[s];
+      const int key = keys[s];
+      const T v = vals[s];
+      oi[s] = key;
+      ov[s] = v;
+      const double dv = (double)v;
+      if (key == r) dsum += dv;
+      fsum = fma(dv, dv, fsum);
     }
-    if (lane == 0) Out.nnz[r] = nk;
+    dsum = warp_sum(dsum);
+    fsum = warp_sum(fsum);
+    if (lane == 0) {
+      Out.nnz[r] = nk;
+      rowstat[r] = make_double2(dsum, fsum);
+    }
     __syncwarp();
   }
   if (lane == 0) {
@@ -469,22 +497,30 @@ __global__ void __launch_bounds__(HashCfg<T, 11>::WARPS * 32)
       if (h >= 0) vals[h] = fmadd(beta, B.val[(size_t)r * B.w + s], vals[h]);
     }
     __syncwarp();
-    double dsum = 0.0, fsum = 0.0;
-    const int nk = compact_table<T, TS>(keys, vals, r, tau, lane, dsum, fsum);
-    dsum = warp_sum(dsum);
-    fsum = warp_sum(fsum);
+    const int nk = compact_table<T, TS>(keys, vals, tau, lane);
     wmax = max(wmax, nk);
-    if (lane == 0) rowstat[r] = make_double2(dsum, fsum);
     if (nk > A.w) {
       ++wover;
+      if (lane == 0) rowstat[r] = make_double2(0.0, 0.0);
       continue;
     }
     sort_prefix<T>(keys, vals, nk, lane);
+    double dsum = 0.0, fsum = 0.0;
     for (int s = lane; s < nk; s += 32) {
-      A.idx[(size_t)r * A.w + s] = keys[s];
-      A.val[(size_t)r * A.w + s] = vals[s];
+      const int key = keys[s];
+      const T v = vals[s];
+      A.idx[(size_t)r * A.w + s] = key;
+      A.val[(size_t)r * A.w + s] = v;
+      const double dv = (double)v;
+      if (key == r) dsum += dv;
+      fsum = fma(dv, dv, fsum);
     }
-    if (lane == 0) A.nnz[r] = nk;
+    dsum = warp_sum(dsum);
+    fsum = warp_sum(fsum);
+    if (lane == 0) {
+      A.nnz[r] = nk;
+      rowstat[r] = make_double2(dsum, fsum);
+    }
     __syncwarp();
   }
   if (lane == 0) {

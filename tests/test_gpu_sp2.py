@@ -68,13 +68,15 @@ def test_sp2_3d_gapped_f64_and_mixed(gpu):
     D64, s64 = S.sp2_purify(dev(S, H), n // 2, tol, S.sp2_options_default(tau=tau))
     assert s64["iterations"] == so["iterations"] and s64["branch"] == so["branch"]
     assert np.linalg.norm(dense_D(D64) - Dr) / np.sqrt(n) < 1e-10
-    Dm, sm = S.sp2_purify(dev(S, H), n // 2, tol, S.sp2_options_default(tau=tau, precision=S.SP2_PREC_MIXED))
+    Dm, sm = S.sp2_purify(dev(S, H), n // 2, tol, S.sp2_options_default(tau=tau, precision=S.SP2_PREC_MIXED),
+                          allow_notconv=True)
     Dmd = dense_D(Dm)
     dD = np.linalg.norm(Dmd - Dr) / np.sqrt(n)
     print("mixed: iterations %d (fp32 %d) status %s dD %.3e err %s; fp64: %d iterations, branches %s / %s" % (
         sm["iterations"], sm["fp32_iterations"], sm["status"], dD, ["%.2e" % e for e in sm["err"]],
         so["iterations"], "".join("2" if b == "2X-X2" else "1" for b in sm["branch"]),
         "".join("2" if b == "2X-X2" else "1" for b in so["branch"])))
+    assert sm["status"] in ("converged", "stalled")
     assert dD <= 1e-5
     assert sm["fp32_iterations"] >= 1 and sm["iterations"] - sm["fp32_iterations"] >= 2
     assert abs(np.trace(Dmd) - n // 2) < 1e-3

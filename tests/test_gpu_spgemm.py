@@ -107,6 +107,23 @@ def test_multiply_tight_binding_product(gpu):
     compare_spgemm(out2.to_numpy(), X1, X1, X1, -1.0, 2.0, 1e-6)
 
 
+def test_multiply_tight_binding_product_f32(gpu):
+    """FP32 values on the same realistic pattern, both branches of the SP2 update."""
+    S = gpu
+    n = 6000
+    H = ell(I.tight_binding(n, seed=4, delta=10.0))
+    lo, hi = O.gershgorin(H)
+    X0 = O.x0(H, lo, hi, 1e-5)
+    X1 = f32_input(O.spgemm(X0, X0, None, 1.0, 0.0, 1e-5))
+    for alpha, beta in ((1.0, 0.0), (-1.0, 2.0)):
+        ref = O.spgemm(X1, X1, X1 if beta else None, alpha, beta, 1e-5)
+        w = ((int(ref.nnz.max()) + 31) // 32) * 32
+        d1 = dev(S, X1, S.SP2_F32)
+        out = dev(S, X1, S.SP2_F32, width=w) if beta else S.Ellpack.empty(n, w, S.SP2_F32)
+        S.ellpack_multiply(d1, d1, out, alpha, beta, 1e-5)
+        compare_spgemm(out.to_numpy(), X1, X1, X1, alpha, beta, 1e-5, fp32=True)
+
+
 def test_multiply_is_deterministic(gpu):
     S = gpu
     n = 3000

@@ -323,6 +323,8 @@ extern "C" int sp2_step(const ellpack_t *X, ellpack_t *Xn, double nocc, double t
   info->nnz_total = res.nnz_total;
   info->max_row_nnz = res.max_nnz;
   info->required_width = res.max_count;
+  info->rows_deferred = res.n_fallback;
+  info->rows_dense = res.n_fallback2;
   if (res.overflow_rows > 0)
     return fail(SP2E_OVERFLOW, "sp2_step: %d row(s) need %d slots, Xn width is %d", res.overflow_rows, res.max_count,
                 Xn->width);

@@ -178,7 +178,7 @@ struct HashCfg {
   static constexpr int TS = 1 << LOG2T;
   static constexpr int LIMIT = TS - TS / 8;
   static constexpr int BYTES_PER_WARP = TS * (int)(sizeof(int) + sizeof(T));
-  static constexpr int WARPS_RAW = (229376 / BYTES_PER_WARP);
+  static constexpr int WARPS_RAW = (232192 / BYTES_PER_WARP);
   static constexpr int WARPS = WARPS_RAW > 16 ? 16 : (WARPS_RAW < 1 ? 1 : WARPS_RAW);
   static constexpr int SMEM = WARPS * BYTES_PER_WARP;
 };
@@ -337,6 +337,310 @@ __global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32, 1)
     if (lane == 0) {
       Out.nnz[r] = nk;
       rowstat[r] = make_double2(dsum, fsum);
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (wmax) atomicMax(&ctl->max_count, wmax);
+    if (wover) atomicAdd(&ctl->overflow_rows, wover);
+  }
+}
+
+// ------------------------------------------------------------------ block accumulator
+// First pass of the multiply.  Columns are taken in groups of GW = 2^GSH consecutive
+// indices.  Each group a row touches gets a dense block of GW accumulators in the warp's
+// shared memory; a small open-addressing table maps group -> block (entry = g << 8 | b).
+// The accumulator of column j is vals[b * GW + (j & (GW-1))]: no per-column key, no
+// probing, and the bank of a column is fixed by its low bits, so a warp holding a run of
+// consecutive columns touches distinct banks.  Untouched accumulators hold a signalling
+// NaN bit pattern (arithmetic never produces it), so "structural" means "touched".
+// Blocks are handed out by one elected lane per distinct new group.  The row comes out
+// sorted by walking the groups in ascending order: no sort of the entries is needed.
+template <typename T> struct BlockCfg;
+template <> struct BlockCfg<double> {
+  static constexpr int GSH = 4, NB = 224, LOG2G = 10;
+};
+template <> struct BlockCfg<float> {
+  static constexpr int GSH = 5, NB = 128, LOG2G = 9;
+};
+template <typename T>
+struct BlockGeo {
+  static constexpr int GSH = BlockCfg<T>::GSH, GW = 1 << GSH, NB = BlockCfg<T>::NB;
+  static constexpr int G = 1 << BlockCfg<T>::LOG2G;
+  static constexpr int VAL_BYTES = NB * GW * (int)sizeof(T);
+  static constexpr int BYTES_PER_WARP = VAL_BYTES + G * 4 + 16;
+  static constexpr int WARPS_RAW = 232192 / BYTES_PER_WARP;
+  static constexpr int WARPS = WARPS_RAW > 16 ? 16 : (WARPS_RAW < 1 ? 1 : WARPS_RAW);
+  static constexpr int SMEM = WARPS * BYTES_PER_WARP;
+  static constexpr unsigned MAX_GROUP = 1u << 24;  // g < 2^24 fits the packed entry
+};
+
+__device__ __forceinline__ bool is_untouched(double v) {
+  return __double_as_longlong(v) == (long long)0xFFF4A5A5A5A5A5A5ULL;
+}
+__device__ __forceinline__ bool is_untouched(float v) { return __float_as_uint(v) == 0xFFA5A5A5u; }
+template <typename T> __device__ __forceinline__ T untouched();
+template <> __device__ __forceinline__ double untouched<double>() { return __longlong_as_double((long long)0xFFF4A5A5A5A5A5A5ULL); }
+template <> __device__ __forceinline__ float untouched<float>() { return __uint_as_float(0xFFA5A5A5u); }
+
+template <int LOG2G>
+__device__ __forceinline__ int ghash(unsigned g) { return (int)((g * 0x9E3779B1u) >> (32 - LOG2G)); }
+
+// Group -> block, allocating (and clearing) a block when the group is new.  Called by
+// one lane per distinct group; returns the block or -1 when the blocks are used up.
+template <typename T>
+__device__ __forceinline__ int group_block(unsigned *gtab, T *vals, int *nblk, unsigned g) {
+  using Geo = BlockGeo<T>;
+  int h = ghash<BlockCfg<T>::LOG2G>(g);
+#pragma unroll 1
+  for (int p = 0; p < Geo::G; ++p) {
+    const unsigned e = ((volatile unsigned *)gtab)[h];
+    if (e != 0xFFFFFFFFu && (e >> 8) == g) {
+      __threadfence_block();  // pairs with the fence of the lane that cleared the block
+      return (int)(e & 0xFFu);
+    }
+    if (e == 0xFFFFFFFFu) {
+      const int b = atomicAdd(nblk, 1);
+      if (b >= Geo::NB) return -1;
+      T *blk = vals + (size_t)b * Geo::GW;
+#pragma unroll
+      for (int t = 0; t < Geo::GW; ++t) blk[t] = untouched<T>();
+      __threadfence_block();  // the cleared block is visible before the entry naming it
+      const unsigned old = atomicCAS(gtab + h, 0xFFFFFFFFu, (g << 8) | (unsigned)b);
+      if (old == 0xFFFFFFFFu) return b;
+      // the slot was claimed first by another group (this block stays unused) or by the
+      // same group from another lane (use that block); keep probing otherwise
+      if ((old >> 8) == g) {
+        __threadfence_block();
+        return (int)(old & 0xFFu);
+      }
+    }
+    h = (h + 1) & (Geo::G - 1);
+  }
+  return -1;
+}
+
+template <typename T, int QM>
+__global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
+    spgemm_block_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
+                        int use_add, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
+                        int *__restrict__ fb_list, int *__restrict__ fb_count) {
+  using Geo = BlockGeo<T>;
+  constexpr int GW = Geo::GW, GSH = Geo::GSH, G = Geo::G;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned char *base = smem + (size_t)wid * Geo::BYTES_PER_WARP;
+  T *vals = reinterpret_cast<T *>(base);
+  unsigned *gtab = reinterpret_cast<unsigned *>(base + Geo::VAL_BYTES);
+  int *nblk = reinterpret_cast<int *>(base + Geo::VAL_BYTES + G * 4);
+  const int ncol = Out.n;
+  const int nw = gridDim.x * Geo::WARPS;
+  const unsigned lt = lanemask_lt();
+  int wmax = 0, wover = 0;
+
+  for (int r = blockIdx.x * Geo::WARPS + wid; r < A.n; r += nw) {
+    for (int s = lane * 4; s < G; s += 128) *reinterpret_cast<uint4 *>(gtab + s) = make_uint4(~0u, ~0u, ~0u, ~0u);
+    if (lane == 0) *nblk = 0;
+    __syncwarp();
+    bool aborted = false;
+
+    // One step: accumulate a * (row `src` entries) into the blocks.  The addend row of
+    // C (beta) is step -1, then the rows of B for the entries of A's row.
+    const int na = min(A.nnz[r], A.w);
+    const int nc = use_add ? min(Add.nnz[r], Add.w) : 0;
+    const int nsteps = na + (use_add ? 1 : 0);
+    // register prefetch of the next step's row
+    auto step_row = [&](int t, const int *&ri, const T *&rv, int &nb, T &a) {
+      if (use_add && t == 0) {
+        ri = Add.idx + (size_t)r * Add.w;
+        rv = Add.val + (size_t)r * Add.w;
+        nb = nc;
+        a = beta;
+        return;
+      }
+      const int s = t - (use_add ? 1 : 0);
+      const int k = __ldg(A.idx + (size_t)r * A.w + s);
+      if ((unsigned)k < (unsigned)B.n) {
+        ri = B.idx + (size_t)k * B.w;
+        rv = B.val + (size_t)k * B.w;
+        nb = min(__ldg(B.nnz + k), B.w);
+        a = alpha * __ldg(A.val + (size_t)r * A.w + s);
+      } else {
+        ri = B.idx;
+        rv = B.val;
+        nb = 0;
+        a = T(0);
+      }
+    };
+    const int *ri = B.idx;
+    const T *rv = B.val;
+    int nb = 0;
+    T a = T(0);
+    if (nsteps > 0) step_row(0, ri, rv, nb, a);
+    int jr[QM];
+    T vr[QM];
+#pragma unroll
+    for (int u = 0; u < QM; ++u) {
+      const int q = lane + 32 * u;
+      jr[u] = q < nb ? __ldg(ri + q) : -1;
+      vr[u] = q < nb ? __ldg(rv + q) : T(0);
+    }
+    for (int t = 0; t < nsteps; ++t) {
+      const int nu = (nb + 31) >> 5;
+      const int *ri1 = ri;
+      const T *rv1 = rv;
+      int nb1 = 0;
+      T a1 = T(0);
+      if (t + 1 < nsteps) step_row(t + 1, ri1, rv1, nb1, a1);
+      int jn[QM];
+      T vn[QM];
+#pragma unroll
+      for (int u = 0; u < QM; ++u) {
+        const int q = lane + 32 * u;
+        jn[u] = q < nb1 ? __ldg(ri1 + q) : -1;
+        vn[u] = q < nb1 ? __ldg(rv1 + q) : T(0);
+      }
+      // phase A: group -> block for every held column
+      int bs[QM];
+      unsigned miss = 0;
+#pragma unroll
+      for (int u = 0; u < QM; ++u) {
+        bs[u] = -1;
+        if (u < nu && (unsigned)jr[u] < (unsigned)ncol) {
+          const unsigned g = (unsigned)jr[u] >> GSH;
+          const unsigned e = ((volatile unsigned *)gtab)[ghash<BlockCfg<T>::LOG2G>(g)];
+          if (e != 0xFFFFFFFFu && (e >> 8) == g) bs[u] = (int)(e & 0xFFu);
+          else miss |= 1u << u;
+        }
+      }
+      // misses: one elected lane per distinct group finds or allocates its block
+      while (__any_sync(kFull, miss != 0)) {
+        const int u = miss ? __ffs(miss) - 1 : -1;
+        int jj = jr[0];
+#pragma unroll
+        for (int w = 1; w < QM; ++w)
+          if (u == w) jj = jr[w];
+        const unsigned act = __ballot_sync(kFull, u >= 0);
+        if (u >= 0) {
+          const unsigned g = (unsigned)jj >> GSH;
+          const unsigned peers = __match_any_sync(act, g);
+          const int leader = __ffs(peers) - 1;
+          int b = -1;
+          if (lane == leader) b = g < Geo::MAX_GROUP ? group_block<T>(gtab, vals, nblk, g) : -1;
+          b = __shfl_sync(peers, b, leader);
+#pragma unroll
+          for (int w = 0; w < QM; ++w)
+            if (u == w) bs[w] = b;
+          if (b < 0) aborted = true;
+          miss &= miss - 1;
+        }
+      }
+      __syncwarp();
+      // phase B: accumulate (loads first, then FMAs and stores: QM independent chains)
+      T old[QM];
+#pragma unroll
+      for (int u = 0; u < QM; ++u)
+        if (u < nu) old[u] = bs[u] >= 0 ? vals[bs[u] * GW + (jr[u] & (GW - 1))] : T(0);
+#pragma unroll
+      for (int u = 0; u < QM; ++u)
+        if (u < nu && bs[u] >= 0) {
+          const T o = is_untouched(old[u]) ? T(0) : old[u];
+          vals[bs[u] * GW + (jr[u] & (GW - 1))] = fmadd(a, vr[u], o);
+        }
+      // entries beyond 32*QM (rows longer than the register prefetch)
+      for (int q = lane + 32 * QM; q < nb; q += 32) {
+        const int j = __ldg(ri + q);
+        if ((unsigned)j >= (unsigned)ncol) continue;
+        const unsigned g = (unsigned)j >> GSH;
+        int b = -1;
+        // serial per lane: distinct columns, but a new group may race with another lane;
+        // group_block's CAS keeps one block per group
+        b = g < Geo::MAX_GROUP ? group_block<T>(gtab, vals, nblk, g) : -1;
+        if (b < 0) { aborted = true; continue; }
+        T *slot = vals + b * GW + (j & (GW - 1));
+        const T o = is_untouched(*slot) ? T(0) : *slot;
+        *slot = fmadd(a, __ldg(rv + q), o);
+      }
+      __syncwarp();
+      aborted = __any_sync(kFull, aborted);
+      if (aborted) break;
+      ri = ri1; rv = rv1; nb = nb1; a = a1;
+#pragma unroll
+      for (int u = 0; u < QM; ++u) { jr[u] = jn[u]; vr[u] = vn[u]; }
+    }
+    if (aborted) {
+      if (lane == 0) {
+        const int p = atomicAdd(fb_count, 1);
+        fb_list[p] = r;
+      }
+      continue;
+    }
+    // compact the used group entries to the front of the table, sort them by group
+    int ng = 0;
+    for (int c = 0; c < G; c += 32) {
+      const unsigned e = gtab[c + lane];
+      const bool used = e != 0xFFFFFFFFu;
+      const unsigned m = __ballot_sync(kFull, used);
+      __syncwarp();
+      if (used) gtab[ng + __popc(m & lt)] = e;
+      ng += __popc(m);
+    }
+    {
+      int P = 32;
+      while (P < ng) P <<= 1;
+      for (int s = ng + lane; s < P; s += 32) gtab[s] = 0xFFFFFFFFu;
+      __syncwarp();
+      for (int k = 2; k <= P; k <<= 1)
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+          for (int e = lane; e < (P >> 1); e += 32) {
+            const int i = ((e & ~(jj - 1)) << 1) | (e & (jj - 1));
+            const unsigned x = gtab[i], y = gtab[i + jj];
+            if ((x > y) == ((i & k) == 0)) { gtab[i] = y; gtab[i + jj] = x; }
+          }
+          __syncwarp();
+        }
+    }
+    // walk the groups in column order: 32 / GW groups per warp pass, lane -> column
+    const auto tb = mag_bits(tau);
+    const bool keep_all = tau == T(0);
+    int nk = 0;
+    double dsum = 0.0, fsum = 0.0;
+    int *oi = Out.idx + (size_t)r * Out.w;
+    T *ov = Out.val + (size_t)r * Out.w;
+    constexpr int GPP = 32 / GW;  // groups per pass
+    for (int c = 0; c < ng; c += GPP) {
+      const int gi = c + lane / GW;
+      bool keep = false;
+      int j = 0;
+      T v = T(0);
+      if (gi < ng) {
+        const unsigned e = gtab[gi];
+        const int b = (int)(e & 0xFFu);
+        j = (int)((e >> 8) << GSH) + (lane & (GW - 1));
+        v = vals[b * GW + (lane & (GW - 1))];
+        keep = !is_untouched(v) && (keep_all || mag_bits(v) > tb);
+      }
+      const unsigned m = __ballot_sync(kFull, keep);
+      if (keep) {
+        const int pos = nk + __popc(m & lt);
+        if (pos < Out.w) { oi[pos] = j; ov[pos] = v; }
+        const double dv = (double)v;
+        if (j == r) dsum += dv;
+        fsum = fma(dv, dv, fsum);
+      }
+      nk += __popc(m);
+    }
+    dsum = warp_sum(dsum);
+    fsum = warp_sum(fsum);
+    wmax = max(wmax, nk);
+    if (lane == 0) {
+      if (nk > Out.w) {
+        ++wover;
+        rowstat[r] = make_double2(0.0, 0.0);
+      } else {
+        Out.nnz[r] = nk;
+        rowstat[r] = make_double2(dsum, fsum);
+      }
     }
     __syncwarp();
   }
@@ -649,9 +953,42 @@ int launch_hash(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, const i
 }
 
 template <typename T, int QM>
+int launch_block(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
+  using Geo = BlockGeo<T>;
+  auto kern = spgemm_block_kernel<T, QM>;
+  static bool attr_set[64] = {false};
+  static int occ_cache[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!attr_set[dev]) {
+    SP2_TRY(set_smem(kern, Geo::SMEM));
+    int occ = 0;
+    SP2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Geo::WARPS * 32, Geo::SMEM));
+    occ_cache[dev] = occ < 1 ? 1 : occ;
+    attr_set[dev] = true;
+  }
+  const long long cap = (long long)num_sms() * occ_cache[dev];
+  const long long blocks = ((long long)a.A->n + Geo::WARPS - 1) / Geo::WARPS;
+  int grid = (int)(blocks < cap ? blocks : cap);
+  if (grid < 1) grid = 1;
+  const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
+  prof_begin(SP2_PROF_SPGEMM, s);
+  kern<<<grid, Geo::WARPS * 32, Geo::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
+                                               (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, rowstat,
+                                               ctl, fb, fb_count);
+  note_launch();
+  prof_end(SP2_PROF_SPGEMM, s);
+  SP2_CUDA(cudaGetLastError());
+  return SP2_OK;
+}
+
+template <typename T, int QM>
 int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb1, int *fb2, int lg, cudaStream_t s) {
-  // bin 0: every row, warp-private table of 2^lg slots
-  int rc = lg == 10 ? launch_hash<T, 10, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s)
+  // bin 0: every row; the block accumulator by default, or a warp-private hash table
+  // of 2^lg slots when lg is given
+  int rc = lg == 0  ? launch_block<T, QM>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
+         : lg == 10 ? launch_hash<T, 10, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s)
          : lg == 12 ? launch_hash<T, 12, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s)
                     : launch_hash<T, 11, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s);
   // bin 1: the deferred rows, one warp per CTA with a 2^14-slot table
@@ -667,7 +1004,7 @@ int multiply_t(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStre
   SP2_TRY(dev_alloc((void **)&fb, 2 * sizeof(int) * (size_t)n, s));
   int *fb1 = fb, *fb2 = fb + n;
   const int qm_need = (a.B->width + 31) / 32;
-  const int lg = a.table_log2 == 0 ? 11 : a.table_log2;
+  const int lg = a.table_log2;
   int rc = qm_need <= 4 ? launch_bins<T, 4>(a, rowstat, ctl, fb1, fb2, lg, s)
                         : launch_bins<T, 8>(a, rowstat, ctl, fb1, fb2, lg, s);
   if (rc == SP2_OK) {

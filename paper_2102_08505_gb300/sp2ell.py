@@ -54,7 +54,8 @@ class sp2_step_info(ctypes.Structure):
     _fields_ = [("trX", ctypes.c_double), ("trX2", ctypes.c_double), ("have_traces", ctypes.c_int32),
                 ("branch", ctypes.c_int32), ("err", ctypes.c_double), ("trXn", ctypes.c_double),
                 ("trXn2", ctypes.c_double), ("nnz_total", ctypes.c_int64), ("max_row_nnz", ctypes.c_int32),
-                ("required_width", ctypes.c_int32), ("table_log2", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("required_width", ctypes.c_int32), ("table_log2", ctypes.c_int32),
+                ("rows_deferred", ctypes.c_int32), ("rows_dense", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 SP2_PROF_CLASSES = 4

@@ -262,3 +262,60 @@ def test_x0(gpu, tau):
     for i in range(n):
         assert np.array_equal(gi[i, :gn[i]], ref.row(i)[0])
         assert np.allclose(gv[i, :gn[i]], ref.row(i)[1], rtol=5e-16, atol=1e-300)
+
+
+@pytest.mark.parametrize("first_pass", [0, 11])
+@pytest.mark.parametrize("fp32", [False, True])
+def test_first_pass_variants(gpu, first_pass, fp32):
+    """Both first-pass accumulators (column blocks, per-warp hash table) on one SP2 step of
+    a gapped tight-binding X."""
+    S = gpu
+    n = 5000
+    H = ell(I.tight_binding(n, seed=6, delta=10.0))
+    lo, hi = O.gershgorin(H)
+    X0 = O.x0(H, lo, hi, 1e-5)
+    X1 = O.spgemm(X0, X0, None, 1.0, 0.0, 1e-5)
+    if fp32:
+        X1 = f32_input(X1)
+    dt = S.SP2_F32 if fp32 else S.SP2_F64
+    d1 = dev(S, X1, dt)
+    probe = S.Ellpack.empty(n, 32, dt)
+    rc, info = S.sp2_step(d1, probe, n / 2, 1e-5, table_log2=first_pass, raise_on_overflow=False)
+    out = S.Ellpack.empty(n, ((info.required_width + 31) // 32) * 32, dt)
+    info = S.sp2_step(d1, out, n / 2, 1e-5, table_log2=first_pass)
+    up = info.branch == 2
+    compare_spgemm(out.to_numpy(), X1, X1, X1, -1.0 if up else 1.0, 2.0 if up else 0.0, 1e-5, fp32=fp32)
+    assert info.rows_deferred == 0
+
+
+def hub_matrix(n, hubs, hub_nnz, other_nnz, seed):
+    rng = np.random.default_rng(seed)
+    rows, cols = [], []
+    for i in range(n):
+        k = hub_nnz if i in hubs else other_nnz
+        c = rng.choice(n, size=k, replace=False)
+        rows.append(np.full(k, i))
+        cols.append(c)
+    rows, cols = np.concatenate(rows), np.concatenate(cols)
+    vals = rng.uniform(-1.0, 1.0, len(rows)) * 0.05
+    return O.Ell(*I.coo_to_ellpack(n, rows, cols, vals))
+
+
+def test_all_three_passes(gpu):
+    """Rows with more column groups than the block accumulator holds go to the 2^14-slot
+    table; rows with more distinct columns than that go to the dense global-row pass.
+    Sampled rows (all hubs included) against the oracle."""
+    S = gpu
+    n = 20000
+    hubs = set(range(0, n, 2000)) | {n - 1}
+    X = hub_matrix(n, hubs, 1000, 40, seed=3)
+    dX = dev(S, X)
+    probe = S.Ellpack.empty(n, 32)
+    rc, info = S.sp2_step(dX, probe, n / 2, 0.0, raise_on_overflow=False)
+    out = S.Ellpack.empty(n, ((info.required_width + 31) // 32) * 32)
+    info = S.sp2_step(dX, out, n / 2, 0.0)
+    assert info.rows_deferred > len(hubs) and info.rows_dense >= len(hubs)
+    up = info.branch == 2
+    rng = np.random.default_rng(4)
+    rows = np.unique(np.concatenate([sorted(hubs), rng.choice(n, 300, replace=False)]))
+    compare_spgemm(out.to_numpy(), X, X, X, -1.0 if up else 1.0, 2.0 if up else 0.0, 0.0, rows=rows)

@@ -444,63 +444,57 @@ __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
     __syncwarp();
     bool aborted = false;
 
-    // One step: accumulate a * (row `src` entries) into the blocks.  The addend row of
-    // C (beta) is step -1, then the rows of B for the entries of A's row.
+    // Step = accumulate a * (one source row) into the blocks: first the row of the
+    // addend C (a = beta), then row k of B for each entry a_ik of A's row (a = alpha*a_ik).
+    // A's entries and nnz(B_k) are loaded 32 steps at a time, one chunk ahead; each B row
+    // is loaded into registers two steps before it is consumed (three buffers rotate).
     const int na = min(A.nnz[r], A.w);
-    const int nc = use_add ? min(Add.nnz[r], Add.w) : 0;
-    const int nsteps = na + (use_add ? 1 : 0);
-    // register prefetch of the next step's row
-    auto step_row = [&](int t, const int *&ri, const T *&rv, int &nb, T &a) {
-      if (use_add && t == 0) {
-        ri = Add.idx + (size_t)r * Add.w;
-        rv = Add.val + (size_t)r * Add.w;
-        nb = nc;
-        a = beta;
-        return;
-      }
-      const int s = t - (use_add ? 1 : 0);
-      const int k = __ldg(A.idx + (size_t)r * A.w + s);
-      if ((unsigned)k < (unsigned)B.n) {
-        ri = B.idx + (size_t)k * B.w;
-        rv = B.val + (size_t)k * B.w;
-        nb = min(__ldg(B.nnz + k), B.w);
-        a = alpha * __ldg(A.val + (size_t)r * A.w + s);
-      } else {
-        ri = B.idx;
-        rv = B.val;
-        nb = 0;
-        a = T(0);
+    const int *arow_i = A.idx + (size_t)r * A.w;
+    const T *arow_v = A.val + (size_t)r * A.w;
+    int ck, cnb, nk_, nnb;
+    T ca, na_;
+    auto load_chunk = [&](int base, int &kk, int &nbk, T &av) {
+      const int s = base + lane;
+      kk = 0; nbk = 0; av = T(0);
+      if (s < na) {
+        const int k = __ldg(arow_i + s);
+        if ((unsigned)k < (unsigned)B.n) {
+          kk = k;
+          av = alpha * __ldg(arow_v + s);
+          nbk = min(__ldg(B.nnz + k), B.w);
+        }
       }
     };
-    const int *ri = B.idx;
-    const T *rv = B.val;
-    int nb = 0;
-    T a = T(0);
-    if (nsteps > 0) step_row(0, ri, rv, nb, a);
-    int jr[QM];
-    T vr[QM];
-#pragma unroll
-    for (int u = 0; u < QM; ++u) {
-      const int q = lane + 32 * u;
-      jr[u] = q < nb ? __ldg(ri + q) : -1;
-      vr[u] = q < nb ? __ldg(rv + q) : T(0);
-    }
-    for (int t = 0; t < nsteps; ++t) {
-      const int nu = (nb + 31) >> 5;
-      const int *ri1 = ri;
-      const T *rv1 = rv;
-      int nb1 = 0;
-      T a1 = T(0);
-      if (t + 1 < nsteps) step_row(t + 1, ri1, rv1, nb1, a1);
-      int jn[QM];
-      T vn[QM];
+    load_chunk(0, ck, cnb, ca);
+    load_chunk(32, nk_, nnb, na_);
+    int cbase = 0;
+    // (k, nb, a) of step t, t in [cbase, cbase + 64)
+    auto info = [&](int t, int &k, int &nb, T &a) {
+      if (t < cbase + 32) {
+        k = __shfl_sync(kFull, ck, t & 31);
+        nb = __shfl_sync(kFull, cnb, t & 31);
+        a = __shfl_sync(kFull, ca, t & 31);
+      } else {
+        k = __shfl_sync(kFull, nk_, t & 31);
+        nb = __shfl_sync(kFull, nnb, t & 31);
+        a = __shfl_sync(kFull, na_, t & 31);
+      }
+    };
+    auto fetch = [&](const int *ri, const T *rv, int nb, int (&jr)[QM], T (&vr)[QM]) {
 #pragma unroll
       for (int u = 0; u < QM; ++u) {
         const int q = lane + 32 * u;
-        jn[u] = q < nb1 ? __ldg(ri1 + q) : -1;
-        vn[u] = q < nb1 ? __ldg(rv1 + q) : T(0);
+        jr[u] = q < nb ? __ldg(ri + q) : -1;
+        vr[u] = q < nb ? __ldg(rv + q) : T(0);
       }
-      // phase A: group -> block for every held column
+    };
+    auto fetch_step = [&](int t, int (&jr)[QM], T (&vr)[QM], int &nb, T &a, int &k) {
+      info(t, k, nb, a);
+      fetch(B.idx + (size_t)k * B.w, B.val + (size_t)k * B.w, nb, jr, vr);
+    };
+    // accumulate one step from registers (+ the entries beyond 32*QM from memory)
+    auto step = [&](const int (&jr)[QM], const T (&vr)[QM], int nb, T a, const int *ri, const T *rv) {
+      const int nu = (nb + 31) >> 5;
       int bs[QM];
       unsigned miss = 0;
 #pragma unroll
@@ -536,7 +530,6 @@ __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
         }
       }
       __syncwarp();
-      // phase B: accumulate (loads first, then FMAs and stores: QM independent chains)
       T old[QM];
 #pragma unroll
       for (int u = 0; u < QM; ++u)
@@ -547,15 +540,11 @@ __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
           const T o = is_untouched(old[u]) ? T(0) : old[u];
           vals[bs[u] * GW + (jr[u] & (GW - 1))] = fmadd(a, vr[u], o);
         }
-      // entries beyond 32*QM (rows longer than the register prefetch)
-      for (int q = lane + 32 * QM; q < nb; q += 32) {
+      for (int q = lane + 32 * QM; q < nb; q += 32) {  // rows longer than the registers
         const int j = __ldg(ri + q);
         if ((unsigned)j >= (unsigned)ncol) continue;
         const unsigned g = (unsigned)j >> GSH;
-        int b = -1;
-        // serial per lane: distinct columns, but a new group may race with another lane;
-        // group_block's CAS keeps one block per group
-        b = g < Geo::MAX_GROUP ? group_block<T>(gtab, vals, nblk, g) : -1;
+        const int b = g < Geo::MAX_GROUP ? group_block<T>(gtab, vals, nblk, g) : -1;
         if (b < 0) { aborted = true; continue; }
         T *slot = vals + b * GW + (j & (GW - 1));
         const T o = is_untouched(*slot) ? T(0) : *slot;
@@ -563,10 +552,38 @@ __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
       }
       __syncwarp();
       aborted = __any_sync(kFull, aborted);
-      if (aborted) break;
-      ri = ri1; rv = rv1; nb = nb1; a = a1;
-#pragma unroll
-      for (int u = 0; u < QM; ++u) { jr[u] = jn[u]; vr[u] = vn[u]; }
+    };
+
+    int j0[QM], j1[QM], j2[QM];
+    T v0[QM], v1[QM], v2[QM];
+    int nb0 = 0, nb1 = 0, nb2 = 0, k0 = 0, k1 = 0, k2 = 0;
+    T a0 = T(0), a1 = T(0), a2 = T(0);
+    if (use_add) {
+      const int nc = min(Add.nnz[r], Add.w);
+      const int *ci = Add.idx + (size_t)r * Add.w;
+      const T *cv = Add.val + (size_t)r * Add.w;
+      fetch(ci, cv, nc, j2, v2);
+      if (na > 0) fetch_step(0, j0, v0, nb0, a0, k0);
+      if (na > 1) fetch_step(1, j1, v1, nb1, a1, k1);
+      step(j2, v2, nc, beta, ci, cv);
+    } else {
+      if (na > 0) fetch_step(0, j0, v0, nb0, a0, k0);
+      if (na > 1) fetch_step(1, j1, v1, nb1, a1, k1);
+    }
+    for (int t = 0; t < na && !aborted; t += 3) {
+      if (t >= cbase + 32) {  // next chunk of A's entries becomes current
+        ck = nk_; cnb = nnb; ca = na_;
+        cbase += 32;
+        load_chunk(cbase + 32, nk_, nnb, na_);
+      }
+      if (t + 2 < na) fetch_step(t + 2, j2, v2, nb2, a2, k2);
+      step(j0, v0, nb0, a0, B.idx + (size_t)k0 * B.w, B.val + (size_t)k0 * B.w);
+      if (t + 1 >= na || aborted) break;
+      if (t + 3 < na) fetch_step(t + 3, j0, v0, nb0, a0, k0);
+      step(j1, v1, nb1, a1, B.idx + (size_t)k1 * B.w, B.val + (size_t)k1 * B.w);
+      if (t + 2 >= na || aborted) break;
+      if (t + 4 < na) fetch_step(t + 4, j1, v1, nb1, a1, k1);
+      step(j2, v2, nb2, a2, B.idx + (size_t)k2 * B.w, B.val + (size_t)k2 * B.w);
     }
     if (aborted) {
       if (lane == 0) {

@@ -21,6 +21,8 @@
 #include <limits.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace sp2 {
@@ -372,7 +374,8 @@ struct BlockGeo {
   static constexpr int WARPS_RAW = 232192 / BYTES_PER_WARP;
   static constexpr int WARPS = WARPS_RAW > 16 ? 16 : (WARPS_RAW < 1 ? 1 : WARPS_RAW);
   static constexpr int SMEM = WARPS * BYTES_PER_WARP;
-  static constexpr unsigned MAX_GROUP = 1u << 24;  // g < 2^24 fits the packed entry
+  // g < 2^24 - 1 fits the packed entry and never matches the empty entry 0xFFFFFFFF
+  static constexpr unsigned MAX_GROUP = (1u << 24) - 1u;
 };
 
 __device__ __forceinline__ bool is_untouched(double v) {
@@ -388,7 +391,7 @@ __device__ __forceinline__ int ghash(unsigned g) { return (int)((g * 0x9E3779B1u
 
 // Group -> block, allocating (and clearing) a block when the group is new.  Called by
 // one lane per distinct group; returns the block or -1 when the blocks are used up.
-template <typename T>
+template <typename T, bool KEEPZ>
 __device__ __forceinline__ int group_block(unsigned *gtab, T *vals, int *nblk, unsigned g) {
   using Geo = BlockGeo<T>;
   int h = ghash<BlockCfg<T>::LOG2G>(g);
@@ -404,7 +407,7 @@ __device__ __forceinline__ int group_block(unsigned *gtab, T *vals, int *nblk, u
       if (b >= Geo::NB) return -1;
       T *blk = vals + (size_t)b * Geo::GW;
 #pragma unroll
-      for (int t = 0; t < Geo::GW; ++t) blk[t] = untouched<T>();
+      for (int t = 0; t < Geo::GW; ++t) blk[t] = KEEPZ ? untouched<T>() : T(0);
       __threadfence_block();  // the cleared block is visible before the entry naming it
       const unsigned old = atomicCAS(gtab + h, 0xFFFFFFFFu, (g << 8) | (unsigned)b);
       if (old == 0xFFFFFFFFu) return b;
@@ -420,7 +423,7 @@ __device__ __forceinline__ int group_block(unsigned *gtab, T *vals, int *nblk, u
   return -1;
 }
 
-template <typename T, int QM>
+template <typename T, int QM, bool KEEPZ>
 __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
     spgemm_block_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
                         int use_add, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
@@ -492,18 +495,21 @@ __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
       info(t, k, nb, a);
       fetch(B.idx + (size_t)k * B.w, B.val + (size_t)k * B.w, nb, jr, vr);
     };
-    // accumulate one step from registers (+ the entries beyond 32*QM from memory)
-    auto step = [&](const int (&jr)[QM], const T (&vr)[QM], int nb, T a, const int *ri, const T *rv) {
-      const int nu = (nb + 31) >> 5;
-      int bs[QM];
+    // accumulate one step from registers (+ the entries beyond 32*QM from memory).  The
+    // body is instantiated for every count NU of occupied register slots (a warp-uniform
+    // switch), so empty slots cost nothing.  Without KEEPZ (tau > 0) blocks start at 0
+    // and an untouched accumulator needs no test: a zero never passes |v| > tau.
+    auto step_nu = [&](auto nu_c, const int (&jr)[QM], const T (&vr)[QM], T a) {
+      constexpr int NU = decltype(nu_c)::value;
+      int sl[NU];
       unsigned miss = 0;
 #pragma unroll
-      for (int u = 0; u < QM; ++u) {
-        bs[u] = -1;
-        if (u < nu && (unsigned)jr[u] < (unsigned)ncol) {
-          const unsigned g = (unsigned)jr[u] >> GSH;
+      for (int u = 0; u < NU; ++u) {
+        sl[u] = -1;
+        const unsigned g = (unsigned)jr[u] >> GSH;
+        if ((unsigned)jr[u] < (unsigned)ncol) {
           const unsigned e = ((volatile unsigned *)gtab)[ghash<BlockCfg<T>::LOG2G>(g)];
-          if (e != 0xFFFFFFFFu && (e >> 8) == g) bs[u] = (int)(e & 0xFFu);
+          if ((e >> 8) == g) sl[u] = (int)(e & 0xFFu) * GW + (jr[u] & (GW - 1));
           else miss |= 1u << u;
         }
       }
@@ -512,7 +518,7 @@ __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
         const int u = miss ? __ffs(miss) - 1 : -1;
         int jj = jr[0];
 #pragma unroll
-        for (int w = 1; w < QM; ++w)
+        for (int w = 1; w < NU; ++w)
           if (u == w) jj = jr[w];
         const unsigned act = __ballot_sync(kFull, u >= 0);
         if (u >= 0) {
@@ -520,35 +526,48 @@ __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
           const unsigned peers = __match_any_sync(act, g);
           const int leader = __ffs(peers) - 1;
           int b = -1;
-          if (lane == leader) b = g < Geo::MAX_GROUP ? group_block<T>(gtab, vals, nblk, g) : -1;
+          if (lane == leader) b = g < Geo::MAX_GROUP ? group_block<T, KEEPZ>(gtab, vals, nblk, g) : -1;
           b = __shfl_sync(peers, b, leader);
 #pragma unroll
-          for (int w = 0; w < QM; ++w)
-            if (u == w) bs[w] = b;
+          for (int w = 0; w < NU; ++w)
+            if (u == w) sl[w] = b < 0 ? -1 : b * GW + (jj & (GW - 1));
           if (b < 0) aborted = true;
           miss &= miss - 1;
         }
       }
       __syncwarp();
-      T old[QM];
+      T old[NU];
 #pragma unroll
-      for (int u = 0; u < QM; ++u)
-        if (u < nu) old[u] = bs[u] >= 0 ? vals[bs[u] * GW + (jr[u] & (GW - 1))] : T(0);
+      for (int u = 0; u < NU; ++u) old[u] = sl[u] >= 0 ? vals[sl[u]] : T(0);
 #pragma unroll
-      for (int u = 0; u < QM; ++u)
-        if (u < nu && bs[u] >= 0) {
-          const T o = is_untouched(old[u]) ? T(0) : old[u];
-          vals[bs[u] * GW + (jr[u] & (GW - 1))] = fmadd(a, vr[u], o);
+      for (int u = 0; u < NU; ++u)
+        if (sl[u] >= 0) {
+          const T o = (KEEPZ && is_untouched(old[u])) ? T(0) : old[u];
+          vals[sl[u]] = fmadd(a, vr[u], o);
         }
-      for (int q = lane + 32 * QM; q < nb; q += 32) {  // rows longer than the registers
-        const int j = __ldg(ri + q);
-        if ((unsigned)j >= (unsigned)ncol) continue;
-        const unsigned g = (unsigned)j >> GSH;
-        const int b = g < Geo::MAX_GROUP ? group_block<T>(gtab, vals, nblk, g) : -1;
-        if (b < 0) { aborted = true; continue; }
-        T *slot = vals + b * GW + (j & (GW - 1));
-        const T o = is_untouched(*slot) ? T(0) : *slot;
-        *slot = fmadd(a, __ldg(rv + q), o);
+    };
+    auto step = [&](const int (&jr)[QM], const T (&vr)[QM], int nb, T a, const int *ri, const T *rv) {
+      const int nu = min((nb + 31) >> 5, QM);
+      switch (nu) {
+        case 0: break;
+        case 1: step_nu(std::integral_constant<int, 1>{}, jr, vr, a); break;
+        case 2: step_nu(std::integral_constant<int, 2>{}, jr, vr, a); break;
+        case 3: step_nu(std::integral_constant<int, 3>{}, jr, vr, a); break;
+        case 4: step_nu(std::integral_constant<int, 4>{}, jr, vr, a); break;
+        case 5: step_nu(std::integral_constant<int, (QM >= 5 ? 5 : QM)>{}, jr, vr, a); break;
+        case 6: step_nu(std::integral_constant<int, (QM >= 6 ? 6 : QM)>{}, jr, vr, a); break;
+        case 7: step_nu(std::integral_constant<int, (QM >= 7 ? 7 : QM)>{}, jr, vr, a); break;
+        default: step_nu(std::integral_constant<int, QM>{}, jr, vr, a); break;
+      }
+      if (nb > 32 * QM) {  // rows longer than the registers: same three phases, from memory
+        for (int base = 32 * QM; base < nb; base += 32) {
+          const int q = base + lane;
+          int jt[QM];
+          T vt[QM];
+          jt[0] = q < nb ? __ldg(ri + q) : -1;
+          vt[0] = q < nb ? __ldg(rv + q) : T(0);
+          step_nu(std::integral_constant<int, 1>{}, jt, vt, a);
+        }
       }
       __syncwarp();
       aborted = __any_sync(kFull, aborted);
@@ -619,7 +638,6 @@ __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
     }
     // walk the groups in column order: 32 / GW groups per warp pass, lane -> column
     const auto tb = mag_bits(tau);
-    const bool keep_all = tau == T(0);
     int nk = 0;
     double dsum = 0.0, fsum = 0.0;
     int *oi = Out.idx + (size_t)r * Out.w;
@@ -635,7 +653,7 @@ __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
         const int b = (int)(e & 0xFFu);
         j = (int)((e >> 8) << GSH) + (lane & (GW - 1));
         v = vals[b * GW + (lane & (GW - 1))];
-        keep = !is_untouched(v) && (keep_all || mag_bits(v) > tb);
+        keep = KEEPZ ? !is_untouched(v) : mag_bits(v) > tb;
       }
       const unsigned m = __ballot_sync(kFull, keep);
       if (keep) {
@@ -969,10 +987,10 @@ int launch_hash(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, const i
   return SP2_OK;
 }
 
-template <typename T, int QM>
+template <typename T, int QM, bool KEEPZ>
 int launch_block(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
   using Geo = BlockGeo<T>;
-  auto kern = spgemm_block_kernel<T, QM>;
+  auto kern = spgemm_block_kernel<T, QM, KEEPZ>;
   static bool attr_set[64] = {false};
   static int occ_cache[64] = {0};
   int dev = 0;
@@ -1004,7 +1022,8 @@ template <typename T, int QM>
 int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb1, int *fb2, int lg, cudaStream_t s) {
   // bin 0: every row; the block accumulator by default, or a warp-private hash table
   // of 2^lg slots when lg is given
-  int rc = lg == 0  ? launch_block<T, QM>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
+  int rc = lg == 0  ? (a.tau == 0.0 ? launch_block<T, QM, true>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
+                                   : launch_block<T, QM, false>(a, rowstat, ctl, fb1, &ctl->n_fallback, s))
          : lg == 10 ? launch_hash<T, 10, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s)
          : lg == 12 ? launch_hash<T, 12, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s)
                     : launch_hash<T, 11, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s);

@@ -41,6 +41,8 @@ def parse():
     p.add_argument("--tau", type=float, default=1e-6)
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--path", type=int, default=0,
+                   help="SpGEMM first pass: 0 automatic, 1/2/4 column blocks with R warps per row, 10-12 hash")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
@@ -263,7 +265,7 @@ def run_ours(a):
     rc, info = S.sp2_step(X1, X2, nocc, a.tau, traces=traces, raise_on_overflow=False)
     w2 = ((info.required_width + 31) // 32) * 32
     X2 = S.Ellpack.empty(a.n, w2, DT)
-    info = S.sp2_step(X1, X2, nocc, a.tau, traces=traces)
+    info = S.sp2_step(X1, X2, nocc, a.tau, traces=traces, spgemm_path=a.path)
     torch.cuda.synchronize()
     h_idx, h_val, h_nnz = [t.cpu().numpy() for t in (X1.idx, X1.val, X1.nnz)]
     nnz_in = int(h_nnz.sum())
@@ -274,7 +276,7 @@ def run_ours(a):
 
     # ---------------- device-timed steps
     for _ in range(a.warmup):
-        S.sp2_step(X1, X2, nocc, a.tau, traces=traces)
+        S.sp2_step(X1, X2, nocc, a.tau, traces=traces, spgemm_path=a.path)
     torch.cuda.synchronize()
     clocks = Clocks(local, enabled=not a.no_clocks)
     if world > 1:
@@ -285,7 +287,7 @@ def run_ours(a):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(a.steps):
-        S.sp2_step(X1, X2, nocc, a.tau, traces=traces)
+        S.sp2_step(X1, X2, nocc, a.tau, traces=traces, spgemm_path=a.path)
     e1.record(stream)
     torch.cuda.synchronize()
     prof = S.sp2_profile_stop()
@@ -329,7 +331,7 @@ def run_ours(a):
 
         def e2e_step():
             S._check(S.lib.ellpack_upload(S._d(Xin), hi.data_ptr(), hv.data_ptr(), hn.data_ptr(), S._stream(stream)))
-            S.sp2_step(Xin, X2, nocc, a.tau, traces=traces)
+            S.sp2_step(Xin, X2, nocc, a.tau, traces=traces, spgemm_path=a.path)
             S._check(S.lib.ellpack_download(S._d(X2), oi.data_ptr(), ov.data_ptr(), on.data_ptr(), S._stream(stream)))
 
         for _ in range(max(1, a.warmup)):
@@ -367,6 +369,7 @@ def run_ours(a):
                 "fma_per_row": fmas / a.n, "branch": "2X-X^2" if info.branch == 2 else "X^2",
                 "l2": "no flush: inputs %.2f GB > 129 MB L2" % (in_bytes / 1e9),
                 "parallelism": "replicas" if world > 1 else "single GPU"}),
+            "spgemm_path": a.path,
             "spgemm_gflops": tflops * 1e3, "spgemm_hbm_gbs": gbs,
             "roofline": roofline,
             "cpu_baseline": cpu,

@@ -189,8 +189,9 @@ typedef struct sp2_options {
   int32_t stall_rule;   /* 1: stop once |trX - trX2| < 0.1 has been seen and err_n >= err_{n-2} */
   int32_t n_fp64_tail;  /* MIXED: minimum FP64 iterations after the switch (default 2) */
   int32_t max_width;    /* cap on the working width (0 = n); SP2E_OVERFLOW beyond it */
-  int32_t table_log2;   /* SpGEMM first pass: 0 = column-block accumulator (default),
-                           10..12 = per-warp hash table of 2^k slots */
+  int32_t spgemm_path;  /* SpGEMM first pass: 0 automatic; 1, 2, 4 = column-block
+                           accumulator shared by that many warps per row; 10..12 =
+                           per-warp hash table of 2^k slots */
   double tau;           /* drop tolerance (default 1e-5) */
   double switch_tol;    /* MIXED: leave the FP32 loop once err_n < switch_tol (0 = automatic:
                            max(tol, 1e-6)); the FP32 stall rule also ends it */
@@ -233,7 +234,7 @@ typedef struct sp2_step_info {
   int64_t nnz_total;       /* out: stored entries of X' */
   int32_t max_row_nnz;     /* out: longest row of X' */
   int32_t required_width;  /* out: longest post-threshold row (valid on overflow too) */
-  int32_t table_log2;      /* in: SpGEMM first pass, 0 = column blocks, 10..12 = hash table */
+  int32_t spgemm_path;     /* in: SpGEMM first pass, as sp2_options.spgemm_path */
   int32_t rows_deferred;   /* out: rows the first pass handed to the 2^14-slot table */
   int32_t rows_dense;      /* out: rows handed further to the dense global-row pass */
   int32_t pad;

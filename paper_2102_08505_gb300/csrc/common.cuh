@@ -116,7 +116,7 @@ struct MultiplyArgs {
   const ellpack_t *A, *B, *Add;
   ellpack_t *Out;
   double alpha, beta, tau;
-  int table_log2;  // first pass: 0 = block accumulator, 10..12 = hash table of 2^k slots per warp
+  int path;  // first pass: 0 automatic, 1/2/4 column blocks with R warps per row, 10..12 hash table
 };
 int multiply_async(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStream_t s);
 

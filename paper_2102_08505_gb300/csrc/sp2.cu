@@ -44,6 +44,8 @@ int read_result(Buffers &b, StepResult *h) {
 }
 
 // (Re)allocates m with at least `width` slots and the given dtype; contents undefined.
+bool valid_path(int p) { return p == 0 || p == 1 || p == 2 || p == 4 || (p >= 10 && p <= 12); }
+
 int ensure(ellpack_t *m, int n, int width, int dtype, cudaStream_t s) {
   if (m->owner && m->width >= width && m->dtype == dtype) return SP2_OK;
   if (m->owner) SP2_TRY(ellpack_destroy(m, s));
@@ -64,7 +66,7 @@ extern "C" void sp2_options_default(sp2_options *o) {
   o->stall_rule = 1;
   o->n_fp64_tail = 2;
   o->max_width = 0;
-  o->table_log2 = 0;
+  o->spgemm_path = 0;
   o->tau = 1e-5;
   o->switch_tol = 0.0;
 }
@@ -86,8 +88,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   if (opt.max_iter < 0 || opt.max_iter + opt.n_fp64_tail >= SP2_STATS_CAP)
     return fail(SP2E_ARG, "sp2_purify: max_iter + n_fp64_tail must be < %d", SP2_STATS_CAP);
   if (opt.n_fp64_tail < 0) return fail(SP2E_ARG, "sp2_purify: n_fp64_tail < 0");
-  if (opt.table_log2 != 0 && (opt.table_log2 < 10 || opt.table_log2 > 12))
-    return fail(SP2E_ARG, "sp2_purify: table_log2 must be 0 or 10..12");
+  if (!valid_path(opt.spgemm_path)) return fail(SP2E_ARG, "sp2_purify: spgemm_path must be 0, 1, 2, 4 or 10..12");
   const int max_w = (opt.max_width > 0 && opt.max_width < n) ? opt.max_width : n;
   if (!(opt.switch_tol >= 0.0) || !isfinite(opt.switch_tol)) return fail(SP2E_ARG, "sp2_purify: bad switch_tol");
   const double switch_tol = opt.switch_tol > 0.0 ? opt.switch_tol : (tol > 1e-6 ? tol : 1e-6);
@@ -210,7 +211,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
     if (guess < 64) guess = 64;
     int width = round_up((int)(guess < max_w ? guess : max_w), 32);
     if (width > n) width = n;
-    const int lg = opt.table_log2;
+    const int lg = opt.spgemm_path;
     for (;;) {
       SP2_TRY(ensure(&b.Y, n, width, b.X.dtype, s));
       MultiplyArgs a{&b.X, &b.X, beta != 0.0 ? &b.X : nullptr, &b.Y, alpha, beta, opt.tau, lg};
@@ -290,8 +291,7 @@ extern "C" int sp2_step(const ellpack_t *X, ellpack_t *Xn, double nocc, double t
   if (X->idx == Xn->idx || X->val == Xn->val || X->nnz == Xn->nnz) return fail(SP2E_ARG, "sp2_step: Xn aliases X");
   if (!(tau >= 0.0) || !isfinite(tau)) return fail(SP2E_ARG, "sp2_step: tau must be finite and >= 0");
   if (!isfinite(nocc)) return fail(SP2E_ARG, "sp2_step: nocc not finite");
-  if (info->table_log2 != 0 && (info->table_log2 < 10 || info->table_log2 > 12))
-    return fail(SP2E_ARG, "sp2_step: table_log2 must be 0 or 10..12");
+  if (!valid_path(info->spgemm_path)) return fail(SP2E_ARG, "sp2_step: spgemm_path must be 0, 1, 2, 4 or 10..12");
   const int n = X->n;
   Buffers b;
   b.s = as_stream(stream);
@@ -313,7 +313,7 @@ extern "C" int sp2_step(const ellpack_t *X, ellpack_t *Xn, double nocc, double t
   info->err = fabs(trX - trX2) / (double)n;
   const bool up = fabs(2.0 * trX - trX2 - nocc) < fabs(trX2 - nocc);
   info->branch = up ? 2 : 1;
-  MultiplyArgs a{X, X, up ? X : nullptr, Xn, up ? -1.0 : 1.0, up ? 2.0 : 0.0, tau, info->table_log2};
+  MultiplyArgs a{X, X, up ? X : nullptr, Xn, up ? -1.0 : 1.0, up ? 2.0 : 0.0, tau, info->spgemm_path};
   SP2_TRY(multiply_async(a, b.rowstat, b.ctl, s));
   launch_reduce_rows(b.rowstat, Xn->nnz, n, b.ctl, b.dres, s);
   SP2_CUDA(cudaGetLastError());

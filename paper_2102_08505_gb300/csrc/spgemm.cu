@@ -350,14 +350,18 @@ __global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32, 1)
 
 // ------------------------------------------------------------------ block accumulator
 // First pass of the multiply.  Columns are taken in groups of GW = 2^GSH consecutive
-// indices.  Each group a row touches gets a dense block of GW accumulators in the warp's
-// shared memory; a small open-addressing table maps group -> block (entry = g << 8 | b).
-// The accumulator of column j is vals[b * GW + (j & (GW-1))]: no per-column key, no
-// probing, and the bank of a column is fixed by its low bits, so a warp holding a run of
-// consecutive columns touches distinct banks.  Untouched accumulators hold a signalling
-// NaN bit pattern (arithmetic never produces it), so "structural" means "touched".
-// Blocks are handed out by one elected lane per distinct new group.  The row comes out
-// sorted by walking the groups in ascending order: no sort of the entries is needed.
+// indices.  Each group a row touches gets a dense block of GW accumulators in shared
+// memory; a small open-addressing table maps group -> block (entry = g << 8 | b).  The
+// accumulator of column j is vals[b * GW + (j & (GW-1))]: no per-column key, no probing,
+// and the bank of a column is fixed by its low bits, so a warp holding a run of
+// consecutive columns touches distinct banks.
+// A row is processed by a group of R warps sharing one accumulator.  In each k step the
+// columns of B_k are distinct, so the R*32 lanes split B_k's entries and update distinct
+// accumulators; one barrier of the R warps orders consecutive steps (no atomics on
+// values).  Blocks are cleared when the row starts (to 0, or to a signalling-NaN
+// sentinel when tau == 0 so that "structural" can be told from "zero"), so handing out
+// a block is a single CAS on the table.  The row comes out sorted by walking the groups
+// in ascending order: no sort of the entries is needed.
 template <typename T> struct BlockCfg;
 template <> struct BlockCfg<double> {
   static constexpr int GSH = 4, NB = 224, LOG2G = 10;
@@ -365,15 +369,17 @@ template <> struct BlockCfg<double> {
 template <> struct BlockCfg<float> {
   static constexpr int GSH = 5, NB = 128, LOG2G = 9;
 };
-template <typename T>
+template <typename T, int R>
 struct BlockGeo {
   static constexpr int GSH = BlockCfg<T>::GSH, GW = 1 << GSH, NB = BlockCfg<T>::NB;
   static constexpr int G = 1 << BlockCfg<T>::LOG2G;
   static constexpr int VAL_BYTES = NB * GW * (int)sizeof(T);
-  static constexpr int BYTES_PER_WARP = VAL_BYTES + G * 4 + 16;
-  static constexpr int WARPS_RAW = 232192 / BYTES_PER_WARP;
-  static constexpr int WARPS = WARPS_RAW > 16 ? 16 : (WARPS_RAW < 1 ? 1 : WARPS_RAW);
-  static constexpr int SMEM = WARPS * BYTES_PER_WARP;
+  static constexpr int BYTES_PER_GROUP = VAL_BYTES + G * 4 + 16;
+  static constexpr int GROUPS_RAW = 232192 / BYTES_PER_GROUP;
+  static constexpr int GROUPS_MAX = (sizeof(T) == 4 ? 10 : 16) / (R > 2 ? 2 : 1);
+  static constexpr int GROUPS = GROUPS_RAW > GROUPS_MAX ? GROUPS_MAX : (GROUPS_RAW < 1 ? 1 : GROUPS_RAW);
+  static constexpr int WARPS = GROUPS * R;
+  static constexpr int SMEM = GROUPS * BYTES_PER_GROUP;
   // g < 2^24 - 1 fits the packed entry and never matches the empty entry 0xFFFFFFFF
   static constexpr unsigned MAX_GROUP = (1u << 24) - 1u;
 };
@@ -389,75 +395,104 @@ template <> __device__ __forceinline__ float untouched<float>() { return __uint_
 template <int LOG2G>
 __device__ __forceinline__ int ghash(unsigned g) { return (int)((g * 0x9E3779B1u) >> (32 - LOG2G)); }
 
-// Group -> block, allocating (and clearing) a block when the group is new.  Called by
-// one lane per distinct group; returns the block or -1 when the blocks are used up.
-template <typename T, bool KEEPZ>
-__device__ __forceinline__ int group_block(unsigned *gtab, T *vals, int *nblk, unsigned g) {
-  using Geo = BlockGeo<T>;
+// Group -> block, taking a fresh (pre-cleared) block when the group is new.  Lanes of
+// different warps may race for the same group: the CAS keeps the first block, the other
+// one stays unused.  Returns -1 when the blocks are used up.
+template <typename T, int R>
+__device__ __forceinline__ int group_block(unsigned *gtab, int *nblk, unsigned g) {
+  using Geo = BlockGeo<T, R>;
   int h = ghash<BlockCfg<T>::LOG2G>(g);
 #pragma unroll 1
   for (int p = 0; p < Geo::G; ++p) {
     const unsigned e = ((volatile unsigned *)gtab)[h];
-    if (e != 0xFFFFFFFFu && (e >> 8) == g) {
-      __threadfence_block();  // pairs with the fence of the lane that cleared the block
-      return (int)(e & 0xFFu);
-    }
+    if ((e >> 8) == g) return (int)(e & 0xFFu);
     if (e == 0xFFFFFFFFu) {
       const int b = atomicAdd(nblk, 1);
       if (b >= Geo::NB) return -1;
-      T *blk = vals + (size_t)b * Geo::GW;
-#pragma unroll
-      for (int t = 0; t < Geo::GW; ++t) blk[t] = KEEPZ ? untouched<T>() : T(0);
-      __threadfence_block();  // the cleared block is visible before the entry naming it
       const unsigned old = atomicCAS(gtab + h, 0xFFFFFFFFu, (g << 8) | (unsigned)b);
       if (old == 0xFFFFFFFFu) return b;
-      // the slot was claimed first by another group (this block stays unused) or by the
-      // same group from another lane (use that block); keep probing otherwise
-      if ((old >> 8) == g) {
-        __threadfence_block();
-        return (int)(old & 0xFFu);
-      }
+      if ((old >> 8) == g) return (int)(old & 0xFFu);
     }
     h = (h + 1) & (Geo::G - 1);
   }
   return -1;
 }
 
-template <typename T, int QM, bool KEEPZ>
-__global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
+// Barrier of the R warps of a row group (named barrier grp + 1; the warp itself when
+// R == 1).  group_sync_or also returns the OR of `pred` over the group's threads, taken
+// by the barrier instruction itself, so every warp sees the same value.
+template <int R>
+__device__ __forceinline__ void group_sync(int grp) {
+  if (R == 1) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(R * 32) : "memory");
+  }
+}
+template <int R>
+__device__ __forceinline__ bool group_sync_or(int grp, bool pred) {
+  if (R == 1) {
+    __syncwarp();
+    return __any_sync(0xffffffffu, pred);
+  }
+  unsigned out;
+  asm volatile(
+      "{\n\t.reg .pred q, p;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, %2, %3, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(out)
+      : "r"((unsigned)pred), "r"(grp + 1), "r"(R * 32)
+      : "memory");
+  return out != 0;
+}
+
+template <typename T, int R, int QW, bool KEEPZ>
+__global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
     spgemm_block_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
                         int use_add, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
                         int *__restrict__ fb_list, int *__restrict__ fb_count) {
-  using Geo = BlockGeo<T>;
+  using Geo = BlockGeo<T, R>;
   constexpr int GW = Geo::GW, GSH = Geo::GSH, G = Geo::G;
+  constexpr int SPAN = 32 * R;  // entries of a B row covered by one register slot of the group
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned char *base = smem + (size_t)wid * Geo::BYTES_PER_WARP;
+  const int grp = wid / R, wr = wid % R, gt = wr * 32 + lane;  // group, warp in group, thread in group
+  unsigned char *base = smem + (size_t)grp * Geo::BYTES_PER_GROUP;
   T *vals = reinterpret_cast<T *>(base);
   unsigned *gtab = reinterpret_cast<unsigned *>(base + Geo::VAL_BYTES);
   int *nblk = reinterpret_cast<int *>(base + Geo::VAL_BYTES + G * 4);
   const int ncol = Out.n;
-  const int nw = gridDim.x * Geo::WARPS;
   const unsigned lt = lanemask_lt();
   int wmax = 0, wover = 0;
 
-  for (int r = blockIdx.x * Geo::WARPS + wid; r < A.n; r += nw) {
-    for (int s = lane * 4; s < G; s += 128) *reinterpret_cast<uint4 *>(gtab + s) = make_uint4(~0u, ~0u, ~0u, ~0u);
-    if (lane == 0) *nblk = 0;
-    __syncwarp();
+  for (int r = blockIdx.x * Geo::GROUPS + grp; r < A.n; r += gridDim.x * Geo::GROUPS) {
+    {  // clear the blocks and the table
+      const T c = KEEPZ ? untouched<T>() : T(0);
+      constexpr int PER16 = 16 / (int)sizeof(T);
+      for (int i = gt * PER16; i < Geo::NB * GW; i += SPAN * PER16) {
+#pragma unroll
+        for (int t = 0; t < PER16; ++t) vals[i + t] = c;
+      }
+      for (int i = gt * 4; i < G; i += SPAN * 4)
+        *reinterpret_cast<uint4 *>(gtab + i) = make_uint4(~0u, ~0u, ~0u, ~0u);
+      if (gt == 0) *nblk = 0;
+    }
+    group_sync<R>(grp);
     bool aborted = false;
 
     // Step = accumulate a * (one source row) into the blocks: first the row of the
     // addend C (a = beta), then row k of B for each entry a_ik of A's row (a = alpha*a_ik).
-    // A's entries and nnz(B_k) are loaded 32 steps at a time, one chunk ahead; each B row
-    // is loaded into registers two steps before it is consumed (three buffers rotate).
+    // A's entries and nnz(B_k) are loaded 32 steps at a time, one chunk ahead; each warp
+    // loads its share of a B row into registers two steps before it is consumed (three
+    // buffers rotate).
     const int na = min(A.nnz[r], A.w);
     const int *arow_i = A.idx + (size_t)r * A.w;
     const T *arow_v = A.val + (size_t)r * A.w;
     int ck, cnb, nk_, nnb;
     T ca, na_;
-    auto load_chunk = [&](int base, int &kk, int &nbk, T &av) {
-      const int s = base + lane;
+    auto load_chunk = [&](int cb, int &kk, int &nbk, T &av) {
+      const int s = cb + lane;
       kk = 0; nbk = 0; av = T(0);
       if (s < na) {
         const int k = __ldg(arow_i + s);
@@ -471,8 +506,7 @@ __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
     load_chunk(0, ck, cnb, ca);
     load_chunk(32, nk_, nnb, na_);
     int cbase = 0;
-    // (k, nb, a) of step t, t in [cbase, cbase + 64)
-    auto info = [&](int t, int &k, int &nb, T &a) {
+    auto info = [&](int t, int &k, int &nb, T &a) {  // t in [cbase, cbase + 64)
       if (t < cbase + 32) {
         k = __shfl_sync(kFull, ck, t & 31);
         nb = __shfl_sync(kFull, cnb, t & 31);
@@ -483,23 +517,21 @@ __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
         a = __shfl_sync(kFull, na_, t & 31);
       }
     };
-    auto fetch = [&](const int *ri, const T *rv, int nb, int (&jr)[QM], T (&vr)[QM]) {
+    auto fetch = [&](const int *ri, const T *rv, int nb, int (&jr)[QW], T (&vr)[QW]) {
 #pragma unroll
-      for (int u = 0; u < QM; ++u) {
-        const int q = lane + 32 * u;
+      for (int u = 0; u < QW; ++u) {
+        const int q = SPAN * u + gt;
         jr[u] = q < nb ? __ldg(ri + q) : -1;
         vr[u] = q < nb ? __ldg(rv + q) : T(0);
       }
     };
-    auto fetch_step = [&](int t, int (&jr)[QM], T (&vr)[QM], int &nb, T &a, int &k) {
+    auto fetch_step = [&](int t, int (&jr)[QW], T (&vr)[QW], int &nb, T &a, int &k) {
       info(t, k, nb, a);
       fetch(B.idx + (size_t)k * B.w, B.val + (size_t)k * B.w, nb, jr, vr);
     };
-    // accumulate one step from registers (+ the entries beyond 32*QM from memory).  The
-    // body is instantiated for every count NU of occupied register slots (a warp-uniform
-    // switch), so empty slots cost nothing.  Without KEEPZ (tau > 0) blocks start at 0
-    // and an untouched accumulator needs no test: a zero never passes |v| > tau.
-    auto step_nu = [&](auto nu_c, const int (&jr)[QM], const T (&vr)[QM], T a) {
+    // accumulate one step from registers, body instantiated per number NU of occupied
+    // register slots of this warp (warp-uniform switch: empty slots cost nothing)
+    auto step_nu = [&](auto nu_c, const int (&jr)[QW], const T (&vr)[QW], T a) {
       constexpr int NU = decltype(nu_c)::value;
       int sl[NU];
       unsigned miss = 0;
@@ -513,7 +545,7 @@ __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
           else miss |= 1u << u;
         }
       }
-      // misses: one elected lane per distinct group finds or allocates its block
+      // misses: one elected lane per distinct group of this warp finds or takes a block
       while (__any_sync(kFull, miss != 0)) {
         const int u = miss ? __ffs(miss) - 1 : -1;
         int jj = jr[0];
@@ -526,7 +558,7 @@ __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
           const unsigned peers = __match_any_sync(act, g);
           const int leader = __ffs(peers) - 1;
           int b = -1;
-          if (lane == leader) b = g < Geo::MAX_GROUP ? group_block<T, KEEPZ>(gtab, vals, nblk, g) : -1;
+          if (lane == leader) b = g < Geo::MAX_GROUP ? group_block<T, R>(gtab, nblk, g) : -1;
           b = __shfl_sync(peers, b, leader);
 #pragma unroll
           for (int w = 0; w < NU; ++w)
@@ -535,7 +567,6 @@ __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
           miss &= miss - 1;
         }
       }
-      __syncwarp();
       T old[NU];
 #pragma unroll
       for (int u = 0; u < NU; ++u) old[u] = sl[u] >= 0 ? vals[sl[u]] : T(0);
@@ -546,35 +577,35 @@ __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
           vals[sl[u]] = fmadd(a, vr[u], o);
         }
     };
-    auto step = [&](const int (&jr)[QM], const T (&vr)[QM], int nb, T a, const int *ri, const T *rv) {
-      const int nu = min((nb + 31) >> 5, QM);
+    auto step = [&](const int (&jr)[QW], const T (&vr)[QW], int nb, T a, const int *ri, const T *rv) {
+      const int mine = nb > 32 * wr ? (nb - 32 * wr + SPAN - 1) / SPAN : 0;  // slots of this warp
+      const int nu = min(mine, QW);
       switch (nu) {
         case 0: break;
         case 1: step_nu(std::integral_constant<int, 1>{}, jr, vr, a); break;
-        case 2: step_nu(std::integral_constant<int, 2>{}, jr, vr, a); break;
-        case 3: step_nu(std::integral_constant<int, 3>{}, jr, vr, a); break;
-        case 4: step_nu(std::integral_constant<int, 4>{}, jr, vr, a); break;
-        case 5: step_nu(std::integral_constant<int, (QM >= 5 ? 5 : QM)>{}, jr, vr, a); break;
-        case 6: step_nu(std::integral_constant<int, (QM >= 6 ? 6 : QM)>{}, jr, vr, a); break;
-        case 7: step_nu(std::integral_constant<int, (QM >= 7 ? 7 : QM)>{}, jr, vr, a); break;
-        default: step_nu(std::integral_constant<int, QM>{}, jr, vr, a); break;
+        case 2: step_nu(std::integral_constant<int, (QW >= 2 ? 2 : QW)>{}, jr, vr, a); break;
+        case 3: step_nu(std::integral_constant<int, (QW >= 3 ? 3 : QW)>{}, jr, vr, a); break;
+        case 4: step_nu(std::integral_constant<int, (QW >= 4 ? 4 : QW)>{}, jr, vr, a); break;
+        case 5: step_nu(std::integral_constant<int, (QW >= 5 ? 5 : QW)>{}, jr, vr, a); break;
+        case 6: step_nu(std::integral_constant<int, (QW >= 6 ? 6 : QW)>{}, jr, vr, a); break;
+        case 7: step_nu(std::integral_constant<int, (QW >= 7 ? 7 : QW)>{}, jr, vr, a); break;
+        default: step_nu(std::integral_constant<int, QW>{}, jr, vr, a); break;
       }
-      if (nb > 32 * QM) {  // rows longer than the registers: same three phases, from memory
-        for (int base = 32 * QM; base < nb; base += 32) {
-          const int q = base + lane;
-          int jt[QM];
-          T vt[QM];
+      if (nb > SPAN * QW) {  // rows longer than the registers: same phases, from memory
+        for (int q0 = SPAN * QW; q0 < nb; q0 += SPAN) {
+          const int q = q0 + gt;
+          int jt[QW];
+          T vt[QW];
           jt[0] = q < nb ? __ldg(ri + q) : -1;
           vt[0] = q < nb ? __ldg(rv + q) : T(0);
           step_nu(std::integral_constant<int, 1>{}, jt, vt, a);
         }
       }
-      __syncwarp();
-      aborted = __any_sync(kFull, aborted);
+      aborted = group_sync_or<R>(grp, aborted);  // orders this step's updates before the next step's
     };
 
-    int j0[QM], j1[QM], j2[QM];
-    T v0[QM], v1[QM], v2[QM];
+    int j0[QW], j1[QW], j2[QW];
+    T v0[QW], v1[QW], v2[QW];
     int nb0 = 0, nb1 = 0, nb2 = 0, k0 = 0, k1 = 0, k2 = 0;
     T a0 = T(0), a1 = T(0), a2 = T(0);
     if (use_add) {
@@ -605,81 +636,84 @@ __global__ void __launch_bounds__(BlockGeo<T>::WARPS * 32, 1)
       step(j2, v2, nb2, a2, B.idx + (size_t)k2 * B.w, B.val + (size_t)k2 * B.w);
     }
     if (aborted) {
-      if (lane == 0) {
+      if (gt == 0) {
         const int p = atomicAdd(fb_count, 1);
         fb_list[p] = r;
       }
+      group_sync<R>(grp);
       continue;
     }
-    // compact the used group entries to the front of the table, sort them by group
-    int ng = 0;
-    for (int c = 0; c < G; c += 32) {
-      const unsigned e = gtab[c + lane];
-      const bool used = e != 0xFFFFFFFFu;
-      const unsigned m = __ballot_sync(kFull, used);
-      __syncwarp();
-      if (used) gtab[ng + __popc(m & lt)] = e;
-      ng += __popc(m);
-    }
-    {
-      int P = 32;
-      while (P < ng) P <<= 1;
-      for (int s = ng + lane; s < P; s += 32) gtab[s] = 0xFFFFFFFFu;
-      __syncwarp();
-      for (int k = 2; k <= P; k <<= 1)
-        for (int jj = k >> 1; jj > 0; jj >>= 1) {
-          for (int e = lane; e < (P >> 1); e += 32) {
-            const int i = ((e & ~(jj - 1)) << 1) | (e & (jj - 1));
-            const unsigned x = gtab[i], y = gtab[i + jj];
-            if ((x > y) == ((i & k) == 0)) { gtab[i] = y; gtab[i + jj] = x; }
+    if (wr == 0) {
+      // compact the used group entries to the front of the table, sort them by group
+      int ng = 0;
+      for (int c = 0; c < G; c += 32) {
+        const unsigned e = gtab[c + lane];
+        const bool used = e != 0xFFFFFFFFu;
+        const unsigned m = __ballot_sync(kFull, used);
+        __syncwarp();
+        if (used) gtab[ng + __popc(m & lt)] = e;
+        ng += __popc(m);
+      }
+      {
+        int P = 32;
+        while (P < ng) P <<= 1;
+        for (int s2 = ng + lane; s2 < P; s2 += 32) gtab[s2] = 0xFFFFFFFFu;
+        __syncwarp();
+        for (int k = 2; k <= P; k <<= 1)
+          for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int e = lane; e < (P >> 1); e += 32) {
+              const int i = ((e & ~(jj - 1)) << 1) | (e & (jj - 1));
+              const unsigned x = gtab[i], y = gtab[i + jj];
+              if ((x > y) == ((i & k) == 0)) { gtab[i] = y; gtab[i + jj] = x; }
+            }
+            __syncwarp();
           }
-          __syncwarp();
+      }
+      // walk the groups in column order: 32 / GW groups per pass, lane -> column
+      const auto tb = mag_bits(tau);
+      int nk = 0;
+      double dsum = 0.0, fsum = 0.0;
+      int *oi = Out.idx + (size_t)r * Out.w;
+      T *ov = Out.val + (size_t)r * Out.w;
+      constexpr int GPP = 32 / GW;
+      for (int c = 0; c < ng; c += GPP) {
+        const int gi = c + lane / GW;
+        bool keep = false;
+        int j = 0;
+        T v = T(0);
+        if (gi < ng) {
+          const unsigned e = gtab[gi];
+          const int b = (int)(e & 0xFFu);
+          j = (int)((e >> 8) << GSH) + (lane & (GW - 1));
+          v = vals[b * GW + (lane & (GW - 1))];
+          keep = KEEPZ ? !is_untouched(v) : mag_bits(v) > tb;
         }
-    }
-    // walk the groups in column order: 32 / GW groups per warp pass, lane -> column
-    const auto tb = mag_bits(tau);
-    int nk = 0;
-    double dsum = 0.0, fsum = 0.0;
-    int *oi = Out.idx + (size_t)r * Out.w;
-    T *ov = Out.val + (size_t)r * Out.w;
-    constexpr int GPP = 32 / GW;  // groups per pass
-    for (int c = 0; c < ng; c += GPP) {
-      const int gi = c + lane / GW;
-      bool keep = false;
-      int j = 0;
-      T v = T(0);
-      if (gi < ng) {
-        const unsigned e = gtab[gi];
-        const int b = (int)(e & 0xFFu);
-        j = (int)((e >> 8) << GSH) + (lane & (GW - 1));
-        v = vals[b * GW + (lane & (GW - 1))];
-        keep = KEEPZ ? !is_untouched(v) : mag_bits(v) > tb;
+        const unsigned m = __ballot_sync(kFull, keep);
+        if (keep) {
+          const int pos = nk + __popc(m & lt);
+          if (pos < Out.w) { oi[pos] = j; ov[pos] = v; }
+          const double dv = (double)v;
+          if (j == r) dsum += dv;
+          fsum = fma(dv, dv, fsum);
+        }
+        nk += __popc(m);
       }
-      const unsigned m = __ballot_sync(kFull, keep);
-      if (keep) {
-        const int pos = nk + __popc(m & lt);
-        if (pos < Out.w) { oi[pos] = j; ov[pos] = v; }
-        const double dv = (double)v;
-        if (j == r) dsum += dv;
-        fsum = fma(dv, dv, fsum);
-      }
-      nk += __popc(m);
-    }
-    dsum = warp_sum(dsum);
-    fsum = warp_sum(fsum);
-    wmax = max(wmax, nk);
-    if (lane == 0) {
-      if (nk > Out.w) {
-        ++wover;
-        rowstat[r] = make_double2(0.0, 0.0);
-      } else {
-        Out.nnz[r] = nk;
-        rowstat[r] = make_double2(dsum, fsum);
+      dsum = warp_sum(dsum);
+      fsum = warp_sum(fsum);
+      wmax = max(wmax, nk);
+      if (lane == 0) {
+        if (nk > Out.w) {
+          ++wover;
+          rowstat[r] = make_double2(0.0, 0.0);
+        } else {
+          Out.nnz[r] = nk;
+          rowstat[r] = make_double2(dsum, fsum);
+        }
       }
     }
-    __syncwarp();
+    group_sync<R>(grp);  // the accumulator is free for the next row
   }
-  if (lane == 0) {
+  if (lane == 0 && wr == 0) {
     if (wmax) atomicMax(&ctl->max_count, wmax);
     if (wover) atomicAdd(&ctl->overflow_rows, wover);
   }
@@ -987,10 +1021,10 @@ int launch_hash(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, const i
   return SP2_OK;
 }
 
-template <typename T, int QM, bool KEEPZ>
+template <typename T, int R, int QW, bool KEEPZ>
 int launch_block(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
-  using Geo = BlockGeo<T>;
-  auto kern = spgemm_block_kernel<T, QM, KEEPZ>;
+  using Geo = BlockGeo<T, R>;
+  auto kern = spgemm_block_kernel<T, R, QW, KEEPZ>;
   static bool attr_set[64] = {false};
   static int occ_cache[64] = {0};
   int dev = 0;
@@ -1004,7 +1038,7 @@ int launch_block(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
     attr_set[dev] = true;
   }
   const long long cap = (long long)num_sms() * occ_cache[dev];
-  const long long blocks = ((long long)a.A->n + Geo::WARPS - 1) / Geo::WARPS;
+  const long long blocks = ((long long)a.A->n + Geo::GROUPS - 1) / Geo::GROUPS;
   int grid = (int)(blocks < cap ? blocks : cap);
   if (grid < 1) grid = 1;
   const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
@@ -1018,16 +1052,28 @@ int launch_block(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
   return SP2_OK;
 }
 
+// Block first pass with R warps per row; the register slots per warp cover the width of B.
+template <typename T, int R>
+int launch_block_r(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
+  constexpr int QW = (R == 1) ? 8 : (R == 2 ? 4 : 2);
+  return a.tau == 0.0 ? launch_block<T, R, QW, true>(a, rowstat, ctl, fb, fb_count, s)
+                      : launch_block<T, R, QW, false>(a, rowstat, ctl, fb, fb_count, s);
+}
+
+// First pass over every row (path: 0 automatic, 1/2/4 column blocks with that many
+// warps per row, 10..12 hash table of 2^path slots per warp), then the deferred rows in
+// a one-warp 2^14-slot hash table.
 template <typename T, int QM>
-int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb1, int *fb2, int lg, cudaStream_t s) {
-  // bin 0: every row; the block accumulator by default, or a warp-private hash table
-  // of 2^lg slots when lg is given
-  int rc = lg == 0  ? (a.tau == 0.0 ? launch_block<T, QM, true>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
-                                   : launch_block<T, QM, false>(a, rowstat, ctl, fb1, &ctl->n_fallback, s))
-         : lg == 10 ? launch_hash<T, 10, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s)
-         : lg == 12 ? launch_hash<T, 12, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s)
-                    : launch_hash<T, 11, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s);
-  // bin 1: the deferred rows, one warp per CTA with a 2^14-slot table
+int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb1, int *fb2, int path, cudaStream_t s) {
+  int rc;
+  switch (path) {
+    case 1: rc = launch_block_r<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
+    case 4: rc = launch_block_r<T, 4>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
+    case 10: rc = launch_hash<T, 10, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s); break;
+    case 11: rc = launch_hash<T, 11, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s); break;
+    case 12: rc = launch_hash<T, 12, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s); break;
+    default: rc = launch_block_r<T, 2>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
+  }
   if (rc == SP2_OK)
     rc = launch_hash<T, 14, QM>(a, rowstat, ctl, fb1, &ctl->n_fallback, fb2, &ctl->n_fallback2, s);
   return rc;
@@ -1040,9 +1086,8 @@ int multiply_t(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStre
   SP2_TRY(dev_alloc((void **)&fb, 2 * sizeof(int) * (size_t)n, s));
   int *fb1 = fb, *fb2 = fb + n;
   const int qm_need = (a.B->width + 31) / 32;
-  const int lg = a.table_log2;
-  int rc = qm_need <= 4 ? launch_bins<T, 4>(a, rowstat, ctl, fb1, fb2, lg, s)
-                        : launch_bins<T, 8>(a, rowstat, ctl, fb1, fb2, lg, s);
+  int rc = qm_need <= 4 ? launch_bins<T, 4>(a, rowstat, ctl, fb1, fb2, a.path, s)
+                        : launch_bins<T, 8>(a, rowstat, ctl, fb1, fb2, a.path, s);
   if (rc == SP2_OK) {
     // bin 2: rows beyond the largest table, dense global-memory rows
     void *acc = nullptr;

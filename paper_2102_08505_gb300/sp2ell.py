@@ -37,7 +37,7 @@ class ellpack_t(ctypes.Structure):
 
 class sp2_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("stall_rule", ctypes.c_int32),
-                ("n_fp64_tail", ctypes.c_int32), ("max_width", ctypes.c_int32), ("table_log2", ctypes.c_int32),
+                ("n_fp64_tail", ctypes.c_int32), ("max_width", ctypes.c_int32), ("spgemm_path", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("switch_tol", ctypes.c_double)]
 
 
@@ -54,7 +54,7 @@ class sp2_step_info(ctypes.Structure):
     _fields_ = [("trX", ctypes.c_double), ("trX2", ctypes.c_double), ("have_traces", ctypes.c_int32),
                 ("branch", ctypes.c_int32), ("err", ctypes.c_double), ("trXn", ctypes.c_double),
                 ("trXn2", ctypes.c_double), ("nnz_total", ctypes.c_int64), ("max_row_nnz", ctypes.c_int32),
-                ("required_width", ctypes.c_int32), ("table_log2", ctypes.c_int32),
+                ("required_width", ctypes.c_int32), ("spgemm_path", ctypes.c_int32),
                 ("rows_deferred", ctypes.c_int32), ("rows_dense", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
@@ -317,14 +317,14 @@ def sp2_x0(H, X0, tau, stream=None):
     return lo.value, hi.value
 
 
-def sp2_step(X, Xn, nocc, tau, traces=None, table_log2=0, stream=None, raise_on_overflow=True):
+def sp2_step(X, Xn, nocc, tau, traces=None, spgemm_path=0, stream=None, raise_on_overflow=True):
     """One SP2 iteration X -> Xn.  traces = (trX, trX2) of X if known.  Returns the
     sp2_step_info record (and the status when raise_on_overflow=False)."""
     info = sp2_step_info()
     if traces is not None:
         info.trX, info.trX2 = traces
         info.have_traces = 1
-    info.table_log2 = table_log2
+    info.spgemm_path = spgemm_path
     rc = lib.sp2_step(_d(X), _d(Xn), float(nocc), float(tau), ctypes.byref(info), _stream(stream))
     if not raise_on_overflow:
         if rc not in (SP2_OK, SP2E_OVERFLOW):

@@ -264,7 +264,7 @@ def test_x0(gpu, tau):
         assert np.allclose(gv[i, :gn[i]], ref.row(i)[1], rtol=5e-16, atol=1e-300)
 
 
-@pytest.mark.parametrize("first_pass", [0, 11])
+@pytest.mark.parametrize("first_pass", [0, 1, 2, 4, 11])
 @pytest.mark.parametrize("fp32", [False, True])
 def test_first_pass_variants(gpu, first_pass, fp32):
     """Both first-pass accumulators (column blocks, per-warp hash table) on one SP2 step of
@@ -280,9 +280,9 @@ def test_first_pass_variants(gpu, first_pass, fp32):
     dt = S.SP2_F32 if fp32 else S.SP2_F64
     d1 = dev(S, X1, dt)
     probe = S.Ellpack.empty(n, 32, dt)
-    rc, info = S.sp2_step(d1, probe, n / 2, 1e-5, table_log2=first_pass, raise_on_overflow=False)
+    rc, info = S.sp2_step(d1, probe, n / 2, 1e-5, spgemm_path=first_pass, raise_on_overflow=False)
     out = S.Ellpack.empty(n, ((info.required_width + 31) // 32) * 32, dt)
-    info = S.sp2_step(d1, out, n / 2, 1e-5, table_log2=first_pass)
+    info = S.sp2_step(d1, out, n / 2, 1e-5, spgemm_path=first_pass)
     up = info.branch == 2
     compare_spgemm(out.to_numpy(), X1, X1, X1, -1.0 if up else 1.0, 2.0 if up else 0.0, 1e-5, fp32=fp32)
     assert info.rows_deferred == 0

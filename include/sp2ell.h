@@ -146,6 +146,26 @@ int ellpack_trace(const ellpack_t *A, double *out, void *stream);
  * Synchronises `stream`. */
 int ellpack_frobenius2(const ellpack_t *A, double *out, void *stream);
 
+/*
+ * tr A and sum_ij A_ij^2, like ellpack_trace and ellpack_frobenius2 (same kernels, same
+ * fixed summation order, so the same results), for callers that cannot allocate device
+ * memory: for example a host application that reserves all of the GPU's memory for its
+ * own pool at start-up and forbids any further allocation, or a latency-critical loop
+ * where an allocation call and the synchronisation it may bring are not acceptable.
+ * This entry point allocates nothing.  Its scratch is a fixed array of
+ * SP2_NOALLOC_MAX_N * 16 + 256 bytes (1 MiB + 256 B) in the library's device image,
+ * held by every GPU that loads the library until the process exits; n above
+ * SP2_NOALLOC_MAX_N is rejected with SP2E_ARG.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (other streams, other host threads) race and must not be issued.
+ * The paper has no counterpart; it exists only for such callers.
+ * trace (required) and frobenius2 (optional) are host pointers.  Synchronises `stream`.
+ * Errors: SP2E_ARG, SP2E_CUDA, SP2E_NONFINITE.
+ */
+#define SP2_NOALLOC_MAX_N 65536
+int ellpack_trace_noalloc(const ellpack_t *A, double *trace, double *frobenius2, void *stream);
+
 /* Gershgorin bounds of H: e_min = min_i (H_ii - sum_{j!=i} |H_ij|),
  * e_max = max_i (H_ii + sum_{j!=i} |H_ij|), FP64.  Synchronises `stream`. */
 int ellpack_gershgorin(const ellpack_t *H, double *emin, double *emax, void *stream);

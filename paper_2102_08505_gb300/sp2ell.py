@@ -88,6 +88,7 @@ def _load():
         "ellpack_trace": ([E, P(D), V], ctypes.c_int),
         "ellpack_frobenius2": ([E, P(D), V], ctypes.c_int),
         "ellpack_gershgorin": ([E, P(D), P(D), V], ctypes.c_int),
+        "ellpack_trace_noalloc": ([E, P(D), P(D), V], ctypes.c_int),
         "sp2_options_default": ([P(sp2_options)], None),
         "sp2_purify": ([E, D, D, P(sp2_options), E, P(sp2_stats), V], ctypes.c_int),
         "sp2_x0": ([E, D, E, P(D), P(D), V], ctypes.c_int),
@@ -265,6 +266,17 @@ def ellpack_frobenius2(A, stream=None):
     out = ctypes.c_double()
     _check(lib.ellpack_frobenius2(_d(A), ctypes.byref(out), _stream(stream)))
     return out.value
+
+
+SP2_NOALLOC_MAX_N = 65536
+
+
+def ellpack_trace_noalloc(A, stream=None):
+    """(tr A, ||A||_F^2) through the entry point that allocates no device memory (its
+    scratch is a fixed array inside the library; n <= SP2_NOALLOC_MAX_N)."""
+    tr, fro = ctypes.c_double(), ctypes.c_double()
+    _check(lib.ellpack_trace_noalloc(_d(A), ctypes.byref(tr), ctypes.byref(fro), _stream(stream)))
+    return tr.value, fro.value
 
 
 def ellpack_gershgorin(H, stream=None):

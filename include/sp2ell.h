@@ -211,7 +211,8 @@ typedef struct sp2_options {
   int32_t max_width;    /* cap on the working width (0 = n); SP2E_OVERFLOW beyond it */
   int32_t spgemm_path;  /* SpGEMM first pass: 0 automatic (column blocks, 4 warps per
                            row for F64, 2 for F32); 1, 2, 4 = column-block accumulator
-                           shared by that many warps per row; 10..12 = per-warp hash
+                           shared by that many warps per row; 3 = column blocks, one
+                           warp per row, two k steps per pass; 10..12 = per-warp hash
                            table of 2^k slots */
   double tau;           /* drop tolerance (default 1e-5) */
   double switch_tol;    /* MIXED: leave the FP32 loop once err_n < switch_tol (0 = automatic:

@@ -719,6 +719,278 @@ __global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
   }
 }
 
+// ------------------------------------------------------------------ super-step variant
+// Same column-block accumulator, one warp per row, but S consecutive k steps form a
+// super-step: the table lookups of all S rows of B are issued together (S*QM independent
+// chains), misses are resolved once, then the S read-modify-write passes run back to
+// back separated only by __syncwarp (consecutive passes may touch the same accumulator).
+// Register slots are predicated instead of specialised, which keeps the code small.
+template <typename T, int QM, int S, bool KEEPZ>
+__global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
+    spgemm_super_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
+                        int use_add, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
+                        int *__restrict__ fb_list, int *__restrict__ fb_count) {
+  using Geo = BlockGeo<T, 1>;
+  constexpr int GW = Geo::GW, GSH = Geo::GSH, G = Geo::G;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned char *base = smem + (size_t)wid * Geo::BYTES_PER_GROUP;
+  T *vals = reinterpret_cast<T *>(base);
+  unsigned *gtab = reinterpret_cast<unsigned *>(base + Geo::VAL_BYTES);
+  int *nblk = reinterpret_cast<int *>(base + Geo::VAL_BYTES + G * 4);
+  const int ncol = Out.n;
+  const unsigned lt = lanemask_lt();
+  int wmax = 0, wover = 0;
+
+  for (int r = blockIdx.x * Geo::GROUPS + wid; r < A.n; r += gridDim.x * Geo::GROUPS) {
+    {
+      const T c = KEEPZ ? untouched<T>() : T(0);
+      for (int i = lane; i < Geo::NB * GW; i += 32) vals[i] = c;
+      for (int i = lane * 4; i < G; i += 128) *reinterpret_cast<uint4 *>(gtab + i) = make_uint4(~0u, ~0u, ~0u, ~0u);
+      if (lane == 0) *nblk = 0;
+    }
+    __syncwarp();
+    bool aborted = false;
+    const int na = min(A.nnz[r], A.w);
+    const int nc = use_add ? min(Add.nnz[r], Add.w) : 0;
+    const int nsteps = na + (use_add ? 1 : 0);  // step 0 is the addend row when use_add
+    const int *arow_i = A.idx + (size_t)r * A.w;
+    const T *arow_v = A.val + (size_t)r * A.w;
+    // A's entries for 32 steps at a time (k, nnz(B_k), alpha*a_ik), next chunk preloaded
+    int ck, cnb, nk_, nnb;
+    T ca, na_;
+    auto load_chunk = [&](int cb, int &kk, int &nbk, T &av) {
+      const int s0 = cb + lane;
+      kk = 0; nbk = 0; av = T(0);
+      if (s0 < na) {
+        const int k = __ldg(arow_i + s0);
+        if ((unsigned)k < (unsigned)B.n) {
+          kk = k;
+          av = alpha * __ldg(arow_v + s0);
+          nbk = min(__ldg(B.nnz + k), B.w);
+        }
+      }
+    };
+    load_chunk(0, ck, cnb, ca);
+    load_chunk(32, nk_, nnb, na_);
+    int cbase = 0;
+    // source row of step t (t in [cbase, cbase+64) for the A part)
+    auto src = [&](int t, const int *&ri, const T *&rv, int &nb, T &a) {
+      if (use_add && t == 0) {
+        ri = Add.idx + (size_t)r * Add.w; rv = Add.val + (size_t)r * Add.w; nb = nc; a = beta;
+        return;
+      }
+      const int ta = t - (use_add ? 1 : 0);
+      int k;
+      if (ta < cbase + 32) {
+        k = __shfl_sync(kFull, ck, ta & 31); nb = __shfl_sync(kFull, cnb, ta & 31); a = __shfl_sync(kFull, ca, ta & 31);
+      } else {
+        k = __shfl_sync(kFull, nk_, ta & 31); nb = __shfl_sync(kFull, nnb, ta & 31); a = __shfl_sync(kFull, na_, ta & 31);
+      }
+      ri = B.idx + (size_t)k * B.w; rv = B.val + (size_t)k * B.w;
+    };
+    int jc[S][QM], jn[S][QM];
+    T vc[S][QM], vn[S][QM];
+    int nbc[S], nbn[S];
+    T ac[S], an[S];
+    const int *ric[S], *rin[S];
+    const T *rvc[S], *rvn[S];
+    auto load_super = [&](int t0, int (&jr)[S][QM], T (&vr)[S][QM], int (&nbr)[S], T (&ar)[S], const int *(&rir)[S],
+                          const T *(&rvr)[S]) {
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        nbr[q] = 0; ar[q] = T(0); rir[q] = B.idx; rvr[q] = B.val;
+        if (t0 + q < nsteps) src(t0 + q, rir[q], rvr[q], nbr[q], ar[q]);
+#pragma unroll
+        for (int u = 0; u < QM; ++u) {
+          const int e = 32 * u + lane;
+          jr[q][u] = e < nbr[q] ? __ldg(rir[q] + e) : -1;
+          vr[q][u] = e < nbr[q] ? __ldg(rvr[q] + e) : T(0);
+        }
+      }
+    };
+    load_super(0, jc, vc, nbc, ac, ric, rvc);
+    for (int t0 = 0; t0 < nsteps && !aborted; t0 += S) {
+      // chunk of A entries: steps t0 .. t0+2S-1 must lie in [cbase, cbase+64)
+      const int ta_next = t0 + S + S - 1 - (use_add ? 1 : 0);
+      if (ta_next >= cbase + 64) {
+        ck = nk_; cnb = nnb; ca = na_;
+        cbase += 32;
+        load_chunk(cbase + 32, nk_, nnb, na_);
+      }
+      load_super(t0 + S, jn, vn, nbn, an, rin, rvn);  // prefetch the next super-step
+      // phase A: every held column of the S rows -> accumulator index
+      int sl[S][QM];
+      unsigned miss = 0;
+#pragma unroll
+      for (int q = 0; q < S; ++q)
+#pragma unroll
+        for (int u = 0; u < QM; ++u) {
+          sl[q][u] = -1;
+          const int j = jc[q][u];
+          if ((unsigned)j < (unsigned)ncol) {
+            const unsigned g = (unsigned)j >> GSH;
+            const unsigned e = ((volatile unsigned *)gtab)[ghash<BlockCfg<T>::LOG2G>(g)];
+            if ((e >> 8) == g) sl[q][u] = (int)(e & 0xFFu) * GW + (j & (GW - 1));
+            else miss |= 1u << (q * QM + u);
+          }
+        }
+      while (__any_sync(kFull, miss != 0)) {
+        const int m = miss ? __ffs(miss) - 1 : -1;
+        int jj = -1;
+#pragma unroll
+        for (int q = 0; q < S; ++q)
+#pragma unroll
+          for (int u = 0; u < QM; ++u)
+            if (m == q * QM + u) jj = jc[q][u];
+        const unsigned act = __ballot_sync(kFull, m >= 0);
+        if (m >= 0) {
+          const unsigned g = (unsigned)jj >> GSH;
+          const unsigned peers = __match_any_sync(act, g);
+          const int leader = __ffs(peers) - 1;
+          int b = -1;
+          if (lane == leader) b = g < Geo::MAX_GROUP ? group_block<T, 1>(gtab, nblk, g) : -1;
+          b = __shfl_sync(peers, b, leader);
+#pragma unroll
+          for (int q = 0; q < S; ++q)
+#pragma unroll
+            for (int u = 0; u < QM; ++u)
+              if (m == q * QM + u) sl[q][u] = b < 0 ? -1 : b * GW + (jj & (GW - 1));
+          if (b < 0) aborted = true;
+          miss &= miss - 1;
+        }
+      }
+      __syncwarp();
+      // phase B: one read-modify-write pass per row of the super-step
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        T old[QM];
+#pragma unroll
+        for (int u = 0; u < QM; ++u) old[u] = sl[q][u] >= 0 ? vals[sl[q][u]] : T(0);
+#pragma unroll
+        for (int u = 0; u < QM; ++u)
+          if (sl[q][u] >= 0) {
+            const T o = (KEEPZ && is_untouched(old[u])) ? T(0) : old[u];
+            vals[sl[q][u]] = fmadd(ac[q], vc[q][u], o);
+          }
+        // entries beyond the registers (rows longer than 32*QM), from memory
+        for (int e0 = 32 * QM; e0 < nbc[q]; e0 += 32) {
+          const int e = e0 + lane;
+          const int j = e < nbc[q] ? __ldg(ric[q] + e) : -1;
+          int slt = -1;
+          if ((unsigned)j < (unsigned)ncol) {
+            const unsigned g = (unsigned)j >> GSH;
+            const unsigned en = ((volatile unsigned *)gtab)[ghash<BlockCfg<T>::LOG2G>(g)];
+            if ((en >> 8) == g) slt = (int)(en & 0xFFu) * GW + (j & (GW - 1));
+          }
+          unsigned tmiss = __ballot_sync(kFull, slt < 0 && (unsigned)j < (unsigned)ncol);
+          if (tmiss & (1u << lane)) {
+            const unsigned g = (unsigned)j >> GSH;
+            const unsigned peers = __match_any_sync(tmiss, g);
+            const int leader = __ffs(peers) - 1;
+            int b = -1;
+            if (lane == leader) b = g < Geo::MAX_GROUP ? group_block<T, 1>(gtab, nblk, g) : -1;
+            b = __shfl_sync(peers, b, leader);
+            slt = b < 0 ? -1 : b * GW + (j & (GW - 1));
+            if (b < 0) aborted = true;
+          }
+          __syncwarp();
+          if (slt >= 0) {
+            const T o0 = vals[slt];
+            const T o = (KEEPZ && is_untouched(o0)) ? T(0) : o0;
+            vals[slt] = fmadd(ac[q], __ldg(rvc[q] + e), o);
+          }
+        }
+        __syncwarp();
+      }
+      aborted = __any_sync(kFull, aborted);
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        nbc[q] = nbn[q]; ac[q] = an[q]; ric[q] = rin[q]; rvc[q] = rvn[q];
+#pragma unroll
+        for (int u = 0; u < QM; ++u) { jc[q][u] = jn[q][u]; vc[q][u] = vn[q][u]; }
+      }
+    }
+    if (aborted) {
+      if (lane == 0) {
+        const int p = atomicAdd(fb_count, 1);
+        fb_list[p] = r;
+      }
+      continue;
+    }
+    // epilogue: groups in order, lane -> column (as in the block kernel)
+    int ng = 0;
+    for (int c = 0; c < G; c += 32) {
+      const unsigned e = gtab[c + lane];
+      const bool used = e != 0xFFFFFFFFu;
+      const unsigned m = __ballot_sync(kFull, used);
+      __syncwarp();
+      if (used) gtab[ng + __popc(m & lt)] = e;
+      ng += __popc(m);
+    }
+    {
+      int P = 32;
+      while (P < ng) P <<= 1;
+      for (int s2 = ng + lane; s2 < P; s2 += 32) gtab[s2] = 0xFFFFFFFFu;
+      __syncwarp();
+      for (int k = 2; k <= P; k <<= 1)
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+          for (int e = lane; e < (P >> 1); e += 32) {
+            const int i = ((e & ~(jj - 1)) << 1) | (e & (jj - 1));
+            const unsigned x = gtab[i], y = gtab[i + jj];
+            if ((x > y) == ((i & k) == 0)) { gtab[i] = y; gtab[i + jj] = x; }
+          }
+          __syncwarp();
+        }
+    }
+    const auto tb = mag_bits(tau);
+    int nk = 0;
+    double dsum = 0.0, fsum = 0.0;
+    int *oi = Out.idx + (size_t)r * Out.w;
+    T *ov = Out.val + (size_t)r * Out.w;
+    constexpr int GPP = 32 / GW;
+    for (int c = 0; c < ng; c += GPP) {
+      const int gi = c + lane / GW;
+      bool keep = false;
+      int j = 0;
+      T v = T(0);
+      if (gi < ng) {
+        const unsigned e = gtab[gi];
+        const int b = (int)(e & 0xFFu);
+        j = (int)((e >> 8) << GSH) + (lane & (GW - 1));
+        v = vals[b * GW + (lane & (GW - 1))];
+        keep = KEEPZ ? !is_untouched(v) : mag_bits(v) > tb;
+      }
+      const unsigned m = __ballot_sync(kFull, keep);
+      if (keep) {
+        const int pos = nk + __popc(m & lt);
+        if (pos < Out.w) { oi[pos] = j; ov[pos] = v; }
+        const double dv = (double)v;
+        if (j == r) dsum += dv;
+        fsum = fma(dv, dv, fsum);
+      }
+      nk += __popc(m);
+    }
+    dsum = warp_sum(dsum);
+    fsum = warp_sum(fsum);
+    wmax = max(wmax, nk);
+    if (lane == 0) {
+      if (nk > Out.w) {
+        ++wover;
+        rowstat[r] = make_double2(0.0, 0.0);
+      } else {
+        Out.nnz[r] = nk;
+        rowstat[r] = make_double2(dsum, fsum);
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (wmax) atomicMax(&ctl->max_count, wmax);
+    if (wover) atomicAdd(&ctl->overflow_rows, wover);
+  }
+}
+
 // ------------------------------------------------------------------ large rows
 // One CTA per deferred row: accumulate into a dense row of n values in global memory
 // (per-CTA slot; marks start at -1 and accumulators at 0 and are restored after use),
@@ -1052,6 +1324,44 @@ int launch_block(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
   return SP2_OK;
 }
 
+template <typename T, int QM, int S, bool KEEPZ>
+int launch_super(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
+  using Geo = BlockGeo<T, 1>;
+  auto kern = spgemm_super_kernel<T, QM, S, KEEPZ>;
+  static bool attr_set[64] = {false};
+  static int occ_cache[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!attr_set[dev]) {
+    SP2_TRY(set_smem(kern, Geo::SMEM));
+    int occ = 0;
+    SP2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Geo::WARPS * 32, Geo::SMEM));
+    occ_cache[dev] = occ < 1 ? 1 : occ;
+    attr_set[dev] = true;
+  }
+  const long long cap = (long long)num_sms() * occ_cache[dev];
+  const long long blocks = ((long long)a.A->n + Geo::GROUPS - 1) / Geo::GROUPS;
+  int grid = (int)(blocks < cap ? blocks : cap);
+  if (grid < 1) grid = 1;
+  const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
+  prof_begin(SP2_PROF_SPGEMM, s);
+  kern<<<grid, Geo::WARPS * 32, Geo::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
+                                               (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, rowstat,
+                                               ctl, fb, fb_count);
+  note_launch();
+  prof_end(SP2_PROF_SPGEMM, s);
+  SP2_CUDA(cudaGetLastError());
+  return SP2_OK;
+}
+
+template <typename T>
+int launch_super_auto(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
+  constexpr int QM = sizeof(T) == 8 ? 6 : 6;
+  return a.tau == 0.0 ? launch_super<T, QM, 2, true>(a, rowstat, ctl, fb, fb_count, s)
+                      : launch_super<T, QM, 2, false>(a, rowstat, ctl, fb, fb_count, s);
+}
+
 // Block first pass with R warps per row; the register slots per warp cover the width of B.
 template <typename T, int R>
 int launch_block_r(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
@@ -1073,6 +1383,7 @@ int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
     case 11: rc = launch_hash<T, 11, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s); break;
     case 12: rc = launch_hash<T, 12, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s); break;
     case 2: rc = launch_block_r<T, 2>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
+    case 3: rc = launch_super_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     default:  // automatic: the row-group size measured fastest on the 3D tight-binding
               // products (FP64 4 warps per row, FP32 2)
       rc = sizeof(T) == 8 ? launch_block_r<T, 4>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)

@@ -209,8 +209,8 @@ typedef struct sp2_options {
   int32_t stall_rule;   /* 1: stop once |trX - trX2| < 0.1 has been seen and err_n >= err_{n-2} */
   int32_t n_fp64_tail;  /* MIXED: minimum FP64 iterations after the switch (default 2) */
   int32_t max_width;    /* cap on the working width (0 = n); SP2E_OVERFLOW beyond it */
-  int32_t spgemm_path;  /* SpGEMM first pass: 0 automatic (column blocks, 4 warps per
-                           row for F64, 2 for F32); 1, 2, 4 = column-block accumulator
+  int32_t spgemm_path;  /* SpGEMM first pass: 0 automatic (column blocks; F64: 4 warps
+                           per row, F32: path 3); 1, 2, 4 = column-block accumulator
                            shared by that many warps per row; 3 = column blocks, one
                            warp per row, two k steps per pass; 10..12 = per-warp hash
                            table of 2^k slots */

@@ -1384,10 +1384,10 @@ int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
     case 12: rc = launch_hash<T, 12, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s); break;
     case 2: rc = launch_block_r<T, 2>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 3: rc = launch_super_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
-    default:  // automatic: the row-group size measured fastest on the 3D tight-binding
-              // products (FP64 4 warps per row, FP32 2)
+    default:  // automatic: the variant measured fastest on the 3D tight-binding products
+              // (FP64: 4 warps per row; FP32: one warp per row, two k steps per pass)
       rc = sizeof(T) == 8 ? launch_block_r<T, 4>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
-                          : launch_block_r<T, 2>(a, rowstat, ctl, fb1, &ctl->n_fallback, s);
+                          : launch_super_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s);
       break;
   }
   if (rc == SP2_OK)

@@ -200,6 +200,7 @@ int sp2_profile_stop(sp2_profile *out);
                                until err_n < switch_tol (or the FP32 loop stalls); then X is
                                promoted to FP64 and at least n_fp64_tail FP64 iterations run,
                                continuing until the FP64 stop rule holds */
+#define SP2_PREC_F32 2      /* the FP32 loop of SP2_PREC_MIXED alone (no FP64 tail) */
 
 #define SP2_STATS_CAP 256   /* per-iteration records kept in sp2_stats */
 
@@ -217,6 +218,9 @@ typedef struct sp2_options {
   double tau;           /* drop tolerance (default 1e-5) */
   double switch_tol;    /* MIXED: leave the FP32 loop once err_n < switch_tol (0 = automatic:
                            max(tol, 1e-6)); the FP32 stall rule also ends it */
+  int32_t graph;        /* sp2_purify_batched: 1 = the loop runs as one CUDA graph with a
+                           conditional WHILE node (default); 0 = host-stepped */
+  int32_t reserved;
 } sp2_options;
 
 typedef struct sp2_stats {
@@ -295,6 +299,24 @@ void sp2_options_default(sp2_options *opt);
  */
 int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2_options *opt, ellpack_t *D,
                sp2_stats *stats, void *stream);
+
+/*
+ * Batched SP2: `count` independent purifications (Hamiltonians of any sizes) in one
+ * device-resident loop.  The matrices are stacked block-diagonally so that every SpGEMM
+ * launch covers all rows of all matrices still running; each matrix keeps its own
+ * traces, branch, stop rule (the rules of sp2_purify) and, in SP2_PREC_MIXED, its own
+ * FP32 -> FP64 switch, all decided on the device.  With opt->graph (default) the loop is
+ * one CUDA graph with a conditional WHILE node, launched once.
+ * H[m]: F64 matrices (host array of descriptors); nocc[m] in (0, H[m].n); tol > 0.
+ * On success D[m] receives a new library-owned F64 matrix each (release with
+ * ellpack_destroy) and stats[m] (optional) the per-iteration record of matrix m.
+ * Returns SP2E_NOTCONV (D still set) if some matrix reached max_iter.  If a row
+ * outgrows the working width the loop restarts wider (stats[m].regrows counts it).
+ * Errors: SP2E_ARG, SP2E_NOMEM, SP2E_CUDA, SP2E_OVERFLOW, SP2E_NONFINITE.  Synchronises
+ * `stream` (NULL: a private stream is used for the graph).
+ */
+int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_t count, double tol, const sp2_options *opt,
+                       ellpack_t *D, sp2_stats *stats, void *stream);
 
 #ifdef __cplusplus
 }

@@ -112,11 +112,23 @@ void launch_reduce_rows(const double2 *rowstat, const int *nnz, int n, const Spg
 // Multiply driver: out = drop_tau(alpha * A*B + beta * Add); Add may be null (beta ignored),
 // may equal A (SP2 update 2X - X^2), or equal out (in-place BLAS form).
 // Writes rowstat (n entries) and fills ctl; does not synchronise.
+// Batched multiplies: the matrices of a batch are stacked as one block-diagonal ELLPACK
+// (columns offset by each matrix's first row); each row reads its matrix's alpha, beta
+// and active flag (rows of inactive matrices are left untouched, rowstat included).
+struct BatchView {
+  const int *row_mat = nullptr;   // per row: matrix id (null: one matrix, scalar alpha/beta)
+  const double *alpha = nullptr;  // per matrix
+  const double *beta = nullptr;   // per matrix (0: no addend)
+  const int *active = nullptr;    // per matrix
+};
+
 struct MultiplyArgs {
   const ellpack_t *A, *B, *Add;
   ellpack_t *Out;
   double alpha, beta, tau;
-  int path;  // first pass: 0 automatic, 1/2/4 column blocks with R warps per row, 10..12 hash table
+  int path;  // first pass: 0 automatic, 1..4 column blocks, 10..12 hash table
+  BatchView bv{};              // per-row coefficients for batched multiplies
+  int *fb_prealloc = nullptr;  // 2*n ints for the deferred-row lists (null: allocated per call)
 };
 int multiply_async(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStream_t s);
 

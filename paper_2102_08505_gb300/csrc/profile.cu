@@ -22,8 +22,20 @@ void note_launch() {
   if (g_on.load(std::memory_order_relaxed)) g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
+// No events while a stream is being captured into a graph (graph bodies of the batched
+// loop may not hold event nodes).
+static bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return st != cudaStreamCaptureStatusNone;
+}
+
 void prof_begin(int cls, cudaStream_t s) {
   if (!g_on.load(std::memory_order_relaxed) || cls < 0 || cls >= SP2_PROF_CLASSES) return;
+  if (capturing(s)) return;
   cudaEvent_t e;
   if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
   cudaEventRecord(e, s);
@@ -32,6 +44,7 @@ void prof_begin(int cls, cudaStream_t s) {
 
 void prof_end(int cls, cudaStream_t s) {
   if (!g_on.load(std::memory_order_relaxed) || cls < 0 || cls >= SP2_PROF_CLASSES || !t_open[cls]) return;
+  if (capturing(s)) return;
   cudaEvent_t e;
   if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
   cudaEventRecord(e, s);

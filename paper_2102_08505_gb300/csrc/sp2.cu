@@ -69,6 +69,8 @@ extern "C" void sp2_options_default(sp2_options *o) {
   o->spgemm_path = 0;
   o->tau = 1e-5;
   o->switch_tol = 0.0;
+  o->graph = 1;
+  o->reserved = 0;
 }
 
 extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2_options *opt_in, ellpack_t *D,
@@ -83,8 +85,12 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   if (!(nocc > 0.0) || !(nocc < (double)n)) return fail(SP2E_ARG, "sp2_purify: nocc=%g must lie in (0, %d)", nocc, n);
   if (!(tol > 0.0) || !isfinite(tol)) return fail(SP2E_ARG, "sp2_purify: tol must be finite and > 0");
   if (!(opt.tau >= 0.0) || !isfinite(opt.tau)) return fail(SP2E_ARG, "sp2_purify: tau must be finite and >= 0");
-  if (opt.precision != SP2_PREC_F64 && opt.precision != SP2_PREC_MIXED)
+  if (opt.precision != SP2_PREC_F64 && opt.precision != SP2_PREC_MIXED && opt.precision != SP2_PREC_F32)
     return fail(SP2E_ARG, "sp2_purify: unknown precision %d", opt.precision);
+  if (opt.precision == SP2_PREC_F32) {  // the FP32 loop alone
+    opt.precision = SP2_PREC_MIXED;
+    opt.n_fp64_tail = 0;
+  }
   if (opt.max_iter < 0 || opt.max_iter + opt.n_fp64_tail >= SP2_STATS_CAP)
     return fail(SP2E_ARG, "sp2_purify: max_iter + n_fp64_tail must be < %d", SP2_STATS_CAP);
   if (opt.n_fp64_tail < 0) return fail(SP2E_ARG, "sp2_purify: n_fp64_tail < 0");

@@ -188,7 +188,7 @@ struct HashCfg {
 template <typename T, int LOG2T, int QM>
 __global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32, 1)
     spgemm_hash_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
-                       int use_add, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
+                       int use_add, BatchView bv, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
                        const int *__restrict__ row_list, const int *__restrict__ row_count,
                        int *__restrict__ fb_list, int *__restrict__ fb_count) {
   using Cfg = HashCfg<T, LOG2T>;
@@ -205,18 +205,27 @@ __global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32, 1)
 
   for (int q = blockIdx.x * Cfg::WARPS + wid; q < nrows; q += nw) {
     const int r = row_list ? row_list[q] : q;
+    T alpha_r = alpha, beta_r = beta;
+    int add_r = use_add;
+    if (bv.row_mat) {
+      const int m = bv.row_mat[r];
+      if (!bv.active[m]) continue;
+      alpha_r = (T)bv.alpha[m];
+      beta_r = (T)bv.beta[m];
+      add_r = beta_r != T(0);
+    }
     for (int s = lane * 4; s < TS; s += 128) *reinterpret_cast<int4 *>(keys + s) = make_int4(-1, -1, -1, -1);
     __syncwarp();
     int ins = 0;
     int bad = 0;
-    if (use_add) {
+    if (add_r) {
       const int nc = min(Add.nnz[r], Add.w);
       for (int s = lane; s < nc; s += 32) {
         const int j = Add.idx[(size_t)r * Add.w + s];
         if ((unsigned)j >= (unsigned)ncol) continue;  // invalid column: ignored, never dereferenced
         const T c = Add.val[(size_t)r * Add.w + s];
         const int h = find_or_insert<LOG2T>(keys, vals, j, ins);
-        if (h >= 0) vals[h] = beta * c; else bad = 1;
+        if (h >= 0) vals[h] = beta_r * c; else bad = 1;
       }
       __syncwarp();
     }
@@ -232,7 +241,7 @@ __global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32, 1)
       if (s < na) {
         kk = __ldg(ai + s);
         if ((unsigned)kk < (unsigned)B.n) {
-          av = alpha * __ldg(avp + s);
+          av = alpha_r * __ldg(avp + s);
           nbk = min(__ldg(B.nnz + kk), B.w);
         } else {
           kk = 0;  // invalid column of A: contributes nothing
@@ -450,7 +459,7 @@ __device__ __forceinline__ bool group_sync_or(int grp, bool pred) {
 template <typename T, int R, int QW, bool KEEPZ>
 __global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
     spgemm_block_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
-                        int use_add, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
+                        int use_add, BatchView bv, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
                         int *__restrict__ fb_list, int *__restrict__ fb_count) {
   using Geo = BlockGeo<T, R>;
   constexpr int GW = Geo::GW, GSH = Geo::GSH, G = Geo::G;
@@ -467,6 +476,15 @@ __global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
   int wmax = 0, wover = 0;
 
   for (int r = blockIdx.x * Geo::GROUPS + grp; r < A.n; r += gridDim.x * Geo::GROUPS) {
+    T alpha_r = alpha, beta_r = beta;
+    int add_r = use_add;
+    if (bv.row_mat) {  // same row for the whole group: every warp takes the same branch
+      const int m = bv.row_mat[r];
+      if (!bv.active[m]) continue;
+      alpha_r = (T)bv.alpha[m];
+      beta_r = (T)bv.beta[m];
+      add_r = beta_r != T(0);
+    }
     {  // clear the blocks and the table
       const T c = KEEPZ ? untouched<T>() : T(0);
       constexpr int PER16 = 16 / (int)sizeof(T);
@@ -498,7 +516,7 @@ __global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
         const int k = __ldg(arow_i + s);
         if ((unsigned)k < (unsigned)B.n) {
           kk = k;
-          av = alpha * __ldg(arow_v + s);
+          av = alpha_r * __ldg(arow_v + s);
           nbk = min(__ldg(B.nnz + k), B.w);
         }
       }
@@ -608,14 +626,14 @@ __global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
     T v0[QW], v1[QW], v2[QW];
     int nb0 = 0, nb1 = 0, nb2 = 0, k0 = 0, k1 = 0, k2 = 0;
     T a0 = T(0), a1 = T(0), a2 = T(0);
-    if (use_add) {
+    if (add_r) {
       const int nc = min(Add.nnz[r], Add.w);
       const int *ci = Add.idx + (size_t)r * Add.w;
       const T *cv = Add.val + (size_t)r * Add.w;
       fetch(ci, cv, nc, j2, v2);
       if (na > 0) fetch_step(0, j0, v0, nb0, a0, k0);
       if (na > 1) fetch_step(1, j1, v1, nb1, a1, k1);
-      step(j2, v2, nc, beta, ci, cv);
+      step(j2, v2, nc, beta_r, ci, cv);
     } else {
       if (na > 0) fetch_step(0, j0, v0, nb0, a0, k0);
       if (na > 1) fetch_step(1, j1, v1, nb1, a1, k1);
@@ -728,7 +746,7 @@ __global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
 template <typename T, int QM, int S, bool KEEPZ>
 __global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
     spgemm_super_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
-                        int use_add, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
+                        int use_add, BatchView bv, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
                         int *__restrict__ fb_list, int *__restrict__ fb_count) {
   using Geo = BlockGeo<T, 1>;
   constexpr int GW = Geo::GW, GSH = Geo::GSH, G = Geo::G;
@@ -743,6 +761,15 @@ __global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
   int wmax = 0, wover = 0;
 
   for (int r = blockIdx.x * Geo::GROUPS + wid; r < A.n; r += gridDim.x * Geo::GROUPS) {
+    T alpha_r = alpha, beta_r = beta;
+    int add_r = use_add;
+    if (bv.row_mat) {
+      const int m = bv.row_mat[r];
+      if (!bv.active[m]) continue;
+      alpha_r = (T)bv.alpha[m];
+      beta_r = (T)bv.beta[m];
+      add_r = beta_r != T(0);
+    }
     {
       const T c = KEEPZ ? untouched<T>() : T(0);
       for (int i = lane; i < Geo::NB * GW; i += 32) vals[i] = c;
@@ -752,8 +779,8 @@ __global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
     __syncwarp();
     bool aborted = false;
     const int na = min(A.nnz[r], A.w);
-    const int nc = use_add ? min(Add.nnz[r], Add.w) : 0;
-    const int nsteps = na + (use_add ? 1 : 0);  // step 0 is the addend row when use_add
+    const int nc = add_r ? min(Add.nnz[r], Add.w) : 0;
+    const int nsteps = na + (add_r ? 1 : 0);  // step 0 is the addend row, if any
     const int *arow_i = A.idx + (size_t)r * A.w;
     const T *arow_v = A.val + (size_t)r * A.w;
     // A's entries for 32 steps at a time (k, nnz(B_k), alpha*a_ik), next chunk preloaded
@@ -766,7 +793,7 @@ __global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
         const int k = __ldg(arow_i + s0);
         if ((unsigned)k < (unsigned)B.n) {
           kk = k;
-          av = alpha * __ldg(arow_v + s0);
+          av = alpha_r * __ldg(arow_v + s0);
           nbk = min(__ldg(B.nnz + k), B.w);
         }
       }
@@ -776,11 +803,11 @@ __global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
     int cbase = 0;
     // source row of step t (t in [cbase, cbase+64) for the A part)
     auto src = [&](int t, const int *&ri, const T *&rv, int &nb, T &a) {
-      if (use_add && t == 0) {
-        ri = Add.idx + (size_t)r * Add.w; rv = Add.val + (size_t)r * Add.w; nb = nc; a = beta;
+      if (add_r && t == 0) {
+        ri = Add.idx + (size_t)r * Add.w; rv = Add.val + (size_t)r * Add.w; nb = nc; a = beta_r;
         return;
       }
-      const int ta = t - (use_add ? 1 : 0);
+      const int ta = t - (add_r ? 1 : 0);
       int k;
       if (ta < cbase + 32) {
         k = __shfl_sync(kFull, ck, ta & 31); nb = __shfl_sync(kFull, cnb, ta & 31); a = __shfl_sync(kFull, ca, ta & 31);
@@ -812,7 +839,7 @@ __global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
     load_super(0, jc, vc, nbc, ac, ric, rvc);
     for (int t0 = 0; t0 < nsteps && !aborted; t0 += S) {
       // chunk of A entries: steps t0 .. t0+2S-1 must lie in [cbase, cbase+64)
-      const int ta_next = t0 + S + S - 1 - (use_add ? 1 : 0);
+      const int ta_next = t0 + S + S - 1 - (add_r ? 1 : 0);
       if (ta_next >= cbase + 64) {
         ck = nk_; cnb = nnb; ca = na_;
         cbase += 32;
@@ -1018,7 +1045,7 @@ __device__ __forceinline__ int block_exclusive_scan_ballot(bool flag, int *s_war
 template <typename T>
 __global__ void __launch_bounds__(kDenseThreads)
     spgemm_dense_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
-                        int use_add, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
+                        int use_add, BatchView bv, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
                         const int *__restrict__ fb_list, const int *__restrict__ fb_count, T *__restrict__ acc_all,
                         int *__restrict__ mark_all) {
   __shared__ int s_warp[kDenseThreads / 32];
@@ -1031,13 +1058,21 @@ __global__ void __launch_bounds__(kDenseThreads)
   int lmax = 0, lover = 0;
   for (int q = blockIdx.x; q < nfb; q += gridDim.x) {
     const int r = fb_list[q];
-    if (use_add) {
+    T alpha_r = alpha, beta_r = beta;
+    int add_r = use_add;
+    if (bv.row_mat) {  // deferred rows belong to active matrices
+      const int m = bv.row_mat[r];
+      alpha_r = (T)bv.alpha[m];
+      beta_r = (T)bv.beta[m];
+      add_r = beta_r != T(0);
+    }
+    if (add_r) {
       const int nc = min(Add.nnz[r], Add.w);
       for (int s = threadIdx.x; s < nc; s += blockDim.x) {
         const int j = Add.idx[(size_t)r * Add.w + s];
         if ((unsigned)j >= (unsigned)n) continue;
         mark[j] = 1;
-        acc[j] += beta * Add.val[(size_t)r * Add.w + s];
+        acc[j] += beta_r * Add.val[(size_t)r * Add.w + s];
       }
     }
     __syncthreads();
@@ -1047,7 +1082,7 @@ __global__ void __launch_bounds__(kDenseThreads)
     for (int t = 0; t < na; ++t) {
       const int k = A.idx[(size_t)r * A.w + t];
       if ((unsigned)k < (unsigned)B.n) {
-        const T a = alpha * A.val[(size_t)r * A.w + t];
+        const T a = alpha_r * A.val[(size_t)r * A.w + t];
         const int nb = min(B.nnz[k], B.w);
         for (int s = threadIdx.x; s < nb; s += blockDim.x) {
           const int j = B.idx[(size_t)k * B.w + s];
@@ -1285,8 +1320,8 @@ int launch_hash(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, const i
   const int cls = row_list ? SP2_PROF_LARGE : SP2_PROF_SPGEMM;
   prof_begin(cls, s);
   kern<<<grid, Cfg::WARPS * 32, Cfg::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
-                                               (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, rowstat,
-                                               ctl, row_list, row_count, fb, fb_count);
+                                               (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv,
+                                               rowstat, ctl, row_list, row_count, fb, fb_count);
   note_launch();
   prof_end(cls, s);
   SP2_CUDA(cudaGetLastError());
@@ -1316,8 +1351,8 @@ int launch_block(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
   const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
   prof_begin(SP2_PROF_SPGEMM, s);
   kern<<<grid, Geo::WARPS * 32, Geo::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
-                                               (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, rowstat,
-                                               ctl, fb, fb_count);
+                                               (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv,
+                                               rowstat, ctl, fb, fb_count);
   note_launch();
   prof_end(SP2_PROF_SPGEMM, s);
   SP2_CUDA(cudaGetLastError());
@@ -1347,8 +1382,8 @@ int launch_super(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
   const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
   prof_begin(SP2_PROF_SPGEMM, s);
   kern<<<grid, Geo::WARPS * 32, Geo::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
-                                               (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, rowstat,
-                                               ctl, fb, fb_count);
+                                               (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv,
+                                               rowstat, ctl, fb, fb_count);
   note_launch();
   prof_end(SP2_PROF_SPGEMM, s);
   SP2_CUDA(cudaGetLastError());
@@ -1398,8 +1433,8 @@ int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
 template <typename T>
 int multiply_t(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStream_t s) {
   const int n = a.A->n;
-  int *fb = nullptr;
-  SP2_TRY(dev_alloc((void **)&fb, 2 * sizeof(int) * (size_t)n, s));
+  int *fb = a.fb_prealloc;
+  if (!fb) SP2_TRY(dev_alloc((void **)&fb, 2 * sizeof(int) * (size_t)n, s));
   int *fb1 = fb, *fb2 = fb + n;
   const int qm_need = (a.B->width + 31) / 32;
   int rc = qm_need <= 4 ? launch_bins<T, 4>(a, rowstat, ctl, fb1, fb2, a.path, s)
@@ -1415,13 +1450,13 @@ int multiply_t(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStre
       const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
       spgemm_dense_kernel<T><<<slots, kDenseThreads, 0, s>>>(
           view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha, (T)a.beta, (T)a.tau,
-          a.Add != nullptr && a.beta != 0.0, rowstat, ctl, fb2, &ctl->n_fallback2, (T *)acc, mark);
+          a.Add != nullptr && a.beta != 0.0, a.bv, rowstat, ctl, fb2, &ctl->n_fallback2, (T *)acc, mark);
       note_launch();
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) rc = cuda_fail(e, "spgemm_dense_kernel", __FILE__, __LINE__);
     }
   }
-  dev_free(fb, s);
+  if (!a.fb_prealloc) dev_free(fb, s);
   return rc;
 }
 

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libsp2ell.so")
 SP2_OK = 0
 SP2E_ARG, SP2E_OVERFLOW, SP2E_NOMEM, SP2E_CUDA, SP2E_NOTCONV, SP2E_NONFINITE, SP2E_TIMEOUT = -1, -2, -3, -4, -5, -6, -7
 SP2_F64, SP2_F32 = 0, 1
-SP2_PREC_F64, SP2_PREC_MIXED = 0, 1
+SP2_PREC_F64, SP2_PREC_MIXED, SP2_PREC_F32 = 0, 1, 2
 SP2_STATS_CAP = 256
 _CODES = {0: "SP2_OK", -1: "SP2E_ARG", -2: "SP2E_OVERFLOW", -3: "SP2E_NOMEM", -4: "SP2E_CUDA",
           -5: "SP2E_NOTCONV", -6: "SP2E_NONFINITE", -7: "SP2E_TIMEOUT"}
@@ -38,7 +38,8 @@ class ellpack_t(ctypes.Structure):
 class sp2_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("stall_rule", ctypes.c_int32),
                 ("n_fp64_tail", ctypes.c_int32), ("max_width", ctypes.c_int32), ("spgemm_path", ctypes.c_int32),
-                ("tau", ctypes.c_double), ("switch_tol", ctypes.c_double)]
+                ("tau", ctypes.c_double), ("switch_tol", ctypes.c_double), ("graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class sp2_stats(ctypes.Structure):
@@ -92,6 +93,7 @@ def _load():
         "sp2_options_default": ([P(sp2_options)], None),
         "sp2_purify": ([E, D, D, P(sp2_options), E, P(sp2_stats), V], ctypes.c_int),
         "sp2_x0": ([E, D, E, P(D), P(D), V], ctypes.c_int),
+        "sp2_purify_batched": ([E, P(D), I, D, P(sp2_options), E, P(sp2_stats), V], ctypes.c_int),
         "sp2_profile_start": ([], ctypes.c_int),
         "sp2_profile_stop": ([P(sp2_profile)], ctypes.c_int),
         "sp2_step": ([E, E, D, D, P(sp2_step_info), V], ctypes.c_int),
@@ -358,3 +360,20 @@ def sp2_profile_stop():
     for i, name in enumerate(PROF_NAMES):
         out[name] = (int(p.count[i]), float(p.total_ms[i]))
     return out
+
+
+def sp2_purify_batched(Hs, noccs, tol, options=None, stream=None, allow_notconv=False):
+    """Batched SP2 of the matrices Hs (Ellpack, F64); returns ([D as OwnedEllpack], [stats])."""
+    count = len(Hs)
+    opt = options if options is not None else sp2_options_default()
+    harr = (ellpack_t * count)(*[h.desc for h in Hs])
+    narr = (ctypes.c_double * count)(*[float(x) for x in noccs])
+    darr = (ellpack_t * count)()
+    sarr = (sp2_stats * count)()
+    rc = lib.sp2_purify_batched(harr, narr, count, float(tol), ctypes.byref(opt), darr, sarr, _stream(stream))
+    Ds = [OwnedEllpack(darr[m]) for m in range(count)]
+    for m in range(count):  # the descriptors now belong to the OwnedEllpack objects
+        darr[m].owner = 0
+    if not (rc == SP2E_NOTCONV and allow_notconv):
+        _check(rc)
+    return Ds, [stats_dict(sarr[m]) for m in range(count)]

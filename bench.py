@@ -41,6 +41,10 @@ def parse():
     p.add_argument("--tau", type=float, default=1e-6)
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--workload", default="spgemm", choices=["spgemm", "sp2", "batched"],
+                   help="spgemm: one SP2 iteration at N=262144 (default); sp2: whole purifications, FP64 vs "
+                        "mixed at N=131072; batched: 256 clusters in one graph launch vs one by one")
+    p.add_argument("--count", type=int, default=256)
     p.add_argument("--path", type=int, default=0,
                    help="SpGEMM first pass: 0 automatic, 1/2/4 column blocks with R warps per row, 10-12 hash")
     p.add_argument("--no-e2e", action="store_true")
@@ -383,10 +387,100 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def diff_fro(S, D1, D2):
+    """||D1 - D2||_F through the library (ellpack_add on a copy, then the norm)."""
+    A = D1.to_torch()
+    w = A.width + D2.width
+    Aw = S.Ellpack.empty(A.n, w, S.SP2_F64)
+    S.ellpack_copy(A, Aw)
+    S.ellpack_add(Aw, D2.to_torch(), 1.0, -1.0, 0.0)
+    return float(np.sqrt(S.ellpack_frobenius2(Aw)))
+
+
+def run_sp2(a):
+    """Whole SP2 purifications of a gapped 3D tight-binding H (A/B onsite splitting 10):
+    FP64 against mixed precision, time to solution and distance between the results."""
+    import torch
+    from paper_2102_08505_gb300 import inputs as I
+    from paper_2102_08505_gb300 import sp2ell as S
+    n = a.n
+    tau = a.tau if a.tau != 1e-6 else 1e-5
+    idx, val, nnz = I.tight_binding(n, seed=a.seed, delta=10.0)
+    H = S.Ellpack.from_numpy(idx, val, nnz)
+    out = {}
+    Ds = {}
+    for name, prec in (("f64", S.SP2_PREC_F64), ("mixed", S.SP2_PREC_MIXED)):
+        opt = S.sp2_options_default(tau=tau, precision=prec, spgemm_path=a.path)
+        for _ in range(max(1, a.warmup)):
+            S.sp2_purify(H, n / 2, 1e-10, opt)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(max(1, a.steps)):
+            t0 = time.perf_counter()
+            D, st = S.sp2_purify(H, n / 2, 1e-10, opt)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        Ds[name] = D
+        out[name] = {"time_s": float(np.median(times)), "iterations": st["iterations"],
+                     "fp32_iterations": st["fp32_iterations"], "status": st["status"],
+                     "iters_per_s": st["iterations"] / float(np.median(times)),
+                     "final_err": float(st["err"][-1]), "nnz_per_row": float(st["nnz_total"][-1]) / n}
+    dD = diff_fro(S, Ds["mixed"], Ds["f64"]) / np.sqrt(n)
+    tr = S.ellpack_trace(Ds["mixed"].to_torch())
+    line = {"workload": "sp2 time to solution, 3D tight-binding gapped N=%d tau=%g tol=1e-10" % (n, tau),
+            "f64": out["f64"], "mixed": out["mixed"], "speedup_mixed_vs_f64": out["f64"]["time_s"] / out["mixed"]["time_s"],
+            "dD_fro_over_sqrtN": dD, "mixed_trace_error": abs(tr - n / 2)}
+    print(json.dumps(line), flush=True)
+
+
+def run_batched(a):
+    """256 gapped open 3D clusters with N log-uniform in [512, 8192]: one graph-captured
+    batched launch (mixed and FP64) against the same matrices purified one by one."""
+    import torch
+    from paper_2102_08505_gb300 import inputs as I
+    from paper_2102_08505_gb300 import sp2ell as S
+    sizes = I.cluster_sizes(a.count, 512, 8192, seed=a.seed)
+    tau = 1e-5
+    Hs = []
+    for m, n in enumerate(sizes):
+        idx, val, nnz = I.tight_binding(int(n), seed=a.seed + m, delta=10.0, periodic=False)
+        Hs.append(S.Ellpack.from_numpy(idx, val, nnz))
+    noccs = [h.n // 2 for h in Hs]
+    res = {}
+    for name, prec, graph in (("batched_mixed_graph", S.SP2_PREC_MIXED, 1), ("batched_f64_graph", S.SP2_PREC_F64, 1),
+                              ("batched_mixed_host", S.SP2_PREC_MIXED, 0)):
+        opt = S.sp2_options_default(tau=tau, precision=prec, graph=graph, spgemm_path=a.path)
+        S.sp2_purify_batched(Hs, noccs, 1e-10, opt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Ds, sts = S.sp2_purify_batched(Hs, noccs, 1e-10, opt)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res[name] = {"time_s": dt, "iterations_total": int(sum(s["iterations"] for s in sts)),
+                     "max_iterations": int(max(s["iterations"] for s in sts))}
+    opt = S.sp2_options_default(tau=tau, precision=S.SP2_PREC_F64, spgemm_path=a.path)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its = 0
+    for H, nocc in zip(Hs, noccs):
+        D, st = S.sp2_purify(H, nocc, 1e-10, opt)
+        its += st["iterations"]
+    torch.cuda.synchronize()
+    res["one_by_one_f64"] = {"time_s": time.perf_counter() - t0, "iterations_total": its}
+    line = {"workload": "batched SP2: %d gapped open 3D clusters, N log-uniform [512, 8192], sum N = %d" % (
+        len(Hs), int(sizes.sum())), **res,
+        "speedup_batched_mixed_vs_one_by_one_f64": res["one_by_one_f64"]["time_s"] / res["batched_mixed_graph"]["time_s"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "sp2":
+        run_sp2(a)
+    elif a.workload == "batched":
+        run_batched(a)
     else:
         run_ours(a)
 

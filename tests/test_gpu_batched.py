@@ -32,7 +32,7 @@ def test_batched_f64_matches_oracle(gpu, graph):
     tau, tol = 1e-5, 1e-10
     mats = batch()
     Hs = [S.Ellpack.from_numpy(m.idx, m.val, m.nnz) for m in mats]
-    noccs = [m.n // 2 for m in mats]
+    noccs = [(m.n + 1) // 2 for m in mats]  # the lower (A) band holds ceil(n/2) states: nocc fills it
     Ds, sts = S.sp2_purify_batched(Hs, noccs, tol, S.sp2_options_default(tau=tau, graph=graph))
     for m, H, D, st in zip(range(len(mats)), mats, Ds, sts):
         Do, so = O.sp2(H, noccs[m], tol, tau)
@@ -48,7 +48,7 @@ def test_batched_mixed_within_1e5_of_oracle(gpu):
     tau, tol = 1e-5, 1e-10
     mats = batch(10)
     Hs = [S.Ellpack.from_numpy(m.idx, m.val, m.nnz) for m in mats]
-    noccs = [m.n // 2 for m in mats]
+    noccs = [(m.n + 1) // 2 for m in mats]  # the lower (A) band holds ceil(n/2) states: nocc fills it
     Ds, sts = S.sp2_purify_batched(Hs, noccs, tol, S.sp2_options_default(tau=tau, precision=S.SP2_PREC_MIXED))
     for m, H, D, st in zip(range(len(mats)), mats, Ds, sts):
         Do, so = O.sp2(H, noccs[m], tol, tau)
@@ -63,7 +63,7 @@ def test_batched_matches_single_matrix_runs(gpu):
     tau, tol = 1e-5, 1e-10
     mats = batch(20)[:3]
     Hs = [S.Ellpack.from_numpy(m.idx, m.val, m.nnz) for m in mats]
-    noccs = [m.n // 2 for m in mats]
+    noccs = [(m.n + 1) // 2 for m in mats]  # the lower (A) band holds ceil(n/2) states: nocc fills it
     for prec in (S.SP2_PREC_F64, S.SP2_PREC_F32):
         opt = S.sp2_options_default(tau=tau, precision=prec)
         Ds, sts = S.sp2_purify_batched(Hs, noccs, tol, opt)
@@ -78,7 +78,7 @@ def test_batched_regrows_when_width_is_too_small(gpu):
     tau, tol = 1e-5, 1e-10
     mats = batch(30)[:2]
     Hs = [S.Ellpack.from_numpy(m.idx, m.val, m.nnz) for m in mats]
-    noccs = [m.n // 2 for m in mats]
+    noccs = [(m.n + 1) // 2 for m in mats]  # the lower (A) band holds ceil(n/2) states: nocc fills it
     Ds, sts = S.sp2_purify_batched(Hs, noccs, tol, S.sp2_options_default(tau=tau, max_width=64))
     assert sts[0]["regrows"] >= 1
     for m, H, D in zip(range(2), mats, Ds):

@@ -41,9 +41,10 @@ def parse():
     p.add_argument("--tau", type=float, default=1e-6)
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--workload", default="spgemm", choices=["spgemm", "sp2", "batched"],
+    p.add_argument("--workload", default="spgemm", choices=["spgemm", "sp2", "batched", "sizing"],
                    help="spgemm: one SP2 iteration at N=262144 (default); sp2: whole purifications, FP64 vs "
-                        "mixed at N=131072; batched: 256 clusters in one graph launch vs one by one")
+                        "mixed at N=131072; batched: 256 clusters in one graph launch vs one by one; sizing: "
+                        "heuristic vs structural vs MLP output widths for mixed SP2 at N=1048576")
     p.add_argument("--count", type=int, default=256)
     p.add_argument("--path", type=int, default=0,
                    help="SpGEMM first pass: 0 automatic, 1/2/4 column blocks with R warps per row, 10-12 hash")
@@ -473,6 +474,62 @@ def run_batched(a):
     print(json.dumps(line), flush=True)
 
 
+def run_sizing(a):
+    """Output sizing of the SP2 products: heuristic widths with regrow, exact structural
+    counts before every multiply, and the row-length MLP (trained on about 50k rows of
+    SP2 products of gapped 3D Hamiltonians of 4096 .. 16384 sites), each used for a mixed
+    precision SP2 run on a gapped 3D tight-binding H of N=1048576 sites (input width 128)."""
+    import torch
+    from paper_2102_08505_gb300 import inputs as I
+    from paper_2102_08505_gb300 import learned
+    from paper_2102_08505_gb300 import sp2ell as S
+    n = a.n if a.n != 262144 else 1048576
+    tau = a.tau if a.tau != 1e-6 else 1e-5
+    t0 = time.perf_counter()
+    feat, counts = learned.default_training_set(seed=100 + a.seed, rows=50000, tau=tau, dtype=S.SP2_F32)
+    torch.cuda.synchronize()
+    t_collect = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pred, loss = learned.train(feat, counts, seed=a.seed, steps=1500, batch=2048, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    idx, val, nnz = I.tight_binding(n, seed=a.seed, delta=10.0)
+    w0 = max(128, ((int(nnz.max()) + 31) // 32) * 32)
+    pad_i = np.zeros((n, w0), np.int32)
+    pad_v = np.full((n, w0), np.nan)
+    pad_i[:, :idx.shape[1]] = idx
+    pad_v[:, :idx.shape[1]] = val
+    H = S.Ellpack.from_numpy(pad_i, pad_v, nnz)
+    res, Ds = {}, {}
+    for mode, name in ((0, "heuristic"), (1, "structural"), (2, "mlp")):
+        kw = dict(tau=tau, precision=S.SP2_PREC_MIXED, sizing=mode, spgemm_path=a.path)
+        if mode == 2:
+            kw["predictor"] = pred
+        opt = S.sp2_options_default(**kw)
+        for _ in range(max(1, min(a.warmup, 2))):
+            S.sp2_purify(H, n / 2, 1e-10, opt)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(max(1, min(a.steps, 3))):
+            t0 = time.perf_counter()
+            D, st = S.sp2_purify(H, n / 2, 1e-10, opt)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        Ds[name] = D
+        res[name] = {"time_s": float(np.median(times)), "iterations": st["iterations"], "status": st["status"],
+                     "width_max": st["width_max"], "regrows": st["regrows"], "struct_passes": st["struct_passes"],
+                     "peak_product_bytes": int(st["width_max"]) * n * 12}
+        if mode == 2:
+            res[name].update({"pred_log_mae": st["pred_log_mae"], "pred_under_frac": st["pred_under_frac"]})
+    line = {"workload": "SP2 output sizing, 3D tight-binding gapped N=%d tau=%g mixed precision" % (n, tau),
+            "training": {"rows": int(counts.shape[0]), "collect_s": t_collect, "train_s": t_train,
+                         "final_batch_loss": loss},
+            **res,
+            "dD_mlp_vs_heuristic": diff_fro(S, Ds["mlp"], Ds["heuristic"]) / np.sqrt(n),
+            "dD_structural_vs_heuristic": diff_fro(S, Ds["structural"], Ds["heuristic"]) / np.sqrt(n)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -481,6 +538,8 @@ def main():
         run_sp2(a)
     elif a.workload == "batched":
         run_batched(a)
+    elif a.workload == "sizing":
+        run_sizing(a)
     else:
         run_ours(a)
 

@@ -193,6 +193,68 @@ int sp2_profile_start(void);
  * Errors: SP2E_CUDA. */
 int sp2_profile_stop(sp2_profile *out);
 
+/* ---------------------------------------------------------------- learned sizing */
+/*
+ * Exact structural row counts of A*B (+ C when C is not NULL): counts[i] =
+ * |union over k in cols(A_i) of cols(B_k)| (union cols(C_i)), an upper bound of the
+ * post-threshold length of row i of the product.  counts: device int32[n];
+ * max_count (optional, host) receives the largest.  A row whose columns fall in more than
+ * 512 groups of 32 reports min(n, sum of the lengths of the rows it gathers) instead
+ * (still an upper bound).  Synchronises `stream`.
+ */
+int ellpack_struct_count(const ellpack_t *A, const ellpack_t *B, const ellpack_t *C, int32_t *counts,
+                         int32_t *max_count, void *stream);
+
+#define NNZPRED_NPARAMS 5313  /* 16*64 + 64 + 64*64 + 64 + 64 + 1 */
+#define NNZPRED_NSTATS 34     /* feature means[16], feature stds[16], target mean, target std */
+
+/* A small MLP (16 -> 64 -> 64 -> 1, ReLU, FP32) predicting log1p of the post-threshold
+ * length of each row of the next SP2 product from features of the current X. */
+typedef struct nnzpred_t {
+  float *params;   /* device: W1[64][16], b1[64], W2[64][64], b2[64], w3[64], b3 */
+  float *adam_m;   /* device: Adam first moments  [NNZPRED_NPARAMS] */
+  float *adam_v;   /* device: Adam second moments [NNZPRED_NPARAMS] */
+  float *stats;    /* device: standardisation statistics [NNZPRED_NSTATS] */
+  int64_t steps;   /* optimiser steps taken */
+} nnzpred_t;
+
+/*
+ * Features of every row i of X (device float[n*16], row-major) for the product that the
+ * SP2 step with `branch` (1 X^2, 2 2X - X^2) and drop tolerance tau will compute:
+ *  0 log1p nnz_i, 1 log1p sum_k nnz_k, 2 log1p max_k nnz_k, 3 log1p min_k nnz_k,
+ *  4 log10 max_k|x_ik|, 5 log10 ||x_i||_2, 6 log10 sum_k|x_ik|, 7 log10 |x_ii|,
+ *  8 log10 sum_k |x_ik| max_j|x_kj|, 9 log1p #{|x_ik| > 10 tau}, 10 log1p #{|x_ik| > 100 tau},
+ *  11 log10 tau, 12 branch == 2, 13 log1p (sum_k |x_ik| nnz_k / sum_k |x_ik|), 14 one, 15 zero
+ * (k over the stored entries of row i).  Asynchronous.
+ */
+int nnzpred_features(const ellpack_t *X, double tau, int32_t branch, float *feat, void *stream);
+
+/* Allocates the predictor (device) and initialises its weights from `seed` (uniform
+ * +-sqrt(6/fan_in), biases 0, identity statistics).  Synchronises `stream`. */
+int nnzpred_create(nnzpred_t *p, uint64_t seed, void *stream);
+int nnzpred_destroy(nnzpred_t *p, void *stream);
+
+/* Standardisation statistics from a training set: features feat[n*16] and exact row
+ * lengths count[n] (device); the model works on standardised log1p(count). */
+int nnzpred_set_stats(nnzpred_t *p, const float *feat, const int32_t *count, int64_t n, void *stream);
+
+/* Gradient of the mean squared error over the n samples into grad[NNZPRED_NPARAMS]
+ * (device) and the loss into *loss (host, optional).  Synchronises `stream`. */
+int nnzpred_grad(const nnzpred_t *p, const float *feat, const int32_t *count, int64_t n, float *grad, float *loss,
+                 void *stream);
+
+/* `steps` Adam steps (lr, betas 0.9/0.999) on mini-batches of `batch` samples drawn by a
+ * counter-based hash; *final_loss (host, optional) = loss of the last batch. */
+int nnzpred_train(nnzpred_t *p, const float *feat, const int32_t *count, int64_t n, int32_t steps, int32_t batch,
+                  float lr, float *final_loss, void *stream);
+
+/* Predicted row lengths pred[n] (device float) from feat[n*16].  Asynchronous. */
+int nnzpred_predict(const nnzpred_t *p, const float *feat, int64_t n, float *pred, void *stream);
+
+/* Weights and statistics to / from a file. */
+int nnzpred_save(const nnzpred_t *p, const char *path, void *stream);
+int nnzpred_load(nnzpred_t *p, const char *path, void *stream);
+
 /* ---------------------------------------------------------------- SP2 */
 
 #define SP2_PREC_F64 0      /* every step in FP64 */
@@ -220,7 +282,11 @@ typedef struct sp2_options {
                            max(tol, 1e-6)); the FP32 stall rule also ends it */
   int32_t graph;        /* sp2_purify_batched: 1 = the loop runs as one CUDA graph with a
                            conditional WHILE node (default); 0 = host-stepped */
-  int32_t reserved;
+  int32_t sizing;       /* sp2_purify output widths: 0 heuristic (4x the longest row of X,
+                           regrow on overflow), 1 exact structural counts before every
+                           multiply, 2 1.1 x the predictor's longest row + 16 (after an
+                           overflow the multiply is repeated at the exact width it counted) */
+  const nnzpred_t *predictor;  /* for sizing 2 */
 } sp2_options;
 
 typedef struct sp2_stats {
@@ -228,6 +294,10 @@ typedef struct sp2_stats {
   int32_t status;                       /* 0 err < tol, 1 stall rule, 2 max_iter */
   int32_t fp32_iterations;              /* MIXED: updates made in FP32 */
   int32_t regrows;                      /* multiplies repeated after a width overflow */
+  int32_t struct_passes;                /* structural-count passes run */
+  int32_t width_max;                    /* largest output width used */
+  double pred_log_mae;                  /* sizing 2: mean |log1p(pred) - log1p(actual)| per row */
+  double pred_under_frac;               /* sizing 2: fraction of rows longer than predicted */
   double emin, emax;                    /* Gershgorin bounds */
   double time_ms;                       /* wall time of the call */
   double trX[SP2_STATS_CAP];            /* per visited X_n (n = 0..iterations) */

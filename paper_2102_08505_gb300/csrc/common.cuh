@@ -153,4 +153,14 @@ int convert_async(const ellpack_t *src, ellpack_t *dst, cudaStream_t s, int *ove
 // Copies src into dst (same dtype; dst->width >= src row lengths; rows copied as is).
 int copy_async(const ellpack_t *src, ellpack_t *dst, cudaStream_t s);
 
+// Learned sizing (nnzpred.cu): structural counts of A*B (+C) into counts[n] with their
+// maximum in *dmax (device); row features; predicted row lengths; prediction error
+// {sum |log1p(pred) - log1p(actual)|, rows above prediction} into out2[2]; max of v.
+int struct_count_async(const ellpack_t *A, const ellpack_t *B, const ellpack_t *C, int *counts, int *dmax,
+                       cudaStream_t s);
+int features_async(const ellpack_t *X, double tau, int branch, float *rmax_scratch, float *feat, cudaStream_t s);
+int predict_async(const nnzpred_t *p, const float *feat, long long n, float *pred, cudaStream_t s);
+int pred_error_async(const float *pred, const int *actual, long long n, double *out2, cudaStream_t s);
+int max_float_async(const float *v, long long n, float *out, cudaStream_t s);
+
 }  // namespace sp2

@@ -24,6 +24,7 @@ struct Buffers {
   SpgemmCtl *ctl = nullptr;
   StepResult *dres = nullptr;
   double *bounds = nullptr;
+  void *sizing = nullptr;  // counts, maxima, features, predictions (sizing modes 1 and 2)
   ellpack_t X{}, Y{}, Hf{};
   bool hf_owned = false;
   ~Buffers() {
@@ -31,6 +32,7 @@ struct Buffers {
     dev_free(ctl, s);
     dev_free(dres, s);
     dev_free(bounds, s);
+    dev_free(sizing, s);
     if (X.owner) ellpack_destroy(&X, s);
     if (Y.owner) ellpack_destroy(&Y, s);
     if (hf_owned) ellpack_destroy(&Hf, s);
@@ -70,7 +72,8 @@ extern "C" void sp2_options_default(sp2_options *o) {
   o->tau = 1e-5;
   o->switch_tol = 0.0;
   o->graph = 1;
-  o->reserved = 0;
+  o->sizing = 0;
+  o->predictor = nullptr;
 }
 
 extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2_options *opt_in, ellpack_t *D,
@@ -97,6 +100,9 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   if (!valid_path(opt.spgemm_path)) return fail(SP2E_ARG, "sp2_purify: spgemm_path must be 0..4 or 10..12");
   const int max_w = (opt.max_width > 0 && opt.max_width < n) ? opt.max_width : n;
   if (!(opt.switch_tol >= 0.0) || !isfinite(opt.switch_tol)) return fail(SP2E_ARG, "sp2_purify: bad switch_tol");
+  if (opt.sizing < 0 || opt.sizing > 2) return fail(SP2E_ARG, "sp2_purify: sizing must be 0, 1 or 2");
+  if (opt.sizing == 2 && (!opt.predictor || !opt.predictor->params))
+    return fail(SP2E_ARG, "sp2_purify: sizing 2 needs a created predictor");
   const double switch_tol = opt.switch_tol > 0.0 ? opt.switch_tol : (tol > 1e-6 ? tol : 1e-6);
 
   Buffers b;
@@ -109,6 +115,32 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   SP2_TRY(dev_alloc((void **)&b.ctl, sizeof(SpgemmCtl), s));
   SP2_TRY(dev_alloc((void **)&b.dres, sizeof(StepResult), s));
   SP2_TRY(dev_alloc((void **)&b.bounds, 2 * sizeof(double), s));
+  // sizing scratch: counts int[n], max int, pred error double[2], max float, rmax float[n],
+  // pred float[n], features float[16n]
+  int *sz_counts = nullptr, *sz_dmax = nullptr;
+  double *sz_perr = nullptr;
+  float *sz_fmax = nullptr, *sz_rmax = nullptr, *sz_pred = nullptr, *sz_feat = nullptr;
+  if (opt.sizing) {
+    const size_t bytes = 32 + 16 + 8 + 8 + sizeof(int) * (size_t)n + sizeof(float) * (size_t)n * 18;
+    SP2_TRY(dev_alloc(&b.sizing, bytes, s));
+    unsigned char *q = static_cast<unsigned char *>(b.sizing);
+    sz_perr = reinterpret_cast<double *>(q);
+    sz_dmax = reinterpret_cast<int *>(q + 16);
+    sz_fmax = reinterpret_cast<float *>(q + 24);
+    sz_counts = reinterpret_cast<int *>(q + 32);
+    sz_rmax = reinterpret_cast<float *>(q + 32 + sizeof(int) * (size_t)n);
+    sz_pred = sz_rmax + n;
+    sz_feat = sz_pred + n;
+  }
+  double mae_sum = 0.0, under_sum = 0.0, rows_seen = 0.0;
+  auto exact_width = [&](const ellpack_t *X, bool up, int *w) -> int {
+    SP2_TRY(struct_count_async(X, X, up ? X : nullptr, sz_counts, sz_dmax, s));
+    int h = 0;
+    SP2_CUDA(cudaMemcpyAsync(&h, sz_dmax, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SP2_CUDA(cudaStreamSynchronize(s));
+    *w = h < 1 ? 1 : h;
+    return SP2_OK;
+  };
 
   // F64 copy of H if needed
   const ellpack_t *H64 = H;
@@ -215,8 +247,23 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
     long long guess = (long long)4 * res.max_nnz;
     if (guess < (long long)(1.25 * last_count)) guess = (long long)(1.25 * last_count);
     if (guess < 64) guess = 64;
+    if (opt.sizing == 1) {  // exact structural bound: never overflows
+      int w = 0;
+      SP2_TRY(exact_width(&b.X, up, &w));
+      st.struct_passes++;
+      guess = w;
+    } else if (opt.sizing == 2) {  // predicted lengths of the product's rows
+      SP2_TRY(features_async(&b.X, opt.tau, up ? 2 : 1, sz_rmax, sz_feat, s));
+      SP2_TRY(predict_async(opt.predictor, sz_feat, n, sz_pred, s));
+      SP2_TRY(max_float_async(sz_pred, n, sz_fmax, s));
+      float fm = 0.f;
+      SP2_CUDA(cudaMemcpyAsync(&fm, sz_fmax, sizeof(float), cudaMemcpyDeviceToHost, s));
+      SP2_CUDA(cudaStreamSynchronize(s));
+      guess = (long long)ceil(1.10 * (double)fm) + 16;
+    }
     int width = round_up((int)(guess < max_w ? guess : max_w), 32);
     if (width > n) width = n;
+    if (width < 32 && n >= 32) width = 32;
     const int lg = opt.spgemm_path;
     for (;;) {
       SP2_TRY(ensure(&b.Y, n, width, b.X.dtype, s));
@@ -228,10 +275,24 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
       if (res.overflow_rows == 0) break;
       if (res.max_count > max_w)
         return fail(SP2E_OVERFLOW, "sp2_purify: a row needs %d slots, above the width cap %d", res.max_count, max_w);
-      width = round_up((int)(1.25 * res.max_count) + 1, 32);
+      if (opt.sizing == 2) {  // the prediction was short: the failed pass counted the exact lengths
+        width = round_up(res.max_count, 32);
+      } else {
+        width = round_up((int)(1.25 * res.max_count) + 1, 32);
+      }
       if (width > max_w) width = round_up(max_w, 32) > n ? n : round_up(max_w, 32);
       if (width < res.max_count) width = res.max_count;
       st.regrows++;
+    }
+    if (width > st.width_max) st.width_max = width;
+    if (opt.sizing == 2) {  // how far the predictions were from the exact lengths
+      SP2_TRY(pred_error_async(sz_pred, b.Y.nnz, n, sz_perr, s));
+      double pe[2];
+      SP2_CUDA(cudaMemcpyAsync(pe, sz_perr, sizeof(pe), cudaMemcpyDeviceToHost, s));
+      SP2_CUDA(cudaStreamSynchronize(s));
+      mae_sum += pe[0];
+      under_sum += pe[1];
+      rows_seen += (double)n;
     }
     last_count = res.max_count;
     ellpack_t t = b.X; b.X = b.Y; b.Y = t;
@@ -250,6 +311,10 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   SP2_CUDA(cudaStreamSynchronize(s));
   st.iterations = it;
   st.status = status;
+  if (rows_seen > 0) {
+    st.pred_log_mae = mae_sum / rows_seen;
+    st.pred_under_frac = under_sum / rows_seen;
+  }
   st.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   if (stats) *stats = st;
   if (status == 2) return fail(SP2E_NOTCONV, "sp2_purify: max_iter=%d reached (err %.3e)", opt.max_iter, st.err[it < SP2_STATS_CAP ? it : SP2_STATS_CAP - 1]);

@@ -35,16 +35,26 @@ class ellpack_t(ctypes.Structure):
                 ("nnz", ctypes.c_void_p)]
 
 
+NNZPRED_NPARAMS, NNZPRED_NSTATS = 5313, 34
+
+
+class nnzpred_t(ctypes.Structure):
+    _fields_ = [("params", ctypes.c_void_p), ("adam_m", ctypes.c_void_p), ("adam_v", ctypes.c_void_p),
+                ("stats", ctypes.c_void_p), ("steps", ctypes.c_int64)]
+
+
 class sp2_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("stall_rule", ctypes.c_int32),
                 ("n_fp64_tail", ctypes.c_int32), ("max_width", ctypes.c_int32), ("spgemm_path", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("switch_tol", ctypes.c_double), ("graph", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("sizing", ctypes.c_int32), ("predictor", ctypes.POINTER(nnzpred_t))]
 
 
 class sp2_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("status", ctypes.c_int32), ("fp32_iterations", ctypes.c_int32),
-                ("regrows", ctypes.c_int32), ("emin", ctypes.c_double), ("emax", ctypes.c_double),
+                ("regrows", ctypes.c_int32), ("struct_passes", ctypes.c_int32), ("width_max", ctypes.c_int32),
+                ("pred_log_mae", ctypes.c_double), ("pred_under_frac", ctypes.c_double),
+                ("emin", ctypes.c_double), ("emax", ctypes.c_double),
                 ("time_ms", ctypes.c_double),
                 ("trX", ctypes.c_double * SP2_STATS_CAP), ("trX2", ctypes.c_double * SP2_STATS_CAP),
                 ("err", ctypes.c_double * SP2_STATS_CAP), ("branch", ctypes.c_int32 * SP2_STATS_CAP),
@@ -94,6 +104,17 @@ def _load():
         "sp2_purify": ([E, D, D, P(sp2_options), E, P(sp2_stats), V], ctypes.c_int),
         "sp2_x0": ([E, D, E, P(D), P(D), V], ctypes.c_int),
         "sp2_purify_batched": ([E, P(D), I, D, P(sp2_options), E, P(sp2_stats), V], ctypes.c_int),
+        "ellpack_struct_count": ([E, E, E, V, P(I), V], ctypes.c_int),
+        "nnzpred_features": ([E, D, I, V, V], ctypes.c_int),
+        "nnzpred_create": ([P(nnzpred_t), ctypes.c_uint64, V], ctypes.c_int),
+        "nnzpred_destroy": ([P(nnzpred_t), V], ctypes.c_int),
+        "nnzpred_set_stats": ([P(nnzpred_t), V, V, ctypes.c_int64, V], ctypes.c_int),
+        "nnzpred_grad": ([P(nnzpred_t), V, V, ctypes.c_int64, V, P(ctypes.c_float), V], ctypes.c_int),
+        "nnzpred_train": ([P(nnzpred_t), V, V, ctypes.c_int64, I, I, ctypes.c_float, P(ctypes.c_float), V],
+                          ctypes.c_int),
+        "nnzpred_predict": ([P(nnzpred_t), V, ctypes.c_int64, V, V], ctypes.c_int),
+        "nnzpred_save": ([P(nnzpred_t), ctypes.c_char_p, V], ctypes.c_int),
+        "nnzpred_load": ([P(nnzpred_t), ctypes.c_char_p, V], ctypes.c_int),
         "sp2_profile_start": ([], ctypes.c_int),
         "sp2_profile_stop": ([P(sp2_profile)], ctypes.c_int),
         "sp2_step": ([E, E, D, D, P(sp2_step_info), V], ctypes.c_int),
@@ -293,6 +314,9 @@ def sp2_options_default(**kw):
     for k, v in kw.items():
         if not hasattr(o, k):
             raise TypeError("unknown sp2 option %r" % k)
+        if k == "predictor":
+            o._pred_ref = v  # keep the predictor alive as long as the options
+            v = ctypes.pointer(v.desc)
         setattr(o, k, v)
     return o
 
@@ -302,7 +326,9 @@ def stats_dict(st):
     m = min(it + 1, SP2_STATS_CAP)
     return {
         "iterations": it, "status": {0: "converged", 1: "stalled", 2: "max_iter"}.get(st.status, st.status),
-        "fp32_iterations": st.fp32_iterations, "regrows": st.regrows, "emin": st.emin, "emax": st.emax,
+        "fp32_iterations": st.fp32_iterations, "regrows": st.regrows, "struct_passes": st.struct_passes,
+        "width_max": st.width_max, "pred_log_mae": st.pred_log_mae, "pred_under_frac": st.pred_under_frac,
+        "emin": st.emin, "emax": st.emax,
         "time_ms": st.time_ms,
         "trX": np.array(st.trX[:m]), "trX2": np.array(st.trX2[:m]), "err": np.array(st.err[:m]),
         "branch": ["X2" if b == 1 else "2X-X2" for b in st.branch[:min(it, SP2_STATS_CAP)]],
@@ -377,3 +403,82 @@ def sp2_purify_batched(Hs, noccs, tol, options=None, stream=None, allow_notconv=
     if not (rc == SP2E_NOTCONV and allow_notconv):
         _check(rc)
     return Ds, [stats_dict(sarr[m]) for m in range(count)]
+
+
+def ellpack_struct_count(A, B, C=None, stream=None):
+    """Exact structural row counts of A*B (+C): (torch int32 tensor [n], max)."""
+    import torch
+    counts = torch.empty(A.n, dtype=torch.int32, device="cuda")
+    mx = ctypes.c_int32()
+    _check(lib.ellpack_struct_count(_d(A), _d(B), _d(C) if C is not None else None, counts.data_ptr(),
+                                    ctypes.byref(mx), _stream(stream)))
+    return counts, mx.value
+
+
+def nnzpred_features(X, tau, branch, stream=None):
+    """Row features of X (torch float32 [n, 16]) for the product of an SP2 step with `branch`."""
+    import torch
+    feat = torch.empty((X.n, 16), dtype=torch.float32, device="cuda")
+    _check(lib.nnzpred_features(_d(X), float(tau), int(branch), feat.data_ptr(), _stream(stream)))
+    return feat
+
+
+class NnzPredictor:
+    """The row-length MLP (weights on the GPU, trained by the library's kernels)."""
+
+    def __init__(self, seed=0, stream=None):
+        self.desc = nnzpred_t()
+        _check(lib.nnzpred_create(ctypes.byref(self.desc), int(seed), _stream(stream)))
+
+    def set_stats(self, feat, counts, stream=None):
+        _check(lib.nnzpred_set_stats(ctypes.byref(self.desc), feat.data_ptr(), counts.data_ptr(), feat.shape[0],
+                                     _stream(stream)))
+
+    def grad(self, feat, counts, stream=None):
+        import torch
+        g = torch.empty(NNZPRED_NPARAMS, dtype=torch.float32, device="cuda")
+        loss = ctypes.c_float()
+        _check(lib.nnzpred_grad(ctypes.byref(self.desc), feat.data_ptr(), counts.data_ptr(), feat.shape[0],
+                                g.data_ptr(), ctypes.byref(loss), _stream(stream)))
+        return g, loss.value
+
+    def train(self, feat, counts, steps, batch=2048, lr=1e-3, stream=None):
+        loss = ctypes.c_float()
+        _check(lib.nnzpred_train(ctypes.byref(self.desc), feat.data_ptr(), counts.data_ptr(), feat.shape[0],
+                                 int(steps), int(batch), float(lr), ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def predict(self, feat, stream=None):
+        import torch
+        pred = torch.empty(feat.shape[0], dtype=torch.float32, device="cuda")
+        _check(lib.nnzpred_predict(ctypes.byref(self.desc), feat.data_ptr(), feat.shape[0], pred.data_ptr(),
+                                   _stream(stream)))
+        return pred
+
+    def params(self):
+        """(weights float32[NNZPRED_NPARAMS], statistics float32[NNZPRED_NSTATS]) on the host,
+        read back through the library's save format."""
+        import os
+        import tempfile
+        fd, path = tempfile.mkstemp(suffix=".nnzpred")
+        os.close(fd)
+        try:
+            self.save(path)
+            raw = np.fromfile(path, dtype=np.uint8)
+            vals = raw[8:].view(np.float32)
+            return vals[:NNZPRED_NPARAMS].copy(), vals[NNZPRED_NPARAMS:].copy()
+        finally:
+            os.remove(path)
+
+    def save(self, path, stream=None):
+        _check(lib.nnzpred_save(ctypes.byref(self.desc), path.encode(), _stream(stream)))
+
+    def load(self, path, stream=None):
+        _check(lib.nnzpred_load(ctypes.byref(self.desc), path.encode(), _stream(stream)))
+
+    def __del__(self):
+        try:
+            if self.desc.params:
+                lib.nnzpred_destroy(ctypes.byref(self.desc), None)
+        except Exception:
+            pass

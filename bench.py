@@ -37,7 +37,8 @@ def parse():
     p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--n", type=int, default=262144)
+    p.add_argument("--n", type=int, default=None,
+                   help="matrix size (default: 262144 for spgemm, 131072 for sp2, 1048576 for sizing)")
     p.add_argument("--tau", type=float, default=1e-6)
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     p.add_argument("--seed", type=int, default=0)
@@ -223,6 +224,18 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def spgemm_kernel_name(a):
+    """The first-pass SpGEMM kernel that the chosen path launches."""
+    p = a.path
+    if p == 0:
+        p = 4 if a.dtype == "f64" else 3
+    if p in (1, 2, 4):
+        return "spgemm_block_kernel (%d warp%s per row)" % (p, "s" if p > 1 else "")
+    if p == 3:
+        return "spgemm_super_kernel (one warp per row, two k steps per pass)"
+    return "spgemm_hash_kernel (2^%d slots per warp)" % p
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(a):
     import torch
@@ -317,7 +330,7 @@ def run_ours(a):
     roofline = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tflops / alu_peak,
                 "traffic": traffic,
                 "peak_source": "derived: 152 SMs x %s FMA/clk x 2 flop x 2.07 GHz" % ("2 FP64" if a.dtype == "f64" else "128 FP32"),
-                "kernel": "spgemm_block_kernel", "kernel_ms": k_ms, "launches_timed": cnt,
+                "kernel": spgemm_kernel_name(a), "kernel_ms": k_ms, "launches_timed": cnt,
                 "hbm_view": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                              "peak_source": "measured" if "fallback" not in pk else "fallback",
                              "algorithmic_bytes_per_launch": alg_bytes}}
@@ -483,7 +496,7 @@ def run_sizing(a):
     from paper_2102_08505_gb300 import inputs as I
     from paper_2102_08505_gb300 import learned
     from paper_2102_08505_gb300 import sp2ell as S
-    n = a.n if a.n != 262144 else 1048576
+    n = a.n
     tau = a.tau if a.tau != 1e-6 else 1e-5
     t0 = time.perf_counter()
     feat, counts = learned.default_training_set(seed=100 + a.seed, rows=50000, tau=tau, dtype=S.SP2_F32)
@@ -501,20 +514,27 @@ def run_sizing(a):
     pad_v[:, :idx.shape[1]] = val
     H = S.Ellpack.from_numpy(pad_i, pad_v, nnz)
     res, Ds = {}, {}
-    for mode, name in ((0, "heuristic"), (1, "structural"), (2, "mlp")):
+    for mode, name in ((2, "mlp"), (1, "structural"), (0, "heuristic")):
         kw = dict(tau=tau, precision=S.SP2_PREC_MIXED, sizing=mode, spgemm_path=a.path)
         if mode == 2:
             kw["predictor"] = pred
         opt = S.sp2_options_default(**kw)
-        for _ in range(max(1, min(a.warmup, 2))):
-            S.sp2_purify(H, n / 2, 1e-10, opt)
-        torch.cuda.synchronize()
         times = []
-        for _ in range(max(1, min(a.steps, 3))):
-            t0 = time.perf_counter()
-            D, st = S.sp2_purify(H, n / 2, 1e-10, opt)
+        try:
+            for _ in range(max(1, min(a.warmup, 2))):
+                S.sp2_purify(H, n / 2, 1e-10, opt)
             torch.cuda.synchronize()
-            times.append(time.perf_counter() - t0)
+            for _ in range(max(1, min(a.steps, 3))):
+                t0 = time.perf_counter()
+                D, st = S.sp2_purify(H, n / 2, 1e-10, opt)
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+        except S.Sp2Error as e:
+            st = getattr(e, "stats", {})
+            res[name] = {"error": str(e), "iterations": st.get("iterations"),
+                         "max_row_nnz": [int(x) for x in st.get("max_row_nnz", [])],
+                         "err": [float(x) for x in st.get("err", [])], "width_max": st.get("width_max")}
+            continue
         Ds[name] = D
         res[name] = {"time_s": float(np.median(times)), "iterations": st["iterations"], "status": st["status"],
                      "width_max": st["width_max"], "regrows": st["regrows"], "struct_passes": st["struct_passes"],
@@ -525,13 +545,14 @@ def run_sizing(a):
             "training": {"rows": int(counts.shape[0]), "collect_s": t_collect, "train_s": t_train,
                          "final_batch_loss": loss},
             **res,
-            "dD_mlp_vs_heuristic": diff_fro(S, Ds["mlp"], Ds["heuristic"]) / np.sqrt(n),
-            "dD_structural_vs_heuristic": diff_fro(S, Ds["structural"], Ds["heuristic"]) / np.sqrt(n)}
+            **{"dD_%s_vs_mlp" % k: diff_fro(S, Ds[k], Ds["mlp"]) / np.sqrt(n) for k in Ds if k != "mlp" and "mlp" in Ds}}
     print(json.dumps(line), flush=True)
 
 
 def main():
     a = parse()
+    if a.n is None:
+        a.n = {"sp2": 131072, "sizing": 1048576}.get(a.workload, 262144)
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "sp2":

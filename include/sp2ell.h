@@ -199,8 +199,9 @@ int sp2_profile_stop(sp2_profile *out);
  * |union over k in cols(A_i) of cols(B_k)| (union cols(C_i)), an upper bound of the
  * post-threshold length of row i of the product.  counts: device int32[n];
  * max_count (optional, host) receives the largest.  A row whose columns fall in more than
- * 512 groups of 32 reports min(n, sum of the lengths of the rows it gathers) instead
- * (still an upper bound).  Synchronises `stream`.
+ * 2048 groups of 32 reports min(n, sum of the lengths of the rows it gathers) instead
+ * (still an upper bound).  Errors: SP2E_ARG (sizes or dtypes differ, or B has more than
+ * 2^26 - 32 columns).  Synchronises `stream`.
  */
 int ellpack_struct_count(const ellpack_t *A, const ellpack_t *B, const ellpack_t *C, int32_t *counts,
                          int32_t *max_count, void *stream);
@@ -365,7 +366,8 @@ void sp2_options_default(sp2_options *opt);
  * (release with ellpack_destroy) and *stats (optional) the per-iteration record.
  * Returns SP2_OK, or SP2E_NOTCONV with D still set when max_iter was reached.
  * Errors: SP2E_ARG, SP2E_NOMEM, SP2E_CUDA, SP2E_OVERFLOW (max_width too small),
- * SP2E_NONFINITE.  Synchronises `stream`.
+ * SP2E_NONFINITE; after an error *stats holds the iterations recorded before it.
+ * Synchronises `stream`.
  */
 int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2_options *opt, ellpack_t *D,
                sp2_stats *stats, void *stream);

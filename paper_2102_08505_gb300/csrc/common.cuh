@@ -35,6 +35,7 @@ inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
 
 int num_sms();
 inline int round_up(int x, int m) { return ((x + m - 1) / m) * m; }
+inline size_t round_up_sz(size_t x, size_t m) { return ((x + m - 1) / m) * m; }
 
 // ------------------------------------------------------------------ profiling
 // note_launch() after every kernel launch; prof_begin/prof_end bracket one launch of a
@@ -160,6 +161,9 @@ int struct_count_async(const ellpack_t *A, const ellpack_t *B, const ellpack_t *
                        cudaStream_t s);
 int features_async(const ellpack_t *X, double tau, int branch, float *rmax_scratch, float *feat, cudaStream_t s);
 int predict_async(const nnzpred_t *p, const float *feat, long long n, float *pred, cudaStream_t s);
+// out2[0] = sum over rows of |log1p(pred) - log1p(actual)|, out2[1] = rows with actual > pred;
+// out2 holds kPredErrDoubles doubles (the rest is scratch for the blocks' partial sums)
+constexpr int kPredErrDoubles = 2 + 2 * 256;
 int pred_error_async(const float *pred, const int *actual, long long n, double *out2, cudaStream_t s);
 int max_float_async(const float *v, long long n, float *out, cudaStream_t s);
 

@@ -20,7 +20,10 @@ namespace {
 constexpr unsigned kFullMask = 0xffffffffu;
 
 // ---------------------------------------------------------------- structural count
-constexpr int kCntLog2G = 10, kCntG = 1 << kCntLog2G, kCntNB = 512;  // 512 blocks of 32 columns
+// A group-table entry packs (group << 11) | block: groups below 2^21 - 1, so n <= 2^26 - 32.
+constexpr int kCntLog2G = 12, kCntG = 1 << kCntLog2G, kCntNB = 2048;  // 2048 blocks of 32 columns
+constexpr int kCntBlkBits = 11;
+constexpr int kCntMaxN = (1 << 26) - 32;
 constexpr int kCntWarps = 8;
 constexpr int kCntBytesPerWarp = kCntG * 4 + kCntNB * 4 + 16;
 
@@ -53,14 +56,14 @@ __global__ void __launch_bounds__(kCntWarps * 32) struct_count_kernel(EllView<T>
         int h = cnt_hash(g), b = -1;
         for (int p = 0; p < kCntG; ++p) {
           const unsigned e = ((volatile unsigned *)gtab)[h];
-          if (e != 0xFFFFFFFFu && (e >> 9) == g) { b = (int)(e & 0x1FFu); break; }
+          if (e != 0xFFFFFFFFu && (e >> kCntBlkBits) == g) { b = (int)(e & (kCntNB - 1)); break; }
           if (e == 0xFFFFFFFFu) {
             // take a block number first; the CAS decides which lane's number is kept
             const int nbn = atomicAdd(nblk, 1);
             if (nbn >= kCntNB) break;
-            const unsigned old = atomicCAS(gtab + h, 0xFFFFFFFFu, (g << 9) | (unsigned)nbn);
+            const unsigned old = atomicCAS(gtab + h, 0xFFFFFFFFu, (g << kCntBlkBits) | (unsigned)nbn);
             if (old == 0xFFFFFFFFu) { b = nbn; break; }
-            if ((old >> 9) == g) { b = (int)(old & 0x1FFu); break; }
+            if ((old >> kCntBlkBits) == g) { b = (int)(old & (kCntNB - 1)); break; }
           }
           h = (h + 1) & (kCntG - 1);
         }
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(kCntWarps * 32) struct_count_kernel(EllView<T>
     for (int i = lane; i < nb; i += 32) c += __popc(mask[i]);
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFullMask, c, o);
     over = __any_sync(kFullMask, over) || *nblk > kCntNB;
-    // rows spanning more than 512 groups of 32 columns: the undeduplicated sum, capped at
+    // rows spanning more than 2048 groups of 32 columns: the undeduplicated sum, capped at
     // the column count (still an upper bound of the structural length)
     if (over) c = (int)(naive < ncol ? naive : ncol);
     if (lane == 0) counts[r] = c;
@@ -193,48 +196,68 @@ __device__ __forceinline__ float norm_in(const float *__restrict__ feat, size_t 
   return (feat[i * 16 + c] - mean[c]) / stdv[c];
 }
 
+// Shared-memory copy of the parameters with padded weight rows (W1 rows of 17, W2 rows of
+// 65 floats), so that a lane per output unit (forward) and a lane per input column
+// (backward) both read distinct banks.
+constexpr int kPW1 = 0, kPB1 = kPW1 + kH * (kIn + 1), kPW2 = kPB1 + kH, kPB2 = kPW2 + kH * (kH + 1), kPW3 = kPB2 + kH,
+              kPB3 = kPW3 + kH, kPN = kPB3 + 1;
+
+__device__ __forceinline__ int padded(int i) {
+  if (i < kB1) return kPW1 + (i / kIn) * (kIn + 1) + i % kIn;
+  if (i < kW2) return kPB1 + (i - kB1);
+  if (i < kB2) return kPW2 + ((i - kW2) / kH) * (kH + 1) + (i - kW2) % kH;
+  return kPB2 + (i - kB2);  // b2, w3, b3 are contiguous in both layouts
+}
+
+__device__ __forceinline__ void load_padded(const float *__restrict__ P, float *sP) {
+  for (int i = threadIdx.x; i < NNZPRED_NPARAMS; i += blockDim.x) sP[padded(i)] = P[i];
+}
+
 // One warp per sample: lane l owns hidden units l and l + 32 of both layers.
 struct WarpAct {
   float x[kIn];
   float h1a, h1b, h2a, h2b, y;
 };
 
-__device__ __forceinline__ void mlp_forward_warp(const float *__restrict__ P, const float *xin, float *h1s,
-                                                 WarpAct &act, int lane) {
+__device__ __forceinline__ void mlp_forward_warp(const float *sP, const float *xin, float *h1s, WarpAct &act,
+                                                 int lane) {
 #pragma unroll
   for (int c = 0; c < kIn; ++c) act.x[c] = xin[c];
-  float a = P[kB1 + lane], b = P[kB1 + lane + 32];
+  const float *w1a = sP + kPW1 + lane * (kIn + 1), *w1b = sP + kPW1 + (lane + 32) * (kIn + 1);
+  float a = sP[kPB1 + lane], b = sP[kPB1 + lane + 32];
 #pragma unroll
   for (int c = 0; c < kIn; ++c) {
-    a = fmaf(P[kW1 + lane * kIn + c], act.x[c], a);
-    b = fmaf(P[kW1 + (lane + 32) * kIn + c], act.x[c], b);
+    a = fmaf(w1a[c], act.x[c], a);
+    b = fmaf(w1b[c], act.x[c], b);
   }
   act.h1a = fmaxf(a, 0.f);
   act.h1b = fmaxf(b, 0.f);
   h1s[lane] = act.h1a;
   h1s[lane + 32] = act.h1b;
   __syncwarp();
-  a = P[kB2 + lane];
-  b = P[kB2 + lane + 32];
+  const float *w2a = sP + kPW2 + lane * (kH + 1), *w2b = sP + kPW2 + (lane + 32) * (kH + 1);
+  a = sP[kPB2 + lane];
+  b = sP[kPB2 + lane + 32];
+#pragma unroll 16
   for (int c = 0; c < kH; ++c) {
     const float h = h1s[c];
-    a = fmaf(P[kW2 + lane * kH + c], h, a);
-    b = fmaf(P[kW2 + (lane + 32) * kH + c], h, b);
+    a = fmaf(w2a[c], h, a);
+    b = fmaf(w2b[c], h, b);
   }
   act.h2a = fmaxf(a, 0.f);
   act.h2b = fmaxf(b, 0.f);
-  float y = fmaf(P[kW3 + lane], act.h2a, P[kW3 + lane + 32] * act.h2b);
+  float y = fmaf(sP[kPW3 + lane], act.h2a, sP[kPW3 + lane + 32] * act.h2b);
   for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(kFullMask, y, o);
-  act.y = y + P[kB3];
+  act.y = y + sP[kPB3];
 }
 
 __global__ void __launch_bounds__(kMlpWarps * 32) mlp_predict_kernel(const float *__restrict__ P,
                                                                      const float *__restrict__ stats,
                                                                      const float *__restrict__ feat, long long n,
                                                                      float *__restrict__ pred) {
-  __shared__ float sP[NNZPRED_NPARAMS];
+  __shared__ float sP[kPN];
   __shared__ float h1s[kMlpWarps][kH];
-  for (int i = threadIdx.x; i < NNZPRED_NPARAMS; i += blockDim.x) sP[i] = P[i];
+  load_padded(P, sP);
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const float *mean = stats, *stdv = stats + 16;
@@ -251,8 +274,9 @@ __global__ void __launch_bounds__(kMlpWarps * 32) mlp_predict_kernel(const float
 }
 
 // Gradient of the mean over samples of (y - t)^2 / 2, t the standardised log1p target.
-// Each warp handles samples; per-block gradients are summed in shared memory, then added
-// to grad (zeroed by the caller).  loss (optional) receives the summed squared error / 2.
+// Each warp handles samples; per-block gradients are summed in shared memory (padded
+// layout), then added to grad (packed layout, zeroed by the caller).  loss (optional)
+// receives the summed squared error / 2.
 __global__ void __launch_bounds__(kMlpWarps * 32) mlp_grad_kernel(const float *__restrict__ P,
                                                                   const float *__restrict__ stats,
                                                                   const float *__restrict__ feat,
@@ -260,12 +284,13 @@ __global__ void __launch_bounds__(kMlpWarps * 32) mlp_grad_kernel(const float *_
                                                                   const int *__restrict__ sel, long long n,
                                                                   float inv_n, float *__restrict__ grad,
                                                                   float *__restrict__ loss) {
-  __shared__ float sP[NNZPRED_NPARAMS];
-  __shared__ float sG[NNZPRED_NPARAMS];
+  __shared__ float sP[kPN];
+  __shared__ float sG[kPN];
   __shared__ float h1s[kMlpWarps][kH];
   __shared__ float dh2s[kMlpWarps][kH];
   __shared__ float sL;
-  for (int i = threadIdx.x; i < NNZPRED_NPARAMS; i += blockDim.x) { sP[i] = P[i]; sG[i] = 0.f; }
+  load_padded(P, sP);
+  for (int i = threadIdx.x; i < kPN; i += blockDim.x) sG[i] = 0.f;
   if (threadIdx.x == 0) sL = 0.f;
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -283,46 +308,48 @@ __global__ void __launch_bounds__(kMlpWarps * 32) mlp_grad_kernel(const float *_
     const float dy = e * inv_n;
     if (lane == 0) atomicAdd(&sL, 0.5f * e * e);
     // layer 3
-    atomicAdd(&sG[kW3 + lane], act.h2a * dy);
-    atomicAdd(&sG[kW3 + lane + 32], act.h2b * dy);
-    if (lane == 0) atomicAdd(&sG[kB3], dy);
-    const float d2a = act.h2a > 0.f ? sP[kW3 + lane] * dy : 0.f;
-    const float d2b = act.h2b > 0.f ? sP[kW3 + lane + 32] * dy : 0.f;
+    atomicAdd(&sG[kPW3 + lane], act.h2a * dy);
+    atomicAdd(&sG[kPW3 + lane + 32], act.h2b * dy);
+    if (lane == 0) atomicAdd(&sG[kPB3], dy);
+    const float d2a = act.h2a > 0.f ? sP[kPW3 + lane] * dy : 0.f;
+    const float d2b = act.h2b > 0.f ? sP[kPW3 + lane + 32] * dy : 0.f;
     dh2s[wid][lane] = d2a;
     dh2s[wid][lane + 32] = d2b;
-    atomicAdd(&sG[kB2 + lane], d2a);
-    atomicAdd(&sG[kB2 + lane + 32], d2b);
+    atomicAdd(&sG[kPB2 + lane], d2a);
+    atomicAdd(&sG[kPB2 + lane + 32], d2b);
     __syncwarp();
     // layer 2 weights: dW2[u][c] = dh2[u] * h1[c]; lane covers columns c = lane, lane + 32
     const float h1c0 = h1s[wid][lane], h1c1 = h1s[wid][lane + 32];
     for (int u = 0; u < kH; ++u) {
       const float d = dh2s[wid][u];
       if (d != 0.f) {
-        atomicAdd(&sG[kW2 + u * kH + lane], d * h1c0);
-        atomicAdd(&sG[kW2 + u * kH + lane + 32], d * h1c1);
+        atomicAdd(&sG[kPW2 + u * (kH + 1) + lane], d * h1c0);
+        atomicAdd(&sG[kPW2 + u * (kH + 1) + lane + 32], d * h1c1);
       }
     }
     // dh1[c] = sum_u W2[u][c] dh2[u], masked by relu
     float g0 = 0.f, g1 = 0.f;
     for (int u = 0; u < kH; ++u) {
       const float d = dh2s[wid][u];
-      g0 = fmaf(sP[kW2 + u * kH + lane], d, g0);
-      g1 = fmaf(sP[kW2 + u * kH + lane + 32], d, g1);
+      g0 = fmaf(sP[kPW2 + u * (kH + 1) + lane], d, g0);
+      g1 = fmaf(sP[kPW2 + u * (kH + 1) + lane + 32], d, g1);
     }
     const float d1a = act.h1a > 0.f ? g0 : 0.f;
     const float d1b = act.h1b > 0.f ? g1 : 0.f;
-    atomicAdd(&sG[kB1 + lane], d1a);
-    atomicAdd(&sG[kB1 + lane + 32], d1b);
+    atomicAdd(&sG[kPB1 + lane], d1a);
+    atomicAdd(&sG[kPB1 + lane + 32], d1b);
 #pragma unroll
     for (int c = 0; c < kIn; ++c) {
-      atomicAdd(&sG[kW1 + lane * kIn + c], d1a * act.x[c]);
-      atomicAdd(&sG[kW1 + (lane + 32) * kIn + c], d1b * act.x[c]);
+      atomicAdd(&sG[kPW1 + lane * (kIn + 1) + c], d1a * act.x[c]);
+      atomicAdd(&sG[kPW1 + (lane + 32) * (kIn + 1) + c], d1b * act.x[c]);
     }
     __syncwarp();
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < NNZPRED_NPARAMS; i += blockDim.x)
-    if (sG[i] != 0.f) atomicAdd(grad + i, sG[i]);
+  for (int i = threadIdx.x; i < NNZPRED_NPARAMS; i += blockDim.x) {
+    const float g = sG[padded(i)];
+    if (g != 0.f) atomicAdd(grad + i, g);
+  }
   if (threadIdx.x == 0 && loss) atomicAdd(loss, sL);
 }
 
@@ -389,38 +416,60 @@ __global__ void feat_stats_kernel(const float *__restrict__ feat, const int *__r
   }
 }
 
-// sum over rows of |log1p(pred) - log1p(actual)| and the number of rows whose actual
-// length exceeds the prediction (one CTA, fixed order)
-__global__ void pred_error_kernel(const float *__restrict__ pred, const int *__restrict__ actual, long long n,
-                                  double *__restrict__ out) {
-  __shared__ double s_e[256];
-  __shared__ double s_u[256];
-  double e = 0.0, u = 0.0;
-  for (long long i = threadIdx.x; i < n; i += 256) {
-    e += fabs(log1p((double)pred[i]) - log1p((double)actual[i]));
-    u += (double)actual[i] > (double)pred[i] ? 1.0 : 0.0;
+// Sum over rows of |log1p(pred) - log1p(actual)| and the number of rows whose actual
+// length exceeds the prediction: per-thread FP32 sums over a grid-stride slice, a
+// fixed-order FP64 tree per block into part[2 * block], then one warp adds the blocks'
+// partial sums in block order (deterministic for a fixed grid).
+constexpr int kErrBlocks = 256, kErrThreads = 256;
+static_assert(kPredErrDoubles >= 2 + 2 * kErrBlocks, "prediction-error scratch");
+
+__global__ void __launch_bounds__(kErrThreads) pred_error_kernel(const float *__restrict__ pred,
+                                                                 const int *__restrict__ actual, long long n,
+                                                                 double *__restrict__ part) {
+  __shared__ double s_e[kErrThreads];
+  __shared__ double s_u[kErrThreads];
+  float e = 0.f, u = 0.f;
+  for (long long i = (long long)blockIdx.x * kErrThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kErrThreads) {
+    const float a = (float)actual[i], p = pred[i];
+    e += fabsf(log1pf(p) - log1pf(a));
+    u += a > p ? 1.f : 0.f;
   }
   s_e[threadIdx.x] = e;
   s_u[threadIdx.x] = u;
   __syncthreads();
-  for (int h = 128; h > 0; h >>= 1) {
+  for (int h = kErrThreads / 2; h > 0; h >>= 1) {
     if ((int)threadIdx.x < h) { s_e[threadIdx.x] += s_e[threadIdx.x + h]; s_u[threadIdx.x] += s_u[threadIdx.x + h]; }
     __syncthreads();
   }
-  if (threadIdx.x == 0) { out[0] = s_e[0]; out[1] = s_u[0]; }
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = s_e[0]; part[2 * blockIdx.x + 1] = s_u[0]; }
 }
 
-__global__ void max_float_kernel(const float *__restrict__ v, long long n, float *__restrict__ out) {
+__global__ void pred_error_final_kernel(const double *__restrict__ part, int blocks, double *__restrict__ out) {
+  const int lane = threadIdx.x;
+  double e = 0.0, u = 0.0;
+  for (int b = lane; b < blocks; b += 32) { e += part[2 * b]; u += part[2 * b + 1]; }
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_xor_sync(kFullMask, e, o);
+    u += __shfl_xor_sync(kFullMask, u, o);
+  }
+  if (lane == 0) { out[0] = e; out[1] = u; }
+}
+
+// Largest of n non-negative floats (as int bits, whose order matches) into *out, which the
+// caller zeroes.
+__global__ void __launch_bounds__(256) max_float_kernel(const float *__restrict__ v, long long n,
+                                                        int *__restrict__ out) {
   __shared__ float s[256];
   float m = 0.f;
-  for (long long i = threadIdx.x; i < n; i += 256) m = fmaxf(m, v[i]);
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+    m = fmaxf(m, v[i]);
   s[threadIdx.x] = m;
   __syncthreads();
   for (int h = 128; h > 0; h >>= 1) {
     if ((int)threadIdx.x < h) s[threadIdx.x] = fmaxf(s[threadIdx.x], s[threadIdx.x + h]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = s[0];
+  if (threadIdx.x == 0 && s[0] > 0.f) atomicMax(out, __float_as_int(s[0]));
 }
 
 int grid_warps(long long items, int warps_per_block) {
@@ -434,6 +483,7 @@ int grid_warps(long long items, int warps_per_block) {
 // Structural counts of A*B (+C); launched from the SP2 driver too.
 int struct_count_async(const ellpack_t *A, const ellpack_t *B, const ellpack_t *C, int *counts, int *dmax,
                        cudaStream_t s) {
+  if (B->n > kCntMaxN) return fail(SP2E_ARG, "structural count: %d columns, above the limit %d", B->n, kCntMaxN);
   SP2_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), s));
   const int smem = kCntWarps * kCntBytesPerWarp;
   const int grid = grid_warps(A->n, kCntWarps);
@@ -472,14 +522,22 @@ int features_async(const ellpack_t *X, double tau, int branch, float *rmax_scrat
 }
 
 int pred_error_async(const float *pred, const int *actual, long long n, double *out2, cudaStream_t s) {
-  pred_error_kernel<<<1, 256, 0, s>>>(pred, actual, n, out2);
+  // out2 holds 2 + 2 * kErrBlocks doubles: the result, then the blocks' partial sums
+  long long b = (n + kErrThreads - 1) / kErrThreads;
+  const int blocks = (int)(b < kErrBlocks ? (b < 1 ? 1 : b) : kErrBlocks);
+  pred_error_kernel<<<blocks, kErrThreads, 0, s>>>(pred, actual, n, out2 + 2);
+  pred_error_final_kernel<<<1, 32, 0, s>>>(out2 + 2, blocks, out2);
+  note_launch();
   note_launch();
   SP2_CUDA(cudaGetLastError());
   return SP2_OK;
 }
 
 int max_float_async(const float *v, long long n, float *out, cudaStream_t s) {
-  max_float_kernel<<<1, 256, 0, s>>>(v, n, out);
+  SP2_CUDA(cudaMemsetAsync(out, 0, sizeof(float), s));
+  long long b = (n + 255) / 256;
+  const long long cap = (long long)num_sms() * 2;
+  max_float_kernel<<<(int)(b < cap ? (b < 1 ? 1 : b) : cap), 256, 0, s>>>(v, n, reinterpret_cast<int *>(out));
   note_launch();
   SP2_CUDA(cudaGetLastError());
   return SP2_OK;

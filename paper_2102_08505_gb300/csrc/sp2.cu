@@ -110,27 +110,29 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   cudaStream_t s = b.s;
   sp2_stats st;
   memset(&st, 0, sizeof(st));
+  if (stats) memset(stats, 0, sizeof(*stats));
 
   SP2_TRY(dev_alloc((void **)&b.rowstat, sizeof(double2) * (size_t)n, s));
   SP2_TRY(dev_alloc((void **)&b.ctl, sizeof(SpgemmCtl), s));
   SP2_TRY(dev_alloc((void **)&b.dres, sizeof(StepResult), s));
   SP2_TRY(dev_alloc((void **)&b.bounds, 2 * sizeof(double), s));
-  // sizing scratch: counts int[n], max int, pred error double[2], max float, rmax float[n],
-  // pred float[n], features float[16n]
+  // sizing scratch: max int, max float, counts int[n], rmax float[n], pred float[n],
+  // features float[16n], then the prediction-error sums (kPredErrDoubles doubles)
   int *sz_counts = nullptr, *sz_dmax = nullptr;
   double *sz_perr = nullptr;
   float *sz_fmax = nullptr, *sz_rmax = nullptr, *sz_pred = nullptr, *sz_feat = nullptr;
   if (opt.sizing) {
-    const size_t bytes = 32 + 16 + 8 + 8 + sizeof(int) * (size_t)n + sizeof(float) * (size_t)n * 18;
+    const size_t off_perr = round_up_sz(16 + sizeof(int) * (size_t)n + sizeof(float) * (size_t)n * 18, 16);
+    const size_t bytes = off_perr + sizeof(double) * kPredErrDoubles;
     SP2_TRY(dev_alloc(&b.sizing, bytes, s));
     unsigned char *q = static_cast<unsigned char *>(b.sizing);
-    sz_perr = reinterpret_cast<double *>(q);
-    sz_dmax = reinterpret_cast<int *>(q + 16);
-    sz_fmax = reinterpret_cast<float *>(q + 24);
-    sz_counts = reinterpret_cast<int *>(q + 32);
-    sz_rmax = reinterpret_cast<float *>(q + 32 + sizeof(int) * (size_t)n);
+    sz_dmax = reinterpret_cast<int *>(q);
+    sz_fmax = reinterpret_cast<float *>(q + 8);
+    sz_counts = reinterpret_cast<int *>(q + 16);
+    sz_rmax = reinterpret_cast<float *>(q + 16 + sizeof(int) * (size_t)n);
     sz_pred = sz_rmax + n;
     sz_feat = sz_pred + n;
+    sz_perr = reinterpret_cast<double *>(q + off_perr);
   }
   double mae_sum = 0.0, under_sum = 0.0, rows_seen = 0.0;
   auto exact_width = [&](const ellpack_t *X, bool up, int *w) -> int {
@@ -184,6 +186,18 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   int tail_left = opt.n_fp64_tail;
   bool armed = false;
   int it = 0;
+  // the record so far reaches the caller on every return from here, errors included
+  struct StatsOnExit {
+    sp2_stats *dst;
+    const sp2_stats *src;
+    const int *it;
+    ~StatsOnExit() {
+      if (dst) {
+        *dst = *src;
+        dst->iterations = *it;
+      }
+    }
+  } stats_on_exit{stats, &st, &it};
   int status = 0;  // set when the loop stops: 0 err < tol, 1 stall rule, 2 max_iter
   int last_count = res.max_nnz;
   for (;;) {

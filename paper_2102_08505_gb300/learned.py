@@ -22,13 +22,13 @@ def sp2_products(H, nocc, tau, steps, dtype=S.SP2_F64):
         X = Xf
     traces = None
     for _ in range(steps):
-        w = 4 * X.width
+        w = min(H.n, max(64, ((4 * int(X.nnz.max().item()) + 31) // 32) * 32))
         while True:
             Xn = S.Ellpack.empty(H.n, w, dtype)
             rc, info = S.sp2_step(X, Xn, nocc, tau, traces=traces, raise_on_overflow=False)
             if rc == 0:
                 break
-            w = ((info.required_width + 31) // 32) * 32
+            w = min(H.n, ((info.required_width + 31) // 32) * 32)
         yield X, info.branch, Xn
         traces = (info.trXn, info.trXn2)
         X = Xn

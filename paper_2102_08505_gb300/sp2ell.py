@@ -346,7 +346,11 @@ def sp2_purify(H, nocc, tol, options=None, stream=None, allow_notconv=False):
     out = OwnedEllpack(D)  # owns D even when an error is raised below (freed with it)
     if rc == SP2E_NOTCONV and allow_notconv:
         return out, stats_dict(st)
-    _check(rc)
+    try:
+        _check(rc)
+    except Sp2Error as e:
+        e.stats = stats_dict(st)  # the iterations recorded before the error
+        raise
     return out, stats_dict(st)
 
 

@@ -34,32 +34,35 @@ def test_struct_counts_match_oracle_pattern(gpu, with_c):
 
 
 def test_struct_counts_wide_row_bound(gpu):
-    """Row 0 gathers 600 column groups of 32 (more than the 512 the count tracks): it
-    reports the undeduplicated sum (2400 >= its exact 1800); the other rows are exact."""
+    """Row 0 gathers 2400 column groups of 32 (more than the 2048 the count tracks): it
+    reports the undeduplicated sum (4800 >= its exact 2400); the other rows are exact."""
     S = gpu
-    n = 40000
-    bi = np.zeros((n, 2), np.int32)
-    bv = np.full((n, 2), np.nan)
-    bn = np.full(n, 2, np.int32)
+    n = 80000
+    # B: rows 2q and 2q+1 (q < 60) hold the same 40 columns, one per group; other rows {i}
+    bi = np.zeros((n, 64), np.int32)
+    bv = np.full((n, 64), np.nan)
+    bn = np.ones(n, np.int32)
     bi[:, 0] = np.arange(n)
-    bi[:, 1] = np.minimum(np.arange(n) + 1, n - 1)
-    bn[n - 1] = 1
-    bv[:, :] = 1.0
-    ai = np.zeros((n, 1216), np.int32)
-    av = np.full((n, 1216), np.nan)
+    bv[:, 0] = 1.0
+    for k in range(120):
+        bi[k, :40] = 32 * (40 * (k // 2) + np.arange(40))
+        bv[k, :40] = 1.0
+        bn[k] = 40
+    # A: row 0 gathers B rows 0..119, every other row i gathers row i
+    ai = np.zeros((n, 128), np.int32)
+    av = np.full((n, 128), np.nan)
     an = np.ones(n, np.int32)
     ai[:, 0] = np.arange(n)
     av[:, 0] = 1.0
-    cols = np.sort(np.concatenate([64 * np.arange(600), 64 * np.arange(600) + 1]))
-    ai[0, :1200] = cols
-    av[0, :1200] = 0.5
-    an[0] = 1200
+    ai[0, :120] = np.arange(120)
+    av[0, :120] = 0.5
+    an[0] = 120
     A, B = O.Ell(ai, av, an), O.Ell(bi, bv, bn)
     ref = O.spgemm(A, B, None, 1.0, 0.0, 0.0)
-    assert ref.nnz[0] == 1800
+    assert ref.nnz[0] == 2400
     c, mx = S.ellpack_struct_count(_dev(S, A), _dev(S, B))
     c = c.cpu().numpy()
-    assert c[0] == 2400 and mx == 2400
+    assert c[0] == 4800 and mx == 4800
     assert np.array_equal(c[1:], ref.nnz[1:])
 
 

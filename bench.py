@@ -241,9 +241,8 @@ def run_ours(a):
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2102_08505_gb300 import shard
+    rank, local, world = shard.rank_info()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -297,8 +296,7 @@ def run_ours(a):
         S.sp2_step(X1, X2, nocc, a.tau, traces=traces, spgemm_path=a.path)
     torch.cuda.synchronize()
     clocks = Clocks(local, enabled=not a.no_clocks)
-    if world > 1:
-        dist.barrier()
+    shard.barrier()
     torch.cuda.synchronize()
     S.sp2_profile_start()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -309,14 +307,9 @@ def run_ours(a):
     e1.record(stream)
     torch.cuda.synchronize()
     prof = S.sp2_profile_stop()
-    if world > 1:
-        dist.barrier()
+    shard.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / a.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = shard.max_over_ranks(e0.elapsed_time(e1) / a.steps, dev)
     value = world * 1000.0 / ms
 
     cnt, tot = prof["spgemm"]
@@ -355,19 +348,14 @@ def run_ours(a):
         for _ in range(max(1, a.warmup)):
             e2e_step()
         ksteps = max(1, min(a.steps, 20))
-        if world > 1:
-            dist.barrier()
+        shard.barrier()
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(ksteps):
             e2e_step()
         e1.record(stream)
         torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1) / ksteps
-        if world > 1:
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = shard.max_over_ranks(e0.elapsed_time(e1) / ksteps, dev)
         out_bytes = a.n * w2 * (4 + esz) + 4 * a.n
         e2e = {"value": world * 1000.0 / ems, "unit": UNIT, "h2d_bytes_per_step": in_bytes,
                "d2h_bytes_per_step": out_bytes, "ms_per_step": ems, "steps": ksteps,
@@ -449,15 +437,25 @@ def run_sp2(a):
 
 def run_batched(a):
     """256 gapped open 3D clusters with N log-uniform in [512, 8192]: one graph-captured
-    batched launch (mixed and FP64) against the same matrices purified one by one."""
+    batched launch (mixed and FP64) against the same matrices purified one by one.  Under
+    torchrun the matrices are dealt to ranks by size (no collective on the data path);
+    times are the maximum over ranks."""
     import torch
+    import torch.distributed as dist
     from paper_2102_08505_gb300 import inputs as I
+    from paper_2102_08505_gb300 import shard
     from paper_2102_08505_gb300 import sp2ell as S
+    rank, local, world = shard.rank_info()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     sizes = I.cluster_sizes(a.count, 512, 8192, seed=a.seed)
+    mine = shard.deal(sizes, world)[rank]
     tau = 1e-5
     Hs = []
-    for m, n in enumerate(sizes):
-        idx, val, nnz = I.tight_binding(int(n), seed=a.seed + m, delta=10.0, periodic=False)
+    for m in mine:
+        idx, val, nnz = I.tight_binding(int(sizes[m]), seed=a.seed + m, delta=10.0, periodic=False)
         Hs.append(S.Ellpack.from_numpy(idx, val, nnz))
     noccs = [h.n // 2 for h in Hs]
     res = {}
@@ -466,25 +464,33 @@ def run_batched(a):
         opt = S.sp2_options_default(tau=tau, precision=prec, graph=graph, spgemm_path=a.path)
         S.sp2_purify_batched(Hs, noccs, 1e-10, opt)
         torch.cuda.synchronize()
+        shard.barrier()
         t0 = time.perf_counter()
         Ds, sts = S.sp2_purify_batched(Hs, noccs, 1e-10, opt)
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        res[name] = {"time_s": dt, "iterations_total": int(sum(s["iterations"] for s in sts)),
-                     "max_iterations": int(max(s["iterations"] for s in sts))}
+        dt = shard.max_over_ranks(time.perf_counter() - t0, dev)
+        res[name] = {"time_s": dt, "iterations_total": int(shard.sum_over_ranks(sum(s["iterations"] for s in sts), dev)),
+                     "max_iterations": int(shard.max_over_ranks(max(s["iterations"] for s in sts), dev))}
     opt = S.sp2_options_default(tau=tau, precision=S.SP2_PREC_F64, spgemm_path=a.path)
     torch.cuda.synchronize()
+    shard.barrier()
     t0 = time.perf_counter()
     its = 0
     for H, nocc in zip(Hs, noccs):
         D, st = S.sp2_purify(H, nocc, 1e-10, opt)
         its += st["iterations"]
     torch.cuda.synchronize()
-    res["one_by_one_f64"] = {"time_s": time.perf_counter() - t0, "iterations_total": its}
-    line = {"workload": "batched SP2: %d gapped open 3D clusters, N log-uniform [512, 8192], sum N = %d" % (
-        len(Hs), int(sizes.sum())), **res,
-        "speedup_batched_mixed_vs_one_by_one_f64": res["one_by_one_f64"]["time_s"] / res["batched_mixed_graph"]["time_s"]}
-    print(json.dumps(line), flush=True)
+    res["one_by_one_f64"] = {"time_s": shard.max_over_ranks(time.perf_counter() - t0, dev),
+                             "iterations_total": int(shard.sum_over_ranks(its, dev))}
+    if rank == 0:
+        line = {"workload": "batched SP2: %d gapped open 3D clusters, N log-uniform [512, 8192], sum N = %d" % (
+            len(sizes), int(sizes.sum())), "n_gpus": world, "parallelism": "matrices dealt to ranks" if world > 1
+            else "single GPU", **res,
+            "speedup_batched_mixed_vs_one_by_one_f64":
+                res["one_by_one_f64"]["time_s"] / res["batched_mixed_graph"]["time_s"]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def run_sizing(a):

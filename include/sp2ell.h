@@ -256,6 +256,41 @@ int nnzpred_predict(const nnzpred_t *p, const float *feat, int64_t n, float *pre
 int nnzpred_save(const nnzpred_t *p, const char *path, void *stream);
 int nnzpred_load(nnzpred_t *p, const char *path, void *stream);
 
+/* ---------------------------------------------------------------- autotuner */
+/*
+ * The SpGEMM first pass has several variants that compute the same product (spgemm_path
+ * 1, 2, 4: column-block accumulator shared by that many warps per row; 3: one warp per
+ * row, two k steps per pass; 10..12: per-warp hash table of 2^path slots).  The tuner
+ * times them on a real product and keeps the fastest per class (SM count, dtype,
+ * floor(log2 n), floor(log2 mean stored row length of A)) in a process-wide host table
+ * (thread-safe).  sp2_purify, sp2_step and sp2_purify_batched use the table when
+ * spgemm_path is SP2_PATH_TUNED, tuning a class on its first product.  The paper has no
+ * counterpart.
+ */
+#define SP2_PATH_TUNED (-1)
+#define SP2_TUNE_CANDIDATES 7  /* 1, 2, 4, 3, 10, 11, 12 in this order */
+
+/* Times every variant on Out <- drop_tau(alpha A*B + beta C) (C may be NULL): one untimed
+ * and `reps` timed runs each (CUDA events on `stream`); records the fastest for A's class
+ * and returns it in *best_path; times_ms (optional, host float[SP2_TUNE_CANDIDATES])
+ * receives the mean time of each.  Out is overwritten with the product (rows that do not
+ * fit are left unspecified, as for ellpack_multiply).  Errors: SP2E_ARG, SP2E_NOMEM,
+ * SP2E_CUDA.  Synchronises `stream`. */
+int sp2_tune_spgemm(const ellpack_t *A, const ellpack_t *B, const ellpack_t *C, ellpack_t *Out, double alpha,
+                    double beta, double tau, int32_t reps, int32_t *best_path, float *times_ms, void *stream);
+
+/* Host-only table access (no GPU work).  sms = 0 in lookup means the current device;
+ * *path = -1 when the class has no entry. */
+int sp2_tune_record(int32_t sms, int32_t dtype, int32_t n, double mean_row_nnz, int32_t path, float ms);
+int sp2_tune_lookup(int32_t sms, int32_t dtype, int32_t n, double mean_row_nnz, int32_t *path);
+int sp2_tune_clear(void);
+int sp2_tune_size(int32_t *entries);
+/* Text file, one class per line ("sms dtype log2_n log2_mean_row path ms"); load merges
+ * into the table (an entry replaces the same class).  SP2E_ARG for an unreadable or
+ * malformed file (nothing is merged then). */
+int sp2_tune_save(const char *path);
+int sp2_tune_load(const char *path);
+
 /* ---------------------------------------------------------------- SP2 */
 
 #define SP2_PREC_F64 0      /* every step in FP64 */
@@ -277,7 +312,7 @@ typedef struct sp2_options {
                            per row, F32: path 3); 1, 2, 4 = column-block accumulator
                            shared by that many warps per row; 3 = column blocks, one
                            warp per row, two k steps per pass; 10..12 = per-warp hash
-                           table of 2^k slots */
+                           table of 2^k slots; SP2_PATH_TUNED = the autotuner's choice */
   double tau;           /* drop tolerance (default 1e-5) */
   double switch_tol;    /* MIXED: leave the FP32 loop once err_n < switch_tol (0 = automatic:
                            max(tol, 1e-6)); the FP32 stall rule also ends it */
@@ -296,6 +331,7 @@ typedef struct sp2_stats {
   int32_t fp32_iterations;              /* MIXED: updates made in FP32 */
   int32_t regrows;                      /* multiplies repeated after a width overflow */
   int32_t struct_passes;                /* structural-count passes run */
+  int32_t tuned;                        /* product classes tuned during the run (SP2_PATH_TUNED) */
   int32_t width_max;                    /* largest output width used */
   double pred_log_mae;                  /* sizing 2: mean |log1p(pred) - log1p(actual)| per row */
   double pred_under_frac;               /* sizing 2: fraction of rows longer than predicted */
@@ -334,7 +370,8 @@ typedef struct sp2_step_info {
   int32_t spgemm_path;     /* in: SpGEMM first pass, as sp2_options.spgemm_path */
   int32_t rows_deferred;   /* out: rows the first pass handed to the 2^14-slot table */
   int32_t rows_dense;      /* out: rows handed further to the dense global-row pass */
-  int32_t pad;
+  int32_t spgemm_path_used; /* out: the first-pass variant that ran (the tuner's choice
+                               for SP2_PATH_TUNED) */
 } sp2_step_info;
 
 /*

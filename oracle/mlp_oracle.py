@@ -5,7 +5,7 @@ standardised features; its target is the standardised log1p of the post-threshol
 length, and the loss of a batch is the mean of (y - t)^2 / 2.  Parameters are packed as
 W1[64][16], b1[64], W2[64][64], b2[64], w3[64], b3.  The paper sizes ELLPACK rows with a
 fixed width (Section "Micro-Kernel Performance Evaluation - NUMA Aware
-Allocation") and has no learned part: the predictor is an extension that sizes
+Data") and has no learned part: the predictor is an extension that sizes
 the output of each SP2 product.  This oracle writes out the standard backpropagation
 equations of that network, and the features below are the plain definitions of the 16
 row statistics.  Only the tests import it.

@@ -384,6 +384,9 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
     return fail(SP2E_ARG, "sp2_purify_batched: unknown precision %d", opt.precision);
   if (opt.max_iter < 0 || opt.max_iter + opt.n_fp64_tail >= SP2_STATS_CAP || opt.n_fp64_tail < 0)
     return fail(SP2E_ARG, "sp2_purify_batched: bad max_iter / n_fp64_tail");
+  if (!(opt.spgemm_path == SP2_PATH_TUNED || (opt.spgemm_path >= 0 && opt.spgemm_path <= 4) ||
+        (opt.spgemm_path >= 10 && opt.spgemm_path <= 12)))
+    return fail(SP2E_ARG, "sp2_purify_batched: spgemm_path must be -1, 0..4 or 10..12");
   long long ntot_ll = 0;
   int wh = 1, nmax = 0;
   std::vector<int> off(count + 1, 0);
@@ -441,7 +444,7 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
   if (width < round_up(wh + 1, 32)) width = round_up(wh + 1, 32);
   if (width > round_up(nmax, 32)) width = round_up(nmax, 32);
   if (width < wh + 1) width = round_up(wh + 1, 32);
-  int regrows = 0;
+  int regrows = 0, tuned_classes = 0;
   long long body_iters = 0;
 
   for (;;) {  // (re)start with a larger width after an overflow
@@ -539,6 +542,23 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
       SP2_TRY(fallback_scratch(ntot, SP2_F64, ntot < 64 ? ntot : 64, &acc, &mark, s));
     }
 
+    // SpGEMM variants: fixed, or the tuner's choice for the stacked product's class.  The
+    // loop is captured once, so the classes are those of X0 * X0 (tuned here, before the
+    // capture, if new; the products written meanwhile are recomputed by the loop).
+    int path32 = opt.spgemm_path, path64 = opt.spgemm_path;
+    if (opt.spgemm_path == SP2_PATH_TUNED) {
+      double mean = 0.0;
+      SP2_TRY(mean_row_nnz(&X64, &mean, s));
+      auto pick = [&](ellpack_t *cur, ellpack_t *nxt, SpgemmCtl *c, int *path) -> int {
+        if (tune_find(cur->dtype, ntot, mean, path)) return SP2_OK;
+        MultiplyArgs a{cur, cur, nullptr, nxt, 1.0, 0.0, opt.tau, 0};
+        SP2_TRY(tune_multiply(a, mean, d_rowstat, c, 2, path, nullptr, s));
+        ++tuned_classes;
+        return SP2_OK;
+      };
+      if (use32) SP2_TRY(pick(&X32, &Y32, d_c32, &path32));
+      if (use64) SP2_TRY(pick(&X64, &Y64, d_c64, &path64));
+    }
     BatchView bv32{d_rowmat, d_a32, d_b32, d_act32};
     BatchView bv64{d_rowmat, d_a64, d_b64, d_act64};
     auto half = [&](int h, cudaGraphConditionalHandle handle, int set_cond) -> int {
@@ -549,13 +569,13 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
         note_launch();
       }
       if (use32) {
-        MultiplyArgs a{cur32, cur32, cur32, nxt32, 1.0, 0.0, opt.tau, opt.spgemm_path};
+        MultiplyArgs a{cur32, cur32, cur32, nxt32, 1.0, 0.0, opt.tau, path32};
         a.bv = bv32;
         a.fb_prealloc = d_fb;
         SP2_TRY(multiply_async(a, d_rowstat, d_c32, s));
       }
       if (use64) {
-        MultiplyArgs a{cur64, cur64, cur64, nxt64, 1.0, 0.0, opt.tau, opt.spgemm_path};
+        MultiplyArgs a{cur64, cur64, cur64, nxt64, 1.0, 0.0, opt.tau, path64};
         a.bv = bv64;
         a.fb_prealloc = d_fb;
         SP2_TRY(multiply_async(a, d_rowstat, d_c64, s));
@@ -665,6 +685,7 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
         o.status = st_out[m].status;
         o.fp32_iterations = use32 ? (mixed && st_out[m].fp32_it > 0 ? st_out[m].fp32_it : (f32only ? st_out[m].it : 0)) : 0;
         o.regrows = regrows;
+        o.tuned = tuned_classes;
         o.emin = hb[2 * m];
         o.emax = hb[2 * m + 1];
         o.time_ms = ms;

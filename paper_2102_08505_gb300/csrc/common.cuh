@@ -167,4 +167,12 @@ constexpr int kPredErrDoubles = 2 + 2 * 256;
 int pred_error_async(const float *pred, const int *actual, long long n, double *out2, cudaStream_t s);
 int max_float_async(const float *v, long long n, float *out, cudaStream_t s);
 
+// Autotuner (tune.cu): mean stored row length of X (synchronises); the table entry for
+// the class of a multiply (false if absent); timing every first-pass variant on the
+// multiply `a`, recording the fastest in the table.
+int mean_row_nnz(const ellpack_t *X, double *mean, cudaStream_t s);
+bool tune_find(int dtype, int n, double mean_nnz, int *path);
+int tune_multiply(MultiplyArgs a, double mean_nnz, double2 *rowstat, SpgemmCtl *ctl, int reps, int *best,
+                  float *times, cudaStream_t s);
+
 }  // namespace sp2

@@ -46,7 +46,7 @@ int read_result(Buffers &b, StepResult *h) {
 }
 
 // (Re)allocates m with at least `width` slots and the given dtype; contents undefined.
-bool valid_path(int p) { return (p >= 0 && p <= 4) || (p >= 10 && p <= 12); }
+bool valid_path(int p) { return p == SP2_PATH_TUNED || (p >= 0 && p <= 4) || (p >= 10 && p <= 12); }
 
 int ensure(ellpack_t *m, int n, int width, int dtype, cudaStream_t s) {
   if (m->owner && m->width >= width && m->dtype == dtype) return SP2_OK;
@@ -97,7 +97,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   if (opt.max_iter < 0 || opt.max_iter + opt.n_fp64_tail >= SP2_STATS_CAP)
     return fail(SP2E_ARG, "sp2_purify: max_iter + n_fp64_tail must be < %d", SP2_STATS_CAP);
   if (opt.n_fp64_tail < 0) return fail(SP2E_ARG, "sp2_purify: n_fp64_tail < 0");
-  if (!valid_path(opt.spgemm_path)) return fail(SP2E_ARG, "sp2_purify: spgemm_path must be 0..4 or 10..12");
+  if (!valid_path(opt.spgemm_path)) return fail(SP2E_ARG, "sp2_purify: spgemm_path must be -1, 0..4 or 10..12");
   const int max_w = (opt.max_width > 0 && opt.max_width < n) ? opt.max_width : n;
   if (!(opt.switch_tol >= 0.0) || !isfinite(opt.switch_tol)) return fail(SP2E_ARG, "sp2_purify: bad switch_tol");
   if (opt.sizing < 0 || opt.sizing > 2) return fail(SP2E_ARG, "sp2_purify: sizing must be 0, 1 or 2");
@@ -278,7 +278,15 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
     int width = round_up((int)(guess < max_w ? guess : max_w), 32);
     if (width > n) width = n;
     if (width < 32 && n >= 32) width = 32;
-    const int lg = opt.spgemm_path;
+    // SpGEMM variant: fixed, or the tuner's choice for this class of product (a class seen
+    // for the first time is tuned once the product fits)
+    int lg = opt.spgemm_path;
+    bool tune_pending = false;
+    const double mean_nnz = (double)res.nnz_total / (double)n;
+    if (lg == SP2_PATH_TUNED && !tune_find(b.X.dtype, n, mean_nnz, &lg)) {
+      lg = 0;
+      tune_pending = true;
+    }
     for (;;) {
       SP2_TRY(ensure(&b.Y, n, width, b.X.dtype, s));
       MultiplyArgs a{&b.X, &b.X, beta != 0.0 ? &b.X : nullptr, &b.Y, alpha, beta, opt.tau, lg};
@@ -297,6 +305,16 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
       if (width > max_w) width = round_up(max_w, 32) > n ? n : round_up(max_w, 32);
       if (width < res.max_count) width = res.max_count;
       st.regrows++;
+    }
+    if (tune_pending) {  // time every variant on this product, then redo it with the fastest
+      MultiplyArgs a{&b.X, &b.X, beta != 0.0 ? &b.X : nullptr, &b.Y, alpha, beta, opt.tau, 0};
+      SP2_TRY(tune_multiply(a, mean_nnz, b.rowstat, b.ctl, 2, &lg, nullptr, s));
+      a.path = lg;
+      SP2_TRY(multiply_async(a, b.rowstat, b.ctl, s));
+      launch_reduce_rows(b.rowstat, b.Y.nnz, n, b.ctl, b.dres, s);
+      SP2_CUDA(cudaGetLastError());
+      SP2_TRY(read_result(b, &res));
+      st.tuned++;
     }
     if (width > st.width_max) st.width_max = width;
     if (opt.sizing == 2) {  // how far the predictions were from the exact lengths
@@ -376,7 +394,7 @@ extern "C" int sp2_step(const ellpack_t *X, ellpack_t *Xn, double nocc, double t
   if (X->idx == Xn->idx || X->val == Xn->val || X->nnz == Xn->nnz) return fail(SP2E_ARG, "sp2_step: Xn aliases X");
   if (!(tau >= 0.0) || !isfinite(tau)) return fail(SP2E_ARG, "sp2_step: tau must be finite and >= 0");
   if (!isfinite(nocc)) return fail(SP2E_ARG, "sp2_step: nocc not finite");
-  if (!valid_path(info->spgemm_path)) return fail(SP2E_ARG, "sp2_step: spgemm_path must be 0..4 or 10..12");
+  if (!valid_path(info->spgemm_path)) return fail(SP2E_ARG, "sp2_step: spgemm_path must be -1, 0..4 or 10..12");
   const int n = X->n;
   Buffers b;
   b.s = as_stream(stream);
@@ -399,6 +417,12 @@ extern "C" int sp2_step(const ellpack_t *X, ellpack_t *Xn, double nocc, double t
   const bool up = fabs(2.0 * trX - trX2 - nocc) < fabs(trX2 - nocc);
   info->branch = up ? 2 : 1;
   MultiplyArgs a{X, X, up ? X : nullptr, Xn, up ? -1.0 : 1.0, up ? 2.0 : 0.0, tau, info->spgemm_path};
+  if (a.path == SP2_PATH_TUNED) {
+    double mean = 0.0;
+    SP2_TRY(mean_row_nnz(X, &mean, s));
+    if (!tune_find(X->dtype, n, mean, &a.path)) SP2_TRY(tune_multiply(a, mean, b.rowstat, b.ctl, 2, &a.path, nullptr, s));
+  }
+  info->spgemm_path_used = a.path;
   SP2_TRY(multiply_async(a, b.rowstat, b.ctl, s));
   launch_reduce_rows(b.rowstat, Xn->nnz, n, b.ctl, b.dres, s);
   SP2_CUDA(cudaGetLastError());

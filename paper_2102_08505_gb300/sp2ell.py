@@ -19,6 +19,7 @@ SP2E_ARG, SP2E_OVERFLOW, SP2E_NOMEM, SP2E_CUDA, SP2E_NOTCONV, SP2E_NONFINITE, SP
 SP2_F64, SP2_F32 = 0, 1
 SP2_PREC_F64, SP2_PREC_MIXED, SP2_PREC_F32 = 0, 1, 2
 SP2_STATS_CAP = 256
+SP2_PATH_TUNED = -1
 _CODES = {0: "SP2_OK", -1: "SP2E_ARG", -2: "SP2E_OVERFLOW", -3: "SP2E_NOMEM", -4: "SP2E_CUDA",
           -5: "SP2E_NOTCONV", -6: "SP2E_NONFINITE", -7: "SP2E_TIMEOUT"}
 
@@ -52,7 +53,8 @@ class sp2_options(ctypes.Structure):
 
 class sp2_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("status", ctypes.c_int32), ("fp32_iterations", ctypes.c_int32),
-                ("regrows", ctypes.c_int32), ("struct_passes", ctypes.c_int32), ("width_max", ctypes.c_int32),
+                ("regrows", ctypes.c_int32), ("struct_passes", ctypes.c_int32), ("tuned", ctypes.c_int32),
+                ("width_max", ctypes.c_int32),
                 ("pred_log_mae", ctypes.c_double), ("pred_under_frac", ctypes.c_double),
                 ("emin", ctypes.c_double), ("emax", ctypes.c_double),
                 ("time_ms", ctypes.c_double),
@@ -66,7 +68,8 @@ class sp2_step_info(ctypes.Structure):
                 ("branch", ctypes.c_int32), ("err", ctypes.c_double), ("trXn", ctypes.c_double),
                 ("trXn2", ctypes.c_double), ("nnz_total", ctypes.c_int64), ("max_row_nnz", ctypes.c_int32),
                 ("required_width", ctypes.c_int32), ("spgemm_path", ctypes.c_int32),
-                ("rows_deferred", ctypes.c_int32), ("rows_dense", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("rows_deferred", ctypes.c_int32), ("rows_dense", ctypes.c_int32),
+                ("spgemm_path_used", ctypes.c_int32)]
 
 
 SP2_PROF_CLASSES = 4
@@ -118,6 +121,13 @@ def _load():
         "sp2_profile_start": ([], ctypes.c_int),
         "sp2_profile_stop": ([P(sp2_profile)], ctypes.c_int),
         "sp2_step": ([E, E, D, D, P(sp2_step_info), V], ctypes.c_int),
+        "sp2_tune_spgemm": ([E, E, E, E, D, D, D, I, P(I), P(ctypes.c_float), V], ctypes.c_int),
+        "sp2_tune_record": ([I, I, I, D, I, ctypes.c_float], ctypes.c_int),
+        "sp2_tune_lookup": ([I, I, I, D, P(I)], ctypes.c_int),
+        "sp2_tune_clear": ([], ctypes.c_int),
+        "sp2_tune_size": ([P(I)], ctypes.c_int),
+        "sp2_tune_save": ([ctypes.c_char_p], ctypes.c_int),
+        "sp2_tune_load": ([ctypes.c_char_p], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -327,6 +337,7 @@ def stats_dict(st):
     return {
         "iterations": it, "status": {0: "converged", 1: "stalled", 2: "max_iter"}.get(st.status, st.status),
         "fp32_iterations": st.fp32_iterations, "regrows": st.regrows, "struct_passes": st.struct_passes,
+        "tuned": st.tuned,
         "width_max": st.width_max, "pred_log_mae": st.pred_log_mae, "pred_under_frac": st.pred_under_frac,
         "emin": st.emin, "emax": st.emax,
         "time_ms": st.time_ms,
@@ -486,3 +497,46 @@ class NnzPredictor:
                 lib.nnzpred_destroy(ctypes.byref(self.desc), None)
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- autotuner
+TUNE_CANDIDATES = (1, 2, 4, 3, 10, 11, 12)
+
+
+def sp2_tune_spgemm(A, B, C, Out, alpha=1.0, beta=0.0, tau=0.0, reps=3, stream=None):
+    """Times every SpGEMM first-pass variant on Out <- drop_tau(alpha A*B + beta C) and
+    records the fastest; returns (best path, {path: ms})."""
+    best = ctypes.c_int32()
+    times = (ctypes.c_float * len(TUNE_CANDIDATES))()
+    _check(lib.sp2_tune_spgemm(_d(A), _d(B), _d(C) if C is not None else None, _d(Out), float(alpha), float(beta),
+                               float(tau), int(reps), ctypes.byref(best), times, _stream(stream)))
+    return best.value, dict(zip(TUNE_CANDIDATES, list(times)))
+
+
+def sp2_tune_record(sms, dtype, n, mean_row_nnz, path, ms=0.0):
+    _check(lib.sp2_tune_record(int(sms), int(dtype), int(n), float(mean_row_nnz), int(path), float(ms)))
+
+
+def sp2_tune_lookup(sms, dtype, n, mean_row_nnz):
+    """The recorded variant for the class, or -1 (sms = 0: the current device)."""
+    p = ctypes.c_int32()
+    _check(lib.sp2_tune_lookup(int(sms), int(dtype), int(n), float(mean_row_nnz), ctypes.byref(p)))
+    return p.value
+
+
+def sp2_tune_clear():
+    _check(lib.sp2_tune_clear())
+
+
+def sp2_tune_size():
+    v = ctypes.c_int32()
+    _check(lib.sp2_tune_size(ctypes.byref(v)))
+    return v.value
+
+
+def sp2_tune_save(path):
+    _check(lib.sp2_tune_save(str(path).encode()))
+
+
+def sp2_tune_load(path):
+    _check(lib.sp2_tune_load(str(path).encode()))

@@ -256,6 +256,43 @@ int nnzpred_predict(const nnzpred_t *p, const float *feat, int64_t n, float *pre
 int nnzpred_save(const nnzpred_t *p, const char *path, void *stream);
 int nnzpred_load(nnzpred_t *p, const char *path, void *stream);
 
+/* ---------------------------------------------------------------- standalone ops */
+/*
+ * Operations of the BML-style ELLPACK surface around the SP2 path (the paper names the
+ * BML library and its ELLPACK format, Sections "Introduction" and "Performance
+ * Evaluation using System Matrices"; these are their plain definitions on the stored
+ * entries).  Rows stay sorted by column; results are bitwise reproducible.
+ */
+
+/* A <- alpha * A on the stored entries (pattern unchanged).  Asynchronous.
+ * Errors: SP2E_ARG (alpha not finite). */
+int ellpack_scale(ellpack_t *A, double alpha, void *stream);
+
+/* Drops in place the stored entries with |v| <= tau (tau = 0 drops exact zeros); the
+ * kept entries keep their order.  Asynchronous.  Errors: SP2E_ARG (tau < 0 or not finite). */
+int ellpack_threshold(ellpack_t *A, double tau, void *stream);
+
+/* out3 (host double[3]) = { max |a_ij|, max_i sum_j |a_ij| (infinity norm), ||A||_F },
+ * FP64 over the stored entries.  Synchronises `stream`.  Errors: SP2E_ARG,
+ * SP2E_NONFINITE (a NaN or Inf entry). */
+int ellpack_norms(const ellpack_t *A, double *out3, void *stream);
+
+/* At <- A^T (same n and dtype; At must not share arrays with A), rows sorted by column.
+ * *required_width (optional) receives the longest column count of A; SP2E_OVERFLOW
+ * (At unchanged) when it exceeds At->width.  Synchronises `stream`. */
+int ellpack_transpose(const ellpack_t *A, ellpack_t *At, int32_t *required_width, void *stream);
+
+/* dense (device, row-major n x ld, A's dtype, ld >= n) <- A, zeros elsewhere.
+ * Asynchronous.  Errors: SP2E_ARG. */
+int ellpack_to_dense(const ellpack_t *A, void *dense, int64_t ld, void *stream);
+
+/* A <- the entries of the dense matrix (device, row-major n x ld, A's dtype) with v != 0
+ * (tau = 0) or |v| > tau, in column order.  *required_width (optional) receives the
+ * longest row; SP2E_OVERFLOW when a row does not fit A->width (its stored prefix is then
+ * unspecified).  Synchronises `stream`. */
+int ellpack_from_dense(const void *dense, int64_t ld, double tau, ellpack_t *A, int32_t *required_width,
+                       void *stream);
+
 /* ---------------------------------------------------------------- autotuner */
 /*
  * The SpGEMM first pass has several variants that compute the same product (spgemm_path

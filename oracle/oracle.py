@@ -308,3 +308,72 @@ def checks(Hd, Dd, nocc):
         "comm_err": float(np.linalg.norm(Hd @ Dd - Dd @ Hd)),
         "gap": float(w[int(nocc)] - w[int(nocc) - 1]) if 0 < nocc < n else float("nan"),
     }
+
+
+# ---------------------------------------------------------------- standalone ELLPACK ops
+# Plain definitions of the library's standalone operations (scale, drop threshold,
+# norms, transpose, dense conversion) on the stored entries of an Ell matrix.
+
+def _live(A):
+    return np.arange(A.w)[None, :] < A.nnz[:, None]
+
+
+def scale(A, alpha):
+    """alpha * A on the stored entries (pattern unchanged)."""
+    B = Ell(A.idx.copy(), A.val.copy(), A.nnz.copy())
+    lv = _live(A)
+    B.val[lv] = A.val[lv] * alpha
+    return B
+
+
+def threshold(A, tau):
+    """Keeps the stored entries with |v| > tau, in their order (tau = 0 drops exact zeros)."""
+    B = Ell.empty(A.n, A.w)
+    for i in range(A.n):
+        j, v = A.row(i)
+        keep = np.abs(v) > tau
+        k = int(keep.sum())
+        B.idx[i, :k] = j[keep]
+        B.val[i, :k] = v[keep]
+        B.nnz[i] = k
+    return B
+
+
+def norms(A):
+    """(max |a_ij|, max_i sum_j |a_ij|, sqrt(sum a_ij^2)) over the stored entries."""
+    lv = _live(A)
+    a = np.where(lv, np.abs(A.val), 0.0)
+    return float(a.max(initial=0.0)), float(a.sum(axis=1).max(initial=0.0)), float(np.sqrt((a * a).sum()))
+
+
+def transpose(A, width=None):
+    """A^T with rows sorted by column: the stored entries (i, j, v) become (j, i, v)."""
+    lv = _live(A)
+    rows = np.repeat(np.arange(A.n), A.nnz)
+    cols = A.idx[lv]
+    vals = A.val[lv]
+    order = np.lexsort((rows, cols))
+    cols, rows, vals = cols[order], rows[order], vals[order]
+    cnt = np.bincount(cols, minlength=A.n).astype(np.int32)
+    w = max(1, int(cnt.max(initial=0))) if width is None else width
+    T = Ell.empty(A.n, w)
+    start = np.concatenate([[0], np.cumsum(cnt)])
+    for j in range(A.n):
+        k = cnt[j]
+        T.idx[j, :k] = rows[start[j]:start[j] + k]
+        T.val[j, :k] = vals[start[j]:start[j] + k]
+        T.nnz[j] = k
+    return T
+
+
+def from_dense_tau(M, tau, width=None):
+    """ELLPACK of a dense matrix keeping v != 0 (tau = 0) or |v| > tau, in column order."""
+    n = M.shape[0]
+    rows = [np.nonzero(M[i] != 0)[0] if tau == 0 else np.nonzero(np.abs(M[i]) > tau)[0] for i in range(n)]
+    w = max(1, max((len(r) for r in rows), default=1)) if width is None else width
+    E = Ell.empty(n, w)
+    for i, r in enumerate(rows):
+        E.idx[i, :len(r)] = r
+        E.val[i, :len(r)] = M[i, r]
+        E.nnz[i] = len(r)
+    return E

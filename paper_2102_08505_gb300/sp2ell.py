@@ -121,6 +121,12 @@ def _load():
         "sp2_profile_start": ([], ctypes.c_int),
         "sp2_profile_stop": ([P(sp2_profile)], ctypes.c_int),
         "sp2_step": ([E, E, D, D, P(sp2_step_info), V], ctypes.c_int),
+        "ellpack_scale": ([E, D, V], ctypes.c_int),
+        "ellpack_threshold": ([E, D, V], ctypes.c_int),
+        "ellpack_norms": ([E, P(D), V], ctypes.c_int),
+        "ellpack_transpose": ([E, E, P(I), V], ctypes.c_int),
+        "ellpack_to_dense": ([E, V, ctypes.c_int64, V], ctypes.c_int),
+        "ellpack_from_dense": ([V, ctypes.c_int64, D, E, P(I), V], ctypes.c_int),
         "sp2_tune_spgemm": ([E, E, E, E, D, D, D, I, P(I), P(ctypes.c_float), V], ctypes.c_int),
         "sp2_tune_record": ([I, I, I, D, I, ctypes.c_float], ctypes.c_int),
         "sp2_tune_lookup": ([I, I, I, D, P(I)], ctypes.c_int),
@@ -540,3 +546,54 @@ def sp2_tune_save(path):
 
 def sp2_tune_load(path):
     _check(lib.sp2_tune_load(str(path).encode()))
+
+
+# ---------------------------------------------------------------- standalone ops
+def ellpack_scale(A, alpha, stream=None):
+    _check(lib.ellpack_scale(_d(A), float(alpha), _stream(stream)))
+
+
+def ellpack_threshold(A, tau, stream=None):
+    _check(lib.ellpack_threshold(_d(A), float(tau), _stream(stream)))
+
+
+def ellpack_norms(A, stream=None):
+    """(max |a_ij|, infinity norm, Frobenius norm)."""
+    out = (ctypes.c_double * 3)()
+    _check(lib.ellpack_norms(_d(A), out, _stream(stream)))
+    return tuple(out)
+
+
+def ellpack_transpose(A, At, stream=None, raise_on_overflow=True):
+    """At <- A^T; returns the longest column count of A (and the status when
+    raise_on_overflow=False)."""
+    w = ctypes.c_int32()
+    rc = lib.ellpack_transpose(_d(A), _d(At), ctypes.byref(w), _stream(stream))
+    if not raise_on_overflow:
+        if rc not in (SP2_OK, SP2E_OVERFLOW):
+            _check(rc)
+        return rc, w.value
+    _check(rc)
+    return w.value
+
+
+def ellpack_to_dense(A, stream=None):
+    """Dense torch tensor [n, n] of A's dtype on the GPU."""
+    import torch
+    D = torch.empty((A.n, A.n), dtype=_torch_dtype(A.dtype), device="cuda")
+    _check(lib.ellpack_to_dense(_d(A), D.data_ptr(), A.n, _stream(stream)))
+    return D
+
+
+def ellpack_from_dense(D, A, tau=0.0, stream=None, raise_on_overflow=True):
+    """A <- entries of the dense torch tensor D (A's dtype, [n, ld]); returns the longest
+    row (and the status when raise_on_overflow=False)."""
+    assert D.is_cuda and D.dim() == 2 and D.is_contiguous() and D.dtype == _torch_dtype(A.dtype)
+    w = ctypes.c_int32()
+    rc = lib.ellpack_from_dense(D.data_ptr(), D.shape[1], float(tau), _d(A), ctypes.byref(w), _stream(stream))
+    if not raise_on_overflow:
+        if rc not in (SP2_OK, SP2E_OVERFLOW):
+            _check(rc)
+        return rc, w.value
+    _check(rc)
+    return w.value

@@ -42,10 +42,11 @@ def parse():
     p.add_argument("--tau", type=float, default=1e-6)
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--workload", default="spgemm", choices=["spgemm", "sp2", "batched", "sizing"],
+    p.add_argument("--workload", default="spgemm", choices=["spgemm", "sp2", "batched", "sizing", "model"],
                    help="spgemm: one SP2 iteration at N=262144 (default); sp2: whole purifications, FP64 vs "
                         "mixed at N=131072; batched: 256 clusters in one graph launch vs one by one; sizing: "
-                        "heuristic vs structural vs MLP output widths for mixed SP2 at N=1048576")
+                        "heuristic vs structural vs MLP output widths for mixed SP2 at N=1048576; model: the paper's "
+                        "model Hamiltonians at N=32000")
     p.add_argument("--count", type=int, default=256)
     p.add_argument("--path", type=int, default=0,
                    help="SpGEMM first pass: 0 automatic, 1/2/4 column blocks with R warps per row, 10-12 hash")
@@ -493,6 +494,68 @@ def run_batched(a):
         dist.destroy_process_group()
 
 
+MODEL_SETS = {  # the paper's parameter sets of the two-level chain model Hamiltonians
+    "metals": dict(d_aa=-1.0, d_bb=-1.0, k=-0.01),
+    "semiconductor": dict(d_bb=-1.0, d_ab=-2.0, k=-0.01),
+    "soft_matter": dict(d_bb=-1.0, d_ab=-1.0, eps_a=-10.0, k=-0.1, r=1.0),
+}
+
+
+def run_model(a):
+    """The paper's own workload: ELLPACK X^2 of the model Hamiltonians (metals,
+    semiconductor, soft matter) at N = 32000, FP64, tau = 1e-5 (one product each, timed
+    with CUDA events after a warm-up), and SP2 on the semiconductor set (gapped at half
+    filling) at N = 4000."""
+    import torch
+    from paper_2102_08505_gb300 import inputs as I
+    from paper_2102_08505_gb300 import sp2ell as S
+    n = a.n
+    tau = a.tau if a.tau != 1e-6 else 1e-5
+    out = {}
+    for name, p in MODEL_SETS.items():
+        idx, val, nnz = I.model_chain(n, seed=a.seed, **p)
+        H = S.Ellpack.from_numpy(idx, val, nnz)
+        fmas = fma_count(idx, nnz)
+        w = 32
+        while True:
+            C = S.Ellpack.empty(n, w)
+            rc, req = S.ellpack_multiply(H, H, C, 1.0, 0.0, tau, raise_on_overflow=False)
+            if rc == 0:
+                break
+            w = ((req + 31) // 32) * 32
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = max(1, min(a.steps, 3))
+        e0.record()
+        for _ in range(reps):
+            S.ellpack_multiply(H, H, C, 1.0, 0.0, tau)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"nnz_per_row": float(nnz.mean()), "product_nnz_per_row": float(C.nnz.double().mean()),
+                     "fma": fmas, "x2_ms": ms, "gflops": 2.0 * fmas / (ms * 1e-3) / 1e9}
+        del C, H
+    # SP2 on the semiconductor set, the one gapped at half filling (FP64 and mixed), at
+    # N = 4000 (its density matrix keeps ~3100 entries per row)
+    ns = min(n, 4000)
+    idx, val, nnz = I.model_chain(ns, seed=a.seed, **MODEL_SETS["semiconductor"])
+    H = S.Ellpack.from_numpy(idx, val, nnz)
+    for prec_name, prec in (("f64", S.SP2_PREC_F64), ("mixed", S.SP2_PREC_MIXED)):
+        opt = S.sp2_options_default(tau=tau, precision=prec)
+        S.sp2_purify(H, ns / 2, 1e-10, opt, allow_notconv=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        D, st = S.sp2_purify(H, ns / 2, 1e-10, opt, allow_notconv=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out["sp2_semiconductor_n%d_%s" % (ns, prec_name)] = {
+            "time_s": dt, "iterations": st["iterations"], "status": st["status"], "iters_per_s": st["iterations"] / dt,
+            "nnz_per_row_D": float(st["nnz_total"][-1]) / ns}
+    print(json.dumps({"workload": "model Hamiltonians (two-level A/B chain), N=%d, FP64 X^2 and SP2, tau=%g" % (n, tau),
+                      **out}), flush=True)
+
+
 def run_sizing(a):
     """Output sizing of the SP2 products: heuristic widths with regrow, exact structural
     counts before every multiply, and the row-length MLP (trained on about 50k rows of
@@ -558,7 +621,7 @@ def run_sizing(a):
 def main():
     a = parse()
     if a.n is None:
-        a.n = {"sp2": 131072, "sizing": 1048576}.get(a.workload, 262144)
+        a.n = {"sp2": 131072, "sizing": 1048576, "model": 32000}.get(a.workload, 262144)
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "sp2":
@@ -567,6 +630,8 @@ def main():
         run_batched(a)
     elif a.workload == "sizing":
         run_sizing(a)
+    elif a.workload == "model":
+        run_model(a)
     else:
         run_ours(a)
 

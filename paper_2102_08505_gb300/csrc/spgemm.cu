@@ -1018,6 +1018,281 @@ __global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
   }
 }
 
+// ------------------------------------------------------------------ stream first pass
+// One warp per output row.  The row's gather -- the addend row C_i (coefficient beta),
+// then row k of B for every entry a_ik of A's row (coefficient alpha * a_ik) -- is one
+// flat stream of 32-entry chunks, loaded D chunks ahead into a ring of registers.  Per
+// chunk every lane finds its column's block by a short linear probe of the group table
+// (a group seen for the first time takes the slow path once: one elected lane per group
+// claims a block), then does one load-FMA-store.  Chunks are consumed in stream order
+// with a __syncwarp between them, so every output entry accumulates its terms in source
+// order (deterministic) and no barrier spans warps.
+template <typename T>
+struct StreamGeo {
+  static constexpr int GSH = BlockCfg<T>::GSH, GW = 1 << GSH, NB = BlockCfg<T>::NB;
+  static constexpr int LOG2G = BlockCfg<T>::LOG2G, G = 1 << LOG2G;
+  static constexpr int VAL_BYTES = NB * GW * (int)sizeof(T);
+  static constexpr int BYTES_PER_ROW = VAL_BYTES + G * 4 + 16;
+  static constexpr int ROWS_RAW = 232192 / BYTES_PER_ROW;
+  static constexpr int ROWS = ROWS_RAW > 16 ? 16 : (ROWS_RAW < 1 ? 1 : ROWS_RAW);
+  static constexpr int SMEM = ROWS * BYTES_PER_ROW;
+  static constexpr unsigned MAX_GROUP = (1u << 24) - 1u;
+  static_assert(G == BlockGeo<T, 1>::G && NB == BlockGeo<T, 1>::NB, "one group table layout");
+};
+
+// Block of group g, or -1 when g is not in the table (probes until a hit or an empty
+// entry; a probe longer than 16 also answers -1 and the slow path finds the group).
+template <int LOG2G>
+__device__ __forceinline__ int probe_block(const unsigned *gtab, unsigned g) {
+  int h = ghash<LOG2G>(g);
+#pragma unroll 1
+  for (int p = 0; p < 16; ++p) {
+    const unsigned e = ((const volatile unsigned *)gtab)[h];
+    if ((e >> 8) == g) return (int)(e & 0xFFu);
+    if (e == 0xFFFFFFFFu) return -1;
+    h = (h + 1) & ((1 << LOG2G) - 1);
+  }
+  return -1;
+}
+
+template <typename T, int D, bool KEEPZ>
+__global__ void __launch_bounds__(StreamGeo<T>::ROWS * 32, 1)
+    spgemm_stream_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
+                         int use_add, BatchView bv, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
+                         int *__restrict__ fb_list, int *__restrict__ fb_count) {
+  using Geo = StreamGeo<T>;
+  constexpr int GW = Geo::GW, GSH = Geo::GSH, G = Geo::G;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned char *base = smem + (size_t)wid * Geo::BYTES_PER_ROW;
+  T *vals = reinterpret_cast<T *>(base);
+  unsigned *gtab = reinterpret_cast<unsigned *>(base + Geo::VAL_BYTES);
+  int *nblk = reinterpret_cast<int *>(base + Geo::VAL_BYTES + G * 4);
+  const int ncol = Out.n;
+  const unsigned lt = lanemask_lt();
+  int wmax = 0, wover = 0;
+
+  for (int r = blockIdx.x * Geo::ROWS + wid; r < A.n; r += gridDim.x * Geo::ROWS) {
+    T alpha_r = alpha, beta_r = beta;
+    int add_r = use_add;
+    if (bv.row_mat) {
+      const int m = bv.row_mat[r];
+      if (!bv.active[m]) continue;
+      alpha_r = (T)bv.alpha[m];
+      beta_r = (T)bv.beta[m];
+      add_r = beta_r != T(0);
+    }
+    {  // clear the blocks and the table
+      const T c = KEEPZ ? untouched<T>() : T(0);
+      constexpr int PER16 = 16 / (int)sizeof(T);
+      for (int i = lane * PER16; i < Geo::NB * GW; i += 32 * PER16) {
+#pragma unroll
+        for (int t = 0; t < PER16; ++t) vals[i + t] = c;
+      }
+      for (int i = lane * 4; i < G; i += 32 * 4) *reinterpret_cast<uint4 *>(gtab + i) = make_uint4(~0u, ~0u, ~0u, ~0u);
+      if (lane == 0) *nblk = 0;
+    }
+    __syncwarp();
+
+    // ---- producer: the flat chunk stream of this row
+    const int na = min(A.nnz[r], A.w);
+    const int ns = na + (add_r ? 1 : 0);  // sources: [addend row], then the rows of B
+    const int *arow_i = A.idx + (size_t)r * A.w;
+    const T *arow_v = A.val + (size_t)r * A.w;
+    int pk = 0, pnb = 0, pbase = -32;  // A entries pbase .. pbase+31, one per lane
+    T pa = T(0);
+    int ps = 0, pq = 0, p_nb = 0;
+    const int *p_ri = B.idx;
+    const T *p_rv = B.val;
+    T p_a = T(0);
+    auto seek = [&]() {  // ps -> the first source at or after ps with entries (or ns)
+      while (ps < ns) {
+        if (add_r && ps == 0) {
+          p_ri = Add.idx + (size_t)r * Add.w;
+          p_rv = Add.val + (size_t)r * Add.w;
+          p_nb = min(Add.nnz[r], Add.w);
+          p_a = beta_r;
+        } else {
+          const int t = ps - add_r;
+          if (t >= pbase + 32) {
+            pbase = t & ~31;
+            const int s = pbase + lane;
+            pk = 0; pnb = 0; pa = T(0);
+            if (s < na) {
+              const int k = __ldg(arow_i + s);
+              if ((unsigned)k < (unsigned)B.n) {
+                pk = k;
+                pa = alpha_r * __ldg(arow_v + s);
+                pnb = min(__ldg(B.nnz + k), B.w);
+              }
+            }
+          }
+          const int k = __shfl_sync(kFull, pk, t & 31);
+          p_nb = __shfl_sync(kFull, pnb, t & 31);
+          p_a = __shfl_sync(kFull, pa, t & 31);
+          p_ri = B.idx + (size_t)k * B.w;
+          p_rv = B.val + (size_t)k * B.w;
+        }
+        if (p_nb > 0) return;
+        ++ps;
+      }
+    };
+    auto produce = [&](int &j, T &v, T &a) -> bool {
+      if (ps >= ns) {
+        j = -1; v = T(0); a = T(0);
+        return false;
+      }
+      const int q = pq + lane;
+      j = q < p_nb ? __ldg(p_ri + q) : -1;
+      v = q < p_nb ? __ldg(p_rv + q) : T(0);
+      a = p_a;
+      pq += 32;
+      if (pq >= p_nb) {
+        pq = 0;
+        ++ps;
+        seek();
+      }
+      return true;
+    };
+
+    // ---- consumer: one chunk into the blocks
+    bool aborted = false;
+    auto consume = [&](int j, T v, T a) {
+      int slot = -1;
+      bool miss = false;
+      if ((unsigned)j < (unsigned)ncol) {
+        const int b = probe_block<Geo::LOG2G>(gtab, (unsigned)j >> GSH);
+        if (b >= 0) slot = b * GW + (j & (GW - 1));
+        else miss = true;
+      }
+      const unsigned need = __ballot_sync(kFull, miss);
+      if (need) {  // groups seen for the first time: one elected lane per group claims a block
+        if (miss) {
+          const unsigned g = (unsigned)j >> GSH;
+          const unsigned peers = __match_any_sync(need, g);
+          const int leader = __ffs(peers) - 1;
+          int b = -1;
+          if (lane == leader) b = g < Geo::MAX_GROUP ? group_block<T, 1>(gtab, nblk, g) : -1;
+          b = __shfl_sync(peers, b, leader);
+          if (b >= 0) slot = b * GW + (j & (GW - 1));
+          else aborted = true;
+        }
+        aborted = __any_sync(kFull, aborted);
+      }
+      if (slot >= 0) {
+        const T o0 = vals[slot];
+        const T o = (KEEPZ && is_untouched(o0)) ? T(0) : o0;
+        vals[slot] = fmadd(a, v, o);
+      }
+      __syncwarp();  // this chunk's updates land before the next chunk reads
+    };
+
+    seek();
+    int rj[D];
+    T rv[D], ra[D];
+    unsigned live = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+      if (produce(rj[d], rv[d], ra[d])) live |= 1u << d;
+    for (bool done = false; !done;) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        if (done) continue;
+        if (!(live & (1u << d))) {
+          done = true;
+          continue;
+        }
+        consume(rj[d], rv[d], ra[d]);
+        if (aborted) {
+          done = true;
+          continue;
+        }
+        if (produce(rj[d], rv[d], ra[d])) live |= 1u << d;
+        else live &= ~(1u << d);
+      }
+    }
+    if (aborted) {
+      if (lane == 0) {
+        const int p = atomicAdd(fb_count, 1);
+        fb_list[p] = r;
+      }
+      __syncwarp();
+      continue;
+    }
+
+    // ---- epilogue: groups in column order, lane -> column
+    int ng = 0;
+    for (int c = 0; c < G; c += 32) {
+      const unsigned e = gtab[c + lane];
+      const bool used = e != 0xFFFFFFFFu;
+      const unsigned m = __ballot_sync(kFull, used);
+      __syncwarp();
+      if (used) gtab[ng + __popc(m & lt)] = e;
+      ng += __popc(m);
+    }
+    {
+      int P = 32;
+      while (P < ng) P <<= 1;
+      for (int s2 = ng + lane; s2 < P; s2 += 32) gtab[s2] = 0xFFFFFFFFu;
+      __syncwarp();
+      for (int k = 2; k <= P; k <<= 1)
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+          for (int e = lane; e < (P >> 1); e += 32) {
+            const int i = ((e & ~(jj - 1)) << 1) | (e & (jj - 1));
+            const unsigned x = gtab[i], y = gtab[i + jj];
+            if ((x > y) == ((i & k) == 0)) { gtab[i] = y; gtab[i + jj] = x; }
+          }
+          __syncwarp();
+        }
+    }
+    const auto tb = mag_bits(tau);
+    int nk = 0;
+    double dsum = 0.0, fsum = 0.0;
+    int *oi = Out.idx + (size_t)r * Out.w;
+    T *ov = Out.val + (size_t)r * Out.w;
+    constexpr int GPP = 32 / GW;
+    for (int c = 0; c < ng; c += GPP) {
+      const int gi = c + lane / GW;
+      bool keep = false;
+      int j = 0;
+      T v = T(0);
+      if (gi < ng) {
+        const unsigned e = gtab[gi];
+        const int b = (int)(e & 0xFFu);
+        j = (int)((e >> 8) << GSH) + (lane & (GW - 1));
+        v = vals[b * GW + (lane & (GW - 1))];
+        keep = KEEPZ ? !is_untouched(v) : mag_bits(v) > tb;
+      }
+      const unsigned m = __ballot_sync(kFull, keep);
+      if (keep) {
+        const int pos = nk + __popc(m & lt);
+        if (pos < Out.w) { oi[pos] = j; ov[pos] = v; }
+        const double dv = (double)v;
+        if (j == r) dsum += dv;
+        fsum = fma(dv, dv, fsum);
+      }
+      nk += __popc(m);
+    }
+    dsum = warp_sum(dsum);
+    fsum = warp_sum(fsum);
+    wmax = max(wmax, nk);
+    if (lane == 0) {
+      if (nk > Out.w) {
+        ++wover;
+        rowstat[r] = make_double2(0.0, 0.0);
+      } else {
+        Out.nnz[r] = nk;
+        rowstat[r] = make_double2(dsum, fsum);
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (wmax) atomicMax(&ctl->max_count, wmax);
+    if (wover) atomicAdd(&ctl->overflow_rows, wover);
+  }
+}
+
 // ------------------------------------------------------------------ large rows
 // One CTA per deferred row: accumulate into a dense row of n values in global memory
 // (per-CTA slot; marks start at -1 and accumulators at 0 and are restored after use),
@@ -1390,6 +1665,43 @@ int launch_super(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
   return SP2_OK;
 }
 
+template <typename T, int D, bool KEEPZ>
+int launch_stream(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
+  using Geo = StreamGeo<T>;
+  auto kern = spgemm_stream_kernel<T, D, KEEPZ>;
+  static bool attr_set[64] = {false};
+  static int occ_cache[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!attr_set[dev]) {
+    SP2_TRY(set_smem(kern, Geo::SMEM));
+    int occ = 0;
+    SP2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Geo::ROWS * 32, Geo::SMEM));
+    occ_cache[dev] = occ < 1 ? 1 : occ;
+    attr_set[dev] = true;
+  }
+  const long long cap = (long long)num_sms() * occ_cache[dev];
+  const long long blocks = ((long long)a.A->n + Geo::ROWS - 1) / Geo::ROWS;
+  int grid = (int)(blocks < cap ? blocks : cap);
+  if (grid < 1) grid = 1;
+  const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
+  prof_begin(SP2_PROF_SPGEMM, s);
+  kern<<<grid, Geo::ROWS * 32, Geo::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
+                                              (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv,
+                                              rowstat, ctl, fb, fb_count);
+  note_launch();
+  prof_end(SP2_PROF_SPGEMM, s);
+  SP2_CUDA(cudaGetLastError());
+  return SP2_OK;
+}
+
+template <typename T>
+int launch_stream_auto(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
+  return a.tau == 0.0 ? launch_stream<T, 8, true>(a, rowstat, ctl, fb, fb_count, s)
+                      : launch_stream<T, 8, false>(a, rowstat, ctl, fb, fb_count, s);
+}
+
 template <typename T>
 int launch_super_auto(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
   constexpr int QM = sizeof(T) == 8 ? 6 : 6;
@@ -1419,6 +1731,7 @@ int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
     case 12: rc = launch_hash<T, 12, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s); break;
     case 2: rc = launch_block_r<T, 2>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 3: rc = launch_super_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
+    case 5: rc = launch_stream_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     default:  // automatic: the variant measured fastest on the 3D tight-binding products
               // (FP64: 4 warps per row; FP32: one warp per row, two k steps per pass)
       rc = sizeof(T) == 8 ? launch_block_r<T, 4>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)

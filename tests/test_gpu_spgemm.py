@@ -264,11 +264,12 @@ def test_x0(gpu, tau):
         assert np.allclose(gv[i, :gn[i]], ref.row(i)[1], rtol=5e-16, atol=1e-300)
 
 
-@pytest.mark.parametrize("first_pass", [0, 1, 2, 3, 4, 11])
+@pytest.mark.parametrize("first_pass", [0, 1, 2, 3, 4, 5, 11])
 @pytest.mark.parametrize("fp32", [False, True])
 def test_first_pass_variants(gpu, first_pass, fp32):
-    """Both first-pass accumulators (column blocks, per-warp hash table) on one SP2 step of
-    a gapped tight-binding X."""
+    """Every first-pass variant (column blocks with 1, 2, 4 warps per row, the two-step
+    and the chunk-stream one-warp variants, a per-warp hash table) on one SP2 step of a
+    gapped tight-binding X; a second run is bitwise identical."""
     S = gpu
     n = 5000
     H = ell(I.tight_binding(n, seed=6, delta=10.0))
@@ -286,6 +287,10 @@ def test_first_pass_variants(gpu, first_pass, fp32):
     up = info.branch == 2
     compare_spgemm(out.to_numpy(), X1, X1, X1, -1.0 if up else 1.0, 2.0 if up else 0.0, 1e-5, fp32=fp32)
     assert info.rows_deferred == 0
+    again = S.Ellpack.empty(n, out.width, dt)
+    S.sp2_step(d1, again, n / 2, 1e-5, spgemm_path=first_pass)
+    for a, b in zip(out.to_numpy(), again.to_numpy()):
+        assert np.array_equal(np.nan_to_num(a), np.nan_to_num(b))
 
 
 def hub_matrix(n, hubs, hub_nnz, other_nnz, seed):
@@ -301,19 +306,21 @@ def hub_matrix(n, hubs, hub_nnz, other_nnz, seed):
     return O.Ell(*I.coo_to_ellpack(n, rows, cols, vals))
 
 
-def test_all_three_passes(gpu):
+@pytest.mark.parametrize("first_pass", [0, 5])
+def test_all_three_passes(gpu, first_pass):
     """Rows with more column groups than the block accumulator holds go to the 2^14-slot
     table; rows with more distinct columns than that go to the dense global-row pass.
-    Sampled rows (all hubs included) against the oracle."""
+    Sampled rows (all hubs included) against the oracle (tau = 0: every structural entry
+    is kept)."""
     S = gpu
     n = 20000
     hubs = set(range(0, n, 2000)) | {n - 1}
     X = hub_matrix(n, hubs, 1000, 40, seed=3)
     dX = dev(S, X)
     probe = S.Ellpack.empty(n, 32)
-    rc, info = S.sp2_step(dX, probe, n / 2, 0.0, raise_on_overflow=False)
+    rc, info = S.sp2_step(dX, probe, n / 2, 0.0, spgemm_path=first_pass, raise_on_overflow=False)
     out = S.Ellpack.empty(n, ((info.required_width + 31) // 32) * 32)
-    info = S.sp2_step(dX, out, n / 2, 0.0)
+    info = S.sp2_step(dX, out, n / 2, 0.0, spgemm_path=first_pass)
     assert info.rows_deferred > len(hubs) and info.rows_dense >= len(hubs)
     up = info.branch == 2
     rng = np.random.default_rng(4)

@@ -404,6 +404,21 @@ template <> __device__ __forceinline__ float untouched<float>() { return __uint_
 template <int LOG2G>
 __device__ __forceinline__ int ghash(unsigned g) { return (int)((g * 0x9E3779B1u) >> (32 - LOG2G)); }
 
+// Block of group g, or -1 when g is not in the table (probes until a hit or an empty
+// entry; a probe longer than 16 also answers -1 and the slow path finds the group).
+template <int LOG2G>
+__device__ __forceinline__ int probe_block(const unsigned *gtab, unsigned g) {
+  int h = ghash<LOG2G>(g);
+#pragma unroll 1
+  for (int p = 0; p < 16; ++p) {
+    const unsigned e = ((const volatile unsigned *)gtab)[h];
+    if ((e >> 8) == g) return (int)(e & 0xFFu);
+    if (e == 0xFFFFFFFFu) return -1;
+    h = (h + 1) & ((1 << LOG2G) - 1);
+  }
+  return -1;
+}
+
 // Group -> block, taking a fresh (pre-cleared) block when the group is new.  Lanes of
 // different warps may race for the same group: the CAS keeps the first block, the other
 // one stays unused.  Returns -1 when the blocks are used up.
@@ -1039,21 +1054,6 @@ struct StreamGeo {
   static constexpr unsigned MAX_GROUP = (1u << 24) - 1u;
   static_assert(G == BlockGeo<T, 1>::G && NB == BlockGeo<T, 1>::NB, "one group table layout");
 };
-
-// Block of group g, or -1 when g is not in the table (probes until a hit or an empty
-// entry; a probe longer than 16 also answers -1 and the slow path finds the group).
-template <int LOG2G>
-__device__ __forceinline__ int probe_block(const unsigned *gtab, unsigned g) {
-  int h = ghash<LOG2G>(g);
-#pragma unroll 1
-  for (int p = 0; p < 16; ++p) {
-    const unsigned e = ((const volatile unsigned *)gtab)[h];
-    if ((e >> 8) == g) return (int)(e & 0xFFu);
-    if (e == 0xFFFFFFFFu) return -1;
-    h = (h + 1) & ((1 << LOG2G) - 1);
-  }
-  return -1;
-}
 
 template <typename T, int D, bool KEEPZ>
 __global__ void __launch_bounds__(StreamGeo<T>::ROWS * 32, 1)

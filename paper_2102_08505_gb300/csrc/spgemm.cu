@@ -1033,17 +1033,20 @@ __global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
   }
 }
 
-// ------------------------------------------------------------------ stream first pass
-// One warp per output row.  The row's gather -- the addend row C_i (coefficient beta),
-// then row k of B for every entry a_ik of A's row (coefficient alpha * a_ik) -- is one
-// flat stream of 32-entry chunks, loaded D chunks ahead into a ring of registers.  Per
-// chunk every lane finds its column's block by a short linear probe of the group table
-// (a group seen for the first time takes the slow path once: one elected lane per group
-// claims a block), then does one load-FMA-store.  Chunks are consumed in stream order
-// with a __syncwarp between them, so every output entry accumulates its terms in source
-// order (deterministic) and no barrier spans warps.
+// ------------------------------------------------------------------ run first pass
+// One warp per output row.  Each source row of the gather (the addend row C_i, then row
+// k of B for every entry a_ik) is split into 32 runs of consecutive entries, one run per
+// lane (PER = ceil(nb / 32) entries; rows longer than 32 * kRunMax go in rounds of that
+// size).  A sorted row's consecutive entries mostly share a column group, so a lane looks
+// its group up once per change of group, and the warp-level work per source row
+// (shuffles, addresses, branches) is paid once per row instead of once per 32 entries.
+// Source rows are loaded two ahead into registers.  Within a source row the columns are
+// distinct, so lanes never update the same slot; a __syncwarp between source rows orders
+// them, and every output entry accumulates its terms in source order (deterministic).
+constexpr int kRunMax = 8;
+
 template <typename T>
-struct StreamGeo {
+struct RunGeo {
   static constexpr int GSH = BlockCfg<T>::GSH, GW = 1 << GSH, NB = BlockCfg<T>::NB;
   static constexpr int LOG2G = BlockCfg<T>::LOG2G, G = 1 << LOG2G;
   static constexpr int VAL_BYTES = NB * GW * (int)sizeof(T);
@@ -1055,13 +1058,26 @@ struct StreamGeo {
   static_assert(G == BlockGeo<T, 1>::G && NB == BlockGeo<T, 1>::NB, "one group table layout");
 };
 
-template <typename T, int D, bool KEEPZ>
-__global__ void __launch_bounds__(StreamGeo<T>::ROWS * 32, 1)
-    spgemm_stream_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
-                         int use_add, BatchView bv, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
-                         int *__restrict__ fb_list, int *__restrict__ fb_count) {
-  using Geo = StreamGeo<T>;
+// One source row's first round, held by the warp: lane's run of cnt entries, the run
+// length per of the round (uniform), the coefficient, and the row for later rounds.
+template <typename T>
+struct RunBuf {
+  int j[kRunMax];
+  T v[kRunMax];
+  int per, cnt, nb;
+  T a;
+  const int *ri;
+  const T *rv;
+};
+
+template <typename T, bool KEEPZ>
+__global__ void __launch_bounds__(RunGeo<T>::ROWS * 32, 1)
+    spgemm_run_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
+                      int use_add, BatchView bv, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
+                      int *__restrict__ fb_list, int *__restrict__ fb_count) {
+  using Geo = RunGeo<T>;
   constexpr int GW = Geo::GW, GSH = Geo::GSH, G = Geo::G;
+  constexpr int ROUND = 32 * kRunMax;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned char *base = smem + (size_t)wid * Geo::BYTES_PER_ROW;
@@ -1094,122 +1110,151 @@ __global__ void __launch_bounds__(StreamGeo<T>::ROWS * 32, 1)
     }
     __syncwarp();
 
-    // ---- producer: the flat chunk stream of this row
     const int na = min(A.nnz[r], A.w);
     const int ns = na + (add_r ? 1 : 0);  // sources: [addend row], then the rows of B
     const int *arow_i = A.idx + (size_t)r * A.w;
     const T *arow_v = A.val + (size_t)r * A.w;
-    int pk = 0, pnb = 0, pbase = -32;  // A entries pbase .. pbase+31, one per lane
+    int pk = 0, pnb = 0, pbase = -32;  // A entries pbase .. pbase+31 (k, nb(B_k), alpha*a), one per lane
     T pa = T(0);
-    int ps = 0, pq = 0, p_nb = 0;
-    const int *p_ri = B.idx;
-    const T *p_rv = B.val;
-    T p_a = T(0);
-    auto seek = [&]() {  // ps -> the first source at or after ps with entries (or ns)
-      while (ps < ns) {
-        if (add_r && ps == 0) {
-          p_ri = Add.idx + (size_t)r * Add.w;
-          p_rv = Add.val + (size_t)r * Add.w;
-          p_nb = min(Add.nnz[r], Add.w);
-          p_a = beta_r;
+
+    // run of this lane in a round of n entries starting at entry off of row (ri, rv)
+    auto load_run = [&](const int *ri, const T *rv, int off, int n, int &per, int &cnt, int (&jr)[kRunMax],
+                        T (&vr)[kRunMax]) {
+      per = (n + 31) >> 5;
+      const int s0 = lane * per;
+      cnt = max(0, min(per, n - s0));
+#pragma unroll
+      for (int i = 0; i < kRunMax; ++i) {
+        jr[i] = i < cnt ? __ldg(ri + off + s0 + i) : -1;
+        vr[i] = i < cnt ? __ldg(rv + off + s0 + i) : T(0);
+      }
+    };
+    // source s -> buffer (first round loaded); s >= ns gives an empty buffer
+    auto load_src = [&](int s, RunBuf<T> &bf) {
+      bf.nb = 0; bf.a = T(0); bf.ri = B.idx; bf.rv = B.val;
+      if (s < ns) {
+        if (add_r && s == 0) {
+          bf.ri = Add.idx + (size_t)r * Add.w;
+          bf.rv = Add.val + (size_t)r * Add.w;
+          bf.nb = min(Add.nnz[r], Add.w);
+          bf.a = beta_r;
         } else {
-          const int t = ps - add_r;
+          const int t = s - add_r;
           if (t >= pbase + 32) {
             pbase = t & ~31;
-            const int s = pbase + lane;
+            const int q = pbase + lane;
             pk = 0; pnb = 0; pa = T(0);
-            if (s < na) {
-              const int k = __ldg(arow_i + s);
+            if (q < na) {
+              const int k = __ldg(arow_i + q);
               if ((unsigned)k < (unsigned)B.n) {
                 pk = k;
-                pa = alpha_r * __ldg(arow_v + s);
+                pa = alpha_r * __ldg(arow_v + q);
                 pnb = min(__ldg(B.nnz + k), B.w);
               }
             }
           }
           const int k = __shfl_sync(kFull, pk, t & 31);
-          p_nb = __shfl_sync(kFull, pnb, t & 31);
-          p_a = __shfl_sync(kFull, pa, t & 31);
-          p_ri = B.idx + (size_t)k * B.w;
-          p_rv = B.val + (size_t)k * B.w;
+          bf.nb = __shfl_sync(kFull, pnb, t & 31);
+          bf.a = __shfl_sync(kFull, pa, t & 31);
+          bf.ri = B.idx + (size_t)k * B.w;
+          bf.rv = B.val + (size_t)k * B.w;
         }
-        if (p_nb > 0) return;
-        ++ps;
       }
-    };
-    auto produce = [&](int &j, T &v, T &a) -> bool {
-      if (ps >= ns) {
-        j = -1; v = T(0); a = T(0);
-        return false;
-      }
-      const int q = pq + lane;
-      j = q < p_nb ? __ldg(p_ri + q) : -1;
-      v = q < p_nb ? __ldg(p_rv + q) : T(0);
-      a = p_a;
-      pq += 32;
-      if (pq >= p_nb) {
-        pq = 0;
-        ++ps;
-        seek();
-      }
-      return true;
+      load_run(bf.ri, bf.rv, 0, min(bf.nb, ROUND), bf.per, bf.cnt, bf.j, bf.v);
     };
 
-    // ---- consumer: one chunk into the blocks
     bool aborted = false;
-    auto consume = [&](int j, T v, T a) {
-      int slot = -1;
-      bool miss = false;
-      if ((unsigned)j < (unsigned)ncol) {
-        const int b = probe_block<Geo::LOG2G>(gtab, (unsigned)j >> GSH);
-        if (b >= 0) slot = b * GW + (j & (GW - 1));
-        else miss = true;
+    // accumulate one round held in registers: lookups once per change of group, claims
+    // for new groups (one elected lane per group), then one load-FMA-store per entry
+    auto accumulate = [&](auto per_c, int cnt, const int (&jr)[kRunMax], const T (&vr)[kRunMax], T a) {
+      constexpr int PER = decltype(per_c)::value;
+      int bk[PER];
+      unsigned miss = 0;
+      unsigned gp = 0xFFFFFFFFu;
+      int bp = -1;
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        bk[i] = -2;
+        if (i < cnt && (unsigned)jr[i] < (unsigned)ncol) {
+          const unsigned g = (unsigned)jr[i] >> GSH;
+          if (g != gp) {
+            gp = g;
+            bp = probe_block<Geo::LOG2G>(gtab, g);
+          }
+          bk[i] = bp;
+          if (bp < 0) miss |= 1u << i;
+        }
       }
-      const unsigned need = __ballot_sync(kFull, miss);
-      if (need) {  // groups seen for the first time: one elected lane per group claims a block
-        if (miss) {
-          const unsigned g = (unsigned)j >> GSH;
-          const unsigned peers = __match_any_sync(need, g);
+      while (__any_sync(kFull, miss != 0)) {
+        const int i0 = miss ? __ffs(miss) - 1 : -1;
+        unsigned g = 0;
+#pragma unroll
+        for (int i = 0; i < PER; ++i)
+          if (i == i0) g = (unsigned)jr[i] >> GSH;
+        const unsigned act = __ballot_sync(kFull, i0 >= 0);
+        if (i0 >= 0) {
+          const unsigned peers = __match_any_sync(act, g);
           const int leader = __ffs(peers) - 1;
           int b = -1;
           if (lane == leader) b = g < Geo::MAX_GROUP ? group_block<T, 1>(gtab, nblk, g) : -1;
           b = __shfl_sync(peers, b, leader);
-          if (b >= 0) slot = b * GW + (j & (GW - 1));
-          else aborted = true;
+          if (b < 0) aborted = true;
+#pragma unroll
+          for (int i = 0; i < PER; ++i)
+            if ((miss >> i) & 1u && ((unsigned)jr[i] >> GSH) == g) {
+              bk[i] = b;
+              miss &= ~(1u << i);
+            }
         }
-        aborted = __any_sync(kFull, aborted);
+        __syncwarp();
       }
-      if (slot >= 0) {
-        const T o0 = vals[slot];
-        const T o = (KEEPZ && is_untouched(o0)) ? T(0) : o0;
-        vals[slot] = fmadd(a, v, o);
+#pragma unroll
+      for (int i = 0; i < PER; ++i)
+        if (bk[i] >= 0) {
+          const int slot = bk[i] * GW + (jr[i] & (GW - 1));
+          const T o0 = vals[slot];
+          const T o = (KEEPZ && is_untouched(o0)) ? T(0) : o0;
+          vals[slot] = fmadd(a, vr[i], o);
+        }
+    };
+    auto accumulate_any = [&](int per, int cnt, const int (&jr)[kRunMax], const T (&vr)[kRunMax], T a) {
+      switch (per) {
+        case 0: break;
+        case 1: accumulate(std::integral_constant<int, 1>{}, cnt, jr, vr, a); break;
+        case 2: accumulate(std::integral_constant<int, 2>{}, cnt, jr, vr, a); break;
+        case 3: accumulate(std::integral_constant<int, 3>{}, cnt, jr, vr, a); break;
+        case 4: accumulate(std::integral_constant<int, 4>{}, cnt, jr, vr, a); break;
+        case 5: accumulate(std::integral_constant<int, 5>{}, cnt, jr, vr, a); break;
+        case 6: accumulate(std::integral_constant<int, 6>{}, cnt, jr, vr, a); break;
+        case 7: accumulate(std::integral_constant<int, 7>{}, cnt, jr, vr, a); break;
+        default: accumulate(std::integral_constant<int, kRunMax>{}, cnt, jr, vr, a); break;
       }
-      __syncwarp();  // this chunk's updates land before the next chunk reads
+    };
+    auto process = [&](const RunBuf<T> &bf) {
+      accumulate_any(bf.per, bf.cnt, bf.j, bf.v, bf.a);
+      __syncwarp();
+      for (int off = ROUND; off < bf.nb && !aborted; off += ROUND) {  // rows longer than one round
+        int per, cnt, jt[kRunMax];
+        T vt[kRunMax];
+        load_run(bf.ri, bf.rv, off, min(bf.nb - off, ROUND), per, cnt, jt, vt);
+        accumulate_any(per, cnt, jt, vt, bf.a);
+        __syncwarp();
+      }
+      aborted = __any_sync(kFull, aborted);
     };
 
-    seek();
-    int rj[D];
-    T rv[D], ra[D];
-    unsigned live = 0;
-#pragma unroll
-    for (int d = 0; d < D; ++d)
-      if (produce(rj[d], rv[d], ra[d])) live |= 1u << d;
-    for (bool done = false; !done;) {
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        if (done) continue;
-        if (!(live & (1u << d))) {
-          done = true;
-          continue;
-        }
-        consume(rj[d], rv[d], ra[d]);
-        if (aborted) {
-          done = true;
-          continue;
-        }
-        if (produce(rj[d], rv[d], ra[d])) live |= 1u << d;
-        else live &= ~(1u << d);
-      }
+    RunBuf<T> b0, b1, b2;
+    load_src(0, b0);
+    load_src(1, b1);
+    for (int s = 0; s < ns && !aborted; s += 3) {
+      load_src(s + 2, b2);
+      process(b0);
+      if (s + 1 >= ns || aborted) break;
+      load_src(s + 3, b0);
+      process(b1);
+      if (s + 2 >= ns || aborted) break;
+      load_src(s + 4, b1);
+      process(b2);
     }
     if (aborted) {
       if (lane == 0) {
@@ -1665,10 +1710,10 @@ int launch_super(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
   return SP2_OK;
 }
 
-template <typename T, int D, bool KEEPZ>
-int launch_stream(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
-  using Geo = StreamGeo<T>;
-  auto kern = spgemm_stream_kernel<T, D, KEEPZ>;
+template <typename T, bool KEEPZ>
+int launch_run(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
+  using Geo = RunGeo<T>;
+  auto kern = spgemm_run_kernel<T, KEEPZ>;
   static bool attr_set[64] = {false};
   static int occ_cache[64] = {0};
   int dev = 0;
@@ -1697,9 +1742,9 @@ int launch_stream(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *
 }
 
 template <typename T>
-int launch_stream_auto(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
-  return a.tau == 0.0 ? launch_stream<T, 8, true>(a, rowstat, ctl, fb, fb_count, s)
-                      : launch_stream<T, 8, false>(a, rowstat, ctl, fb, fb_count, s);
+int launch_run_auto(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
+  return a.tau == 0.0 ? launch_run<T, true>(a, rowstat, ctl, fb, fb_count, s)
+                      : launch_run<T, false>(a, rowstat, ctl, fb, fb_count, s);
 }
 
 template <typename T>
@@ -1731,7 +1776,7 @@ int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
     case 12: rc = launch_hash<T, 12, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s); break;
     case 2: rc = launch_block_r<T, 2>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 3: rc = launch_super_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
-    case 5: rc = launch_stream_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
+    case 5: rc = launch_run_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     default:  // automatic: the variant measured fastest on the 3D tight-binding products
               // (FP64: 4 warps per row; FP32: one warp per row, two k steps per pass)
       rc = sizeof(T) == 8 ? launch_block_r<T, 4>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)

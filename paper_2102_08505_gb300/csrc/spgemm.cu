@@ -4,20 +4,26 @@
 // "Performance Evaluation using System Matrices" with the "SP2 Loop Misc" update fused
 // into its epilogue (Section "Performance Evaluation using an ExaSP2 Application").
 //
-// Design (GB300): one warp per output row.  The warp walks row i of A; for every k it
-// streams row k of B (coalesced 32-wide loads, prefetched one k ahead into registers)
-// and accumulates a_ik * b_kj into a warp-private open-addressing hash table in shared
-// memory.  Within one k the columns j are distinct, so lanes never update the same slot
-// concurrently; a __syncwarp between k steps orders the steps, and the accumulation is a
-// plain load-FMA-store (one FMA per product, no floating-point atomics).  The slot of
-// column j keeps j's low bits and rotates each aligned block of 2^LOG2T columns by a
-// multiplicative hash of the block number, so consecutive columns -- the common case for
-// Morton-ordered sites -- land in consecutive slots and therefore distinct banks.
-// The epilogue compacts the table in place (drop rule), sorts the survivors by column
-// with a bitonic network, writes the row, and records the row's diagonal value and sum
-// of squares for the FP64 traces of the next SP2 iteration.
-// Rows whose pattern outgrows half the table are deferred to a second kernel that
-// accumulates into a dense global-memory row (one CTA per row), so no row size fails.
+// Design (GB300).  Row-wise Gustavson: output row i accumulates alpha * a_ik * B_k (and
+// beta * Add_i) in shared memory, then the epilogue applies the drop rule, writes the row
+// sorted by column, and records the row's diagonal value and sum of squares for the FP64
+// traces of the next SP2 iteration.  No floating-point atomics: every output entry sums
+// its terms in a fixed order, so results are bitwise reproducible.
+//
+// First pass (one of several variants that compute the same product; the tuner or the
+// caller picks one):
+//  - column blocks (paths 1, 2, 4): a row's output columns are grouped in runs of GW (16
+//    for FP64, 32 for FP32); a per-row group table in shared memory maps a group to a
+//    block of GW accumulator slots (claimed on first touch), so column j sits in bank
+//    j mod 32.  R warps share a row and split each source row's entries, with a named
+//    barrier between source rows.
+//  - two-step (path 3): one warp per row, two source rows per pass.
+//  - runs (path 5): one warp per row, each lane takes a run of consecutive entries of a
+//    source row and looks its group up once per change of group.
+//  - hash (paths 10..12): a per-warp open-addressing table of 2^path slots.
+// Rows whose groups outgrow the table are deferred to a one-warp 2^14-slot hash table
+// (bin 1), and rows beyond that to a dense global-memory row per CTA (bin 2), so no row
+// size fails.
 #include <limits.h>
 #include <math.h>
 
@@ -1210,7 +1216,7 @@ __global__ void __launch_bounds__(RunGeo<T>::ROWS * 32, 1)
       }
 #pragma unroll
       for (int i = 0; i < PER; ++i)
-        if (bk[i] >= 0) {
+        if ((unsigned)bk[i] < (unsigned)Geo::NB) {
           const int slot = bk[i] * GW + (jr[i] & (GW - 1));
           const T o0 = vals[slot];
           const T o = (KEEPZ && is_untouched(o0)) ? T(0) : o0;
@@ -1230,17 +1236,20 @@ __global__ void __launch_bounds__(RunGeo<T>::ROWS * 32, 1)
         default: accumulate(std::integral_constant<int, kRunMax>{}, cnt, jr, vr, a); break;
       }
     };
+    // (aborted is set by single lanes; it is made warp-uniform before every test of it,
+    // since the code it guards uses whole-warp shuffles and votes)
     auto process = [&](const RunBuf<T> &bf) {
       accumulate_any(bf.per, bf.cnt, bf.j, bf.v, bf.a);
-      __syncwarp();
+      __syncwarp();  // this source row's updates land before the next one reads
+      aborted = __any_sync(kFull, aborted);
       for (int off = ROUND; off < bf.nb && !aborted; off += ROUND) {  // rows longer than one round
         int per, cnt, jt[kRunMax];
         T vt[kRunMax];
         load_run(bf.ri, bf.rv, off, min(bf.nb - off, ROUND), per, cnt, jt, vt);
         accumulate_any(per, cnt, jt, vt, bf.a);
         __syncwarp();
+        aborted = __any_sync(kFull, aborted);
       }
-      aborted = __any_sync(kFull, aborted);
     };
 
     RunBuf<T> b0, b1, b2;

@@ -49,7 +49,8 @@ def parse():
                         "model Hamiltonians at N=32000")
     p.add_argument("--count", type=int, default=256)
     p.add_argument("--path", type=int, default=0,
-                   help="SpGEMM first pass: 0 automatic, 1/2/4 column blocks with R warps per row, 10-12 hash")
+                   help="SpGEMM first pass: 0 automatic, 1/2/4/6 column blocks with 1/2/4/5 warps per row, 3 two-step, "
+                        "5 runs, 10-12 hash, -1 tuned")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
@@ -230,8 +231,13 @@ def spgemm_kernel_name(a):
     p = a.path
     if p == 0:
         p = 4 if a.dtype == "f64" else 3
-    if p in (1, 2, 4):
-        return "spgemm_block_kernel (%d warp%s per row)" % (p, "s" if p > 1 else "")
+    if p in (1, 2, 4, 6):
+        w = 5 if p == 6 else p
+        return "spgemm_block_kernel (%d warp%s per row)" % (w, "s" if w > 1 else "")
+    if p == 5:
+        return "spgemm_run_kernel (one warp per row, a run of entries per lane)"
+    if p == -1:
+        return "tuned first pass"
     if p == 3:
         return "spgemm_super_kernel (one warp per row, two k steps per pass)"
     return "spgemm_hash_kernel (2^%d slots per warp)" % p

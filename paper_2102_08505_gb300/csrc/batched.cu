@@ -384,9 +384,9 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
     return fail(SP2E_ARG, "sp2_purify_batched: unknown precision %d", opt.precision);
   if (opt.max_iter < 0 || opt.max_iter + opt.n_fp64_tail >= SP2_STATS_CAP || opt.n_fp64_tail < 0)
     return fail(SP2E_ARG, "sp2_purify_batched: bad max_iter / n_fp64_tail");
-  if (!(opt.spgemm_path == SP2_PATH_TUNED || (opt.spgemm_path >= 0 && opt.spgemm_path <= 5) ||
+  if (!(opt.spgemm_path == SP2_PATH_TUNED || (opt.spgemm_path >= 0 && opt.spgemm_path <= 6) ||
         (opt.spgemm_path >= 10 && opt.spgemm_path <= 12)))
-    return fail(SP2E_ARG, "sp2_purify_batched: spgemm_path must be -1, 0..5 or 10..12");
+    return fail(SP2E_ARG, "sp2_purify_batched: spgemm_path must be -1, 0..6 or 10..12");
   long long ntot_ll = 0;
   int wh = 1, nmax = 0;
   std::vector<int> off(count + 1, 0);

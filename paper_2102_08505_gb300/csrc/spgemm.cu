@@ -12,7 +12,7 @@
 //
 // First pass (one of several variants that compute the same product; the tuner or the
 // caller picks one):
-//  - column blocks (paths 1, 2, 4): a row's output columns are grouped in runs of GW (16
+//  - column blocks (paths 1, 2, 4, 6 = 5 warps): a row's output columns are grouped in runs of GW (16
 //    for FP64, 32 for FP32); a per-row group table in shared memory maps a group to a
 //    block of GW accumulator slots (claimed on first touch), so column j sits in bank
 //    j mod 32.  R warps share a row and split each source row's entries, with a named
@@ -391,7 +391,9 @@ struct BlockGeo {
   static constexpr int VAL_BYTES = NB * GW * (int)sizeof(T);
   static constexpr int BYTES_PER_GROUP = VAL_BYTES + G * 4 + 16;
   static constexpr int GROUPS_RAW = 232192 / BYTES_PER_GROUP;
-  static constexpr int GROUPS_MAX = (sizeof(T) == 4 ? 10 : 16) / (R > 2 ? 2 : 1);
+  // at most 32 warps per CTA (1024 threads)
+  static constexpr int GROUPS_MAX0 = (sizeof(T) == 4 ? 12 : 16) / (R > 2 ? 2 : 1);
+  static constexpr int GROUPS_MAX = GROUPS_MAX0 < 32 / R ? GROUPS_MAX0 : 32 / R;
   static constexpr int GROUPS = GROUPS_RAW > GROUPS_MAX ? GROUPS_MAX : (GROUPS_RAW < 1 ? 1 : GROUPS_RAW);
   static constexpr int WARPS = GROUPS * R;
   static constexpr int SMEM = GROUPS * BYTES_PER_GROUP;
@@ -1780,6 +1782,7 @@ int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
   switch (path) {
     case 1: rc = launch_block_r<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 4: rc = launch_block_r<T, 4>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
+    case 6: rc = launch_block_r<T, 5>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 10: rc = launch_hash<T, 10, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s); break;
     case 11: rc = launch_hash<T, 11, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s); break;
     case 12: rc = launch_hash<T, 12, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s); break;

@@ -42,11 +42,11 @@ def parse():
     p.add_argument("--tau", type=float, default=1e-6)
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--workload", default="spgemm", choices=["spgemm", "sp2", "batched", "sizing", "model"],
+    p.add_argument("--workload", default="spgemm", choices=["spgemm", "sp2", "batched", "sizing", "model", "schedule"],
                    help="spgemm: one SP2 iteration at N=262144 (default); sp2: whole purifications, FP64 vs "
                         "mixed at N=131072; batched: 256 clusters in one graph launch vs one by one; sizing: "
                         "heuristic vs structural vs MLP output widths for mixed SP2 at N=1048576; model: the paper's "
-                        "model Hamiltonians at N=32000")
+                        "model Hamiltonians at N=32000; schedule: stall-rule and precision-schedule variants")
     p.add_argument("--count", type=int, default=256)
     p.add_argument("--path", type=int, default=0,
                    help="SpGEMM first pass: 0 automatic, 1/2/4/6 column blocks with 1/2/4/5 warps per row, 3 two-step, "
@@ -562,6 +562,45 @@ def run_model(a):
                       **out}), flush=True)
 
 
+def run_schedule(a):
+    """Stopping-rule and precision-schedule variants of SP2 on the gapped 3D tight-binding H
+    (N=131072, tau=1e-5, tol=1e-10): the stall rule's arming threshold for FP64, and the
+    FP32 -> FP64 switch point and tail length for mixed precision; time to solution and
+    distance to the FP64 result."""
+    import torch
+    from paper_2102_08505_gb300 import inputs as I
+    from paper_2102_08505_gb300 import sp2ell as S
+    n = a.n
+    tau = a.tau if a.tau != 1e-6 else 1e-5
+    idx, val, nnz = I.tight_binding(n, seed=a.seed, delta=10.0)
+    H = S.Ellpack.from_numpy(idx, val, nnz)
+
+    def timed(opt):
+        S.sp2_purify(H, n / 2, 1e-10, opt, allow_notconv=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        D, st = S.sp2_purify(H, n / 2, 1e-10, opt, allow_notconv=True)
+        torch.cuda.synchronize()
+        return D, st, time.perf_counter() - t0
+
+    out = {}
+    ref = None
+    for arm in (0.1, 0.01, 1.0):
+        D, st, dt = timed(S.sp2_options_default(tau=tau, stall_arm=arm))
+        if arm == 0.1:
+            ref = D
+        out["f64_stall_arm_%g" % arm] = {"time_s": dt, "iterations": st["iterations"], "status": st["status"],
+                                          "final_err": float(st["err"][-1])}
+    for name, sw, tail in (("switch_1e-6_tail_2", 1e-6, 2), ("switch_1e-4_tail_2", 1e-4, 2),
+                           ("switch_1e-8_tail_2", 1e-8, 2), ("switch_at_fp32_stall_tail_2", 1e-300, 2),
+                           ("switch_1e-6_tail_1", 1e-6, 1), ("switch_1e-6_tail_4", 1e-6, 4)):
+        D, st, dt = timed(S.sp2_options_default(tau=tau, precision=S.SP2_PREC_MIXED, switch_tol=sw, n_fp64_tail=tail))
+        out["mixed_" + name] = {"time_s": dt, "iterations": st["iterations"], "fp32_iterations": st["fp32_iterations"],
+                                "status": st["status"], "dD_vs_f64": diff_fro(S, D, ref) / np.sqrt(n)}
+    print(json.dumps({"workload": "SP2 schedule variants, 3D tight-binding gapped N=%d tau=%g tol=1e-10" % (n, tau),
+                      **out}), flush=True)
+
+
 def run_sizing(a):
     """Output sizing of the SP2 products: heuristic widths with regrow, exact structural
     counts before every multiply, and the row-length MLP (trained on about 50k rows of
@@ -627,7 +666,7 @@ def run_sizing(a):
 def main():
     a = parse()
     if a.n is None:
-        a.n = {"sp2": 131072, "sizing": 1048576, "model": 32000}.get(a.workload, 262144)
+        a.n = {"sp2": 131072, "sizing": 1048576, "model": 32000, "schedule": 131072}.get(a.workload, 262144)
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "sp2":
@@ -638,6 +677,8 @@ def main():
         run_sizing(a)
     elif a.workload == "model":
         run_model(a)
+    elif a.workload == "schedule":
+        run_schedule(a)
     else:
         run_ours(a)
 

@@ -343,7 +343,7 @@ int sp2_tune_load(const char *path);
 typedef struct sp2_options {
   int32_t precision;    /* SP2_PREC_F64 or SP2_PREC_MIXED */
   int32_t max_iter;     /* cap on updates (default 100) */
-  int32_t stall_rule;   /* 1: stop once |trX - trX2| < 0.1 has been seen and err_n >= err_{n-2} */
+  int32_t stall_rule;   /* 1: stop once |trX - trX2| < stall_arm has been seen and err_n >= err_{n-2} */
   int32_t n_fp64_tail;  /* MIXED: minimum FP64 iterations after the switch (default 2) */
   int32_t max_width;    /* cap on the working width (0 = n); SP2E_OVERFLOW beyond it */
   int32_t spgemm_path;  /* SpGEMM first pass: 0 automatic (column blocks; F64: 4 warps
@@ -363,6 +363,7 @@ typedef struct sp2_options {
                            multiply, 2 1.1 x the predictor's longest row + 16 (after an
                            overflow the multiply is repeated at the exact width it counted) */
   const nnzpred_t *predictor;  /* for sizing 2 */
+  double stall_arm;     /* the stall rule arms once |trX - trX2| < stall_arm (default 0.1) */
 } sp2_options;
 
 typedef struct sp2_stats {

@@ -335,10 +335,10 @@ static orc_ell add_fit(const orc_ell *A, const orc_ell *B, double alpha, double 
 
 /*
  * SP2 purification of H.  On return *D holds the density matrix (library-allocated
- * arrays, release with orc_free_ell).  Stall rule (if stall != 0): armed once
- * |trX - trX2| < 0.1; fires when err_n >= err_{n-2}.
+ * arrays, release with orc_free_ell).  Stall rule (if stall_arm > 0): armed once
+ * |trX - trX2| < stall_arm (0.1 in the method's reading); fires when err_n >= err_{n-2}.
  */
-int orc_sp2(const orc_ell *H, double nocc, double tol, double tau, int max_iter, int stall,
+int orc_sp2(const orc_ell *H, double nocc, double tol, double tau, int max_iter, double stall_arm,
             orc_ell *D, orc_sp2_stats *st) {
   if (!H || !D || !st || max_iter < 0 || tau < 0.0) return -1;
   int n = H->n;
@@ -360,8 +360,8 @@ int orc_sp2(const orc_ell *H, double nocc, double tol, double tau, int max_iter,
       row_stats(&X, &st->nnz_total[it], &st->max_row_nnz[it]);
     }
     if (err < tol) { st->status = 0; ell_free(&P); break; }
-    if (stall) {
-      if (fabs(trX - trX2) < 0.1) armed = 1;
+    if (stall_arm > 0.0) {
+      if (fabs(trX - trX2) < stall_arm) armed = 1;
       if (armed && it >= 2 && err >= st->err[it - 2]) { st->status = 1; ell_free(&P); break; }
     }
     if (it >= max_iter) { st->status = 2; ell_free(&P); break; }

@@ -52,6 +52,7 @@ struct Control {
   int active_count; // matrices still running after the last control kernel
   int halves;       // half-iterations run so far
   int max_halves;   // hard bound on the loop, whatever the per-matrix state says
+  double stall_arm; // the stall rule arms once |trX - trX2| < stall_arm
 };
 
 struct Stats {
@@ -263,7 +264,7 @@ __global__ void control_kernel(int count, int half, MatState *__restrict__ st, c
         s.final_buf = half == 0 ? 1 : 0;  // the buffer this half wrote
         s.final_dt = s.phase == 0 ? SP2_F32 : SP2_F64;
       }
-      if (fabs(rr.tr - rr.fro) < 0.1) s.armed = 1;
+      if (fabs(rr.tr - rr.fro) < ctl->stall_arm) s.armed = 1;
       const bool stalled = s.armed && it >= 2 && it - 2 < kCap && err >= stats.err[(size_t)m * kCap + it - 2];
       bool done = false;
       if (!isfinite(rr.tr) || !isfinite(rr.fro)) {
@@ -387,6 +388,8 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
   if (!(opt.spgemm_path == SP2_PATH_TUNED || (opt.spgemm_path >= 0 && opt.spgemm_path <= 6) ||
         (opt.spgemm_path >= 10 && opt.spgemm_path <= 12)))
     return fail(SP2E_ARG, "sp2_purify_batched: spgemm_path must be -1, 0..6 or 10..12");
+  if (!(opt.stall_arm > 0.0) || !isfinite(opt.stall_arm))
+    return fail(SP2E_ARG, "sp2_purify_batched: stall_arm must be > 0");
   long long ntot_ll = 0;
   int wh = 1, nmax = 0;
   std::vector<int> off(count + 1, 0);
@@ -490,7 +493,7 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
     SP2_CUDA(cudaMemsetAsync(d_act64, 0, sizeof(int) * count, s));
     SP2_CUDA(cudaMemsetAsync(sd.branch, 0, sizeof(int) * (size_t)count * kCap, s));
     Control ch{opt.max_iter, opt.stall_rule, mixed ? opt.n_fp64_tail : 0, mixed ? 1 : 0, tol, switch_tol, 0, 0, 0,
-               2 * (opt.max_iter + opt.n_fp64_tail + 8)};
+               2 * (opt.max_iter + opt.n_fp64_tail + 8), opt.stall_arm};
     SP2_CUDA(cudaMemcpyAsync(d_ctl, &ch, sizeof(ch), cudaMemcpyHostToDevice, s));
     SP2_CUDA(cudaMemsetAsync(d_c32, 0, sizeof(SpgemmCtl), s));
     SP2_CUDA(cudaMemsetAsync(d_c64, 0, sizeof(SpgemmCtl), s));

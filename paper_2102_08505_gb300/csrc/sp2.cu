@@ -74,6 +74,7 @@ extern "C" void sp2_options_default(sp2_options *o) {
   o->graph = 1;
   o->sizing = 0;
   o->predictor = nullptr;
+  o->stall_arm = 0.1;
 }
 
 extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2_options *opt_in, ellpack_t *D,
@@ -101,6 +102,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   const int max_w = (opt.max_width > 0 && opt.max_width < n) ? opt.max_width : n;
   if (!(opt.switch_tol >= 0.0) || !isfinite(opt.switch_tol)) return fail(SP2E_ARG, "sp2_purify: bad switch_tol");
   if (opt.sizing < 0 || opt.sizing > 2) return fail(SP2E_ARG, "sp2_purify: sizing must be 0, 1 or 2");
+  if (!(opt.stall_arm > 0.0) || !isfinite(opt.stall_arm)) return fail(SP2E_ARG, "sp2_purify: stall_arm must be > 0");
   if (opt.sizing == 2 && (!opt.predictor || !opt.predictor->params))
     return fail(SP2E_ARG, "sp2_purify: sizing 2 needs a created predictor");
   const double switch_tol = opt.switch_tol > 0.0 ? opt.switch_tol : (tol > 1e-6 ? tol : 1e-6);
@@ -214,7 +216,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
     // a7: stop rules
     bool stop = false;
     const bool stalled = [&] {
-      if (fabs(trX - trX2) < 0.1) armed = true;
+      if (fabs(trX - trX2) < opt.stall_arm) armed = true;
       return armed && it >= 2 && err >= st.err[it - 2];
     }();
     if (phase == MAIN) {

@@ -48,7 +48,7 @@ class sp2_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("stall_rule", ctypes.c_int32),
                 ("n_fp64_tail", ctypes.c_int32), ("max_width", ctypes.c_int32), ("spgemm_path", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("switch_tol", ctypes.c_double), ("graph", ctypes.c_int32),
-                ("sizing", ctypes.c_int32), ("predictor", ctypes.POINTER(nnzpred_t))]
+                ("sizing", ctypes.c_int32), ("predictor", ctypes.POINTER(nnzpred_t)), ("stall_arm", ctypes.c_double)]
 
 
 class sp2_stats(ctypes.Structure):

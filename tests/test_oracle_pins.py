@@ -312,3 +312,21 @@ def test_planted_mistake_is_caught(name, tmp_path):
     path = obuild.build_variant(MUTANTS[name], str(tmp_path / ("mut_%s.so" % name)))
     with O.use_variant(path):
         assert not _pins_pass(), "planted mistake %r was not caught by the pins" % name
+
+
+def test_stall_arm_threshold_variants():
+    """The stall rule's arming threshold: never armed (tiny threshold) is the same run as no
+    stall rule; armed from the start (huge threshold) stops a gapless system no later than
+    the reading's 0.1, and the stop is by the stall rule."""
+    H = ell(I.banded(256, band=8, seed=1, delta=0.0))
+    D0, s0 = O.sp2(H, 128, 1e-14, 1e-5, max_iter=60, stall=False)
+    Dn, sn = O.sp2(H, 128, 1e-14, 1e-5, max_iter=60, stall_arm=1e-300)
+    assert sn["iterations"] == s0["iterations"] and sn["status"] == s0["status"] == "max_iter"
+    assert np.array_equal(Dn.to_dense(), D0.to_dense())
+    Dd, sd = O.sp2(H, 128, 1e-14, 1e-5, max_iter=60)
+    Da, sa = O.sp2(H, 128, 1e-14, 1e-5, max_iter=60, stall_arm=1e300)
+    assert sa["status"] == "stalled" and sa["iterations"] <= sd["iterations"]
+    # armed from the start, the rule fires at the first n >= 2 with err_n >= err_{n-2}
+    e = sa["err"]
+    first = next(k for k in range(2, len(e)) if e[k] >= e[k - 2])
+    assert sa["iterations"] == first

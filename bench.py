@@ -214,7 +214,7 @@ def run_reference(a):
     per_step_ms = 1000.0 * float(np.mean(times)) * a.n / rows
     rate = 1000.0 / per_step_ms
     line = {
-        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 0, "steps": a.steps,
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": per_step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(a),

@@ -355,7 +355,7 @@ typedef struct sp2_options {
                            autotuner's choice */
   double tau;           /* drop tolerance (default 1e-5) */
   double switch_tol;    /* MIXED: leave the FP32 loop once err_n < switch_tol (0 = automatic:
-                           max(tol, 1e-6)); the FP32 stall rule also ends it */
+                           max(tol, 1e-4)); the FP32 stall rule also ends it */
   int32_t graph;        /* sp2_purify_batched: 1 = the loop runs as one CUDA graph with a
                            conditional WHILE node (default); 0 = host-stepped */
   int32_t sizing;       /* sp2_purify output widths: 0 heuristic (4x the longest row of X,
@@ -364,6 +364,10 @@ typedef struct sp2_options {
                            overflow the multiply is repeated at the exact width it counted) */
   const nnzpred_t *predictor;  /* for sizing 2 */
   double stall_arm;     /* the stall rule arms once |trX - trX2| < stall_arm (default 0.1) */
+  int32_t symmetric;    /* 1 (default): H must be exactly symmetric (checked: SP2E_ARG
+                           otherwise); every product computes its upper triangle and mirrors
+                           it (the same result bit for bit, about half the products).
+                           0: full rows, no check */
 } sp2_options;
 
 typedef struct sp2_stats {
@@ -413,6 +417,9 @@ typedef struct sp2_step_info {
   int32_t rows_dense;      /* out: rows handed further to the dense global-row pass */
   int32_t spgemm_path_used; /* out: the first-pass variant that ran (the tuner's choice
                                for SP2_PATH_TUNED) */
+  int32_t symmetric;       /* in: 1 = X is exactly symmetric (not checked): the product's
+                              upper triangle is computed and mirrored */
+  int32_t pad;
 } sp2_step_info;
 
 /*

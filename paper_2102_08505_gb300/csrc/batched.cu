@@ -412,7 +412,7 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
   const bool f32only = opt.precision == SP2_PREC_F32;
   const bool use32 = mixed || f32only;
   const bool use64 = !f32only;
-  const double switch_tol = opt.switch_tol > 0.0 ? opt.switch_tol : (tol > 1e-6 ? tol : 1e-6);
+  const double switch_tol = opt.switch_tol > 0.0 ? opt.switch_tol : (tol > 1e-4 ? tol : 1e-4);
 
   cudaStream_t user = as_stream(stream);
   cudaStream_t s = user;
@@ -479,6 +479,10 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
     SP2_TRY(db.get(&d_c32, sizeof(SpgemmCtl)));
     SP2_TRY(db.get(&d_c64, sizeof(SpgemmCtl)));
     SP2_TRY(db.get(&d_rowstat, sizeof(double2) * (size_t)ntot));
+    // scratch of the symmetric products, allocated here: nothing allocates inside the loop
+    unsigned char *d_sym = nullptr;
+    const size_t sym_bytes = opt.symmetric ? sym_scratch_bytes(ntot, width, width, SP2_F64) : 0;
+    if (opt.symmetric) SP2_TRY(db.get(&d_sym, sym_bytes));
     SP2_TRY(db.get(&sd.trX, sizeof(double) * (size_t)count * kCap));
     SP2_TRY(db.get(&sd.trX2, sizeof(double) * (size_t)count * kCap));
     SP2_TRY(db.get(&sd.err, sizeof(double) * (size_t)count * kCap));
@@ -529,6 +533,13 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
     x0_batched_kernel<<<grid_rows(ntot), 256, 0, s>>>(view<double>(&Hs), d_rowmat, d_bounds, opt.tau,
                                                        outview<double>(&X64));
     note_launch();
+    if (opt.symmetric) {  // the upper-triangle products need exactly symmetric matrices
+      long long defects = 0;
+      SP2_TRY(symmetry_defects(&Hs, &defects, s));
+      if (defects)
+        return fail(SP2E_ARG, "sp2_purify_batched: some H is not exactly symmetric (%lld entries without a mirror); "
+                              "use symmetric = 0", defects);
+    }
     if (use32) SP2_TRY(convert_async(&X64, &X32, s));
     // a3 for X0, then the first branch decisions
     SP2_TRY(rowstat_async(use32 ? &X32 : &X64, d_rowstat, s));
@@ -555,6 +566,9 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
       auto pick = [&](ellpack_t *cur, ellpack_t *nxt, SpgemmCtl *c, int *path) -> int {
         if (tune_find(cur->dtype, ntot, mean, path)) return SP2_OK;
         MultiplyArgs a{cur, cur, nullptr, nxt, 1.0, 0.0, opt.tau, 0};
+        a.sym = opt.symmetric != 0;
+        a.sym_prealloc = d_sym;
+        a.sym_prealloc_bytes = sym_bytes;
         SP2_TRY(tune_multiply(a, mean, d_rowstat, c, 2, path, nullptr, s));
         ++tuned_classes;
         return SP2_OK;
@@ -575,12 +589,18 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
         MultiplyArgs a{cur32, cur32, cur32, nxt32, 1.0, 0.0, opt.tau, path32};
         a.bv = bv32;
         a.fb_prealloc = d_fb;
+        a.sym = opt.symmetric != 0;
+        a.sym_prealloc = d_sym;
+        a.sym_prealloc_bytes = sym_bytes;
         SP2_TRY(multiply_async(a, d_rowstat, d_c32, s));
       }
       if (use64) {
         MultiplyArgs a{cur64, cur64, cur64, nxt64, 1.0, 0.0, opt.tau, path64};
         a.bv = bv64;
         a.fb_prealloc = d_fb;
+        a.sym = opt.symmetric != 0;
+        a.sym_prealloc = d_sym;
+        a.sym_prealloc_bytes = sym_bytes;
         SP2_TRY(multiply_async(a, d_rowstat, d_c64, s));
       }
       seg_reduce_kernel<<<count, 256, 0, s>>>(d_rowstat, use32 ? nxt32->nnz : nullptr, use64 ? nxt64->nnz : nullptr,

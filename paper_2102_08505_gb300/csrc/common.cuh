@@ -123,6 +123,15 @@ struct BatchView {
   const int *active = nullptr;    // per matrix
 };
 
+// Upper-triangle mode of a symmetric product (X*X, X symmetric): row i accumulates only
+// the columns j >= i.  tp[i*A.w + t] is the first position of row k = A.idx[i, t] of B
+// with a column >= i (that source row is read from there on); tpd[i] is the same
+// position in the addend row i.  Null pointers: full rows.
+struct Upper {
+  const int *tp = nullptr;
+  const int *tpd = nullptr;
+};
+
 struct MultiplyArgs {
   const ellpack_t *A, *B, *Add;
   ellpack_t *Out;
@@ -130,7 +139,27 @@ struct MultiplyArgs {
   int path;  // first pass: 0 automatic, 1..4 column blocks, 10..12 hash table
   BatchView bv{};              // per-row coefficients for batched multiplies
   int *fb_prealloc = nullptr;  // 2*n ints for the deferred-row lists (null: allocated per call)
+  // X*X (+ X) with X symmetric (A == B, Add null or A): compute the upper triangle and
+  // mirror it (bitwise the same result as full rows, about half the products)
+  bool sym = false;
+  void *sym_prealloc = nullptr;  // scratch of the symmetric product (null: allocated per call)
+  size_t sym_prealloc_bytes = 0;
+  Upper up{};  // set internally for the upper-triangle pass
 };
+// Scratch of a symmetric product with n rows, input width aw and output width ow.
+inline size_t sym_scratch_bytes(int n, int aw, int ow, int dtype) {
+  auto a256 = [](size_t b) { return ((b + 255) / 256) * 256; };
+  const size_t es = dtype == SP2_F64 ? 8 : 4;
+  return a256(es * (size_t)n * ow) + a256(4 * (size_t)n * ow) + a256(4 * (size_t)n) + a256(4 * (size_t)n * aw) +
+         a256(4 * (size_t)n) + a256(4 * (3 * (size_t)n + 1));
+}
+// Symmetric product passes (symm.cu): first positions of the upper triangle; mirroring
+// the upper rows U into full rows of Out (work: 3n+1 ints), rowstat of the full rows.
+int upper_start_async(const ellpack_t *X, int *tp, int *tpd, cudaStream_t s);
+// Entries of X without a bitwise-equal mirror entry (0: X is exactly symmetric); synchronises.
+int symmetry_defects(const ellpack_t *X, long long *defects, cudaStream_t s);
+int mirror_async(const ellpack_t *U, ellpack_t *Out, const BatchView &bv, int *work, double2 *rowstat, SpgemmCtl *ctl,
+                 cudaStream_t s);
 int multiply_async(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStream_t s);
 
 // A <- drop_tau(alpha*A + beta*B), rowstat/ctl as above.

@@ -75,6 +75,7 @@ extern "C" void sp2_options_default(sp2_options *o) {
   o->sizing = 0;
   o->predictor = nullptr;
   o->stall_arm = 0.1;
+  o->symmetric = 1;
 }
 
 extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2_options *opt_in, ellpack_t *D,
@@ -105,7 +106,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   if (!(opt.stall_arm > 0.0) || !isfinite(opt.stall_arm)) return fail(SP2E_ARG, "sp2_purify: stall_arm must be > 0");
   if (opt.sizing == 2 && (!opt.predictor || !opt.predictor->params))
     return fail(SP2E_ARG, "sp2_purify: sizing 2 needs a created predictor");
-  const double switch_tol = opt.switch_tol > 0.0 ? opt.switch_tol : (tol > 1e-6 ? tol : 1e-6);
+  const double switch_tol = opt.switch_tol > 0.0 ? opt.switch_tol : (tol > 1e-4 ? tol : 1e-4);
 
   Buffers b;
   b.s = as_stream(stream);
@@ -164,6 +165,13 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   st.emax = hb[1];
   if (!isfinite(hb[0]) || !isfinite(hb[1])) return fail(SP2E_NONFINITE, "sp2_purify: H holds a NaN or Inf");
   if (!(hb[1] > hb[0])) return fail(SP2E_ARG, "sp2_purify: degenerate spectral bounds (e_max <= e_min)");
+
+  if (opt.symmetric) {  // the upper-triangle products need an exactly symmetric H
+    long long defects = 0;
+    SP2_TRY(symmetry_defects(H64, &defects, s));
+    if (defects) return fail(SP2E_ARG, "sp2_purify: H is not exactly symmetric (%lld entries without a mirror); "
+                                       "use symmetric = 0", defects);
+  }
 
   // a2: X0 in FP64
   SP2_TRY(ellpack_create(n, H64->width + 1, SP2_F64, s, &b.X));
@@ -292,6 +300,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
     for (;;) {
       SP2_TRY(ensure(&b.Y, n, width, b.X.dtype, s));
       MultiplyArgs a{&b.X, &b.X, beta != 0.0 ? &b.X : nullptr, &b.Y, alpha, beta, opt.tau, lg};
+      a.sym = opt.symmetric != 0;
       SP2_TRY(multiply_async(a, b.rowstat, b.ctl, s));
       launch_reduce_rows(b.rowstat, b.Y.nnz, n, b.ctl, b.dres, s);
       SP2_CUDA(cudaGetLastError());
@@ -310,6 +319,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
     }
     if (tune_pending) {  // time every variant on this product, then redo it with the fastest
       MultiplyArgs a{&b.X, &b.X, beta != 0.0 ? &b.X : nullptr, &b.Y, alpha, beta, opt.tau, 0};
+      a.sym = opt.symmetric != 0;
       SP2_TRY(tune_multiply(a, mean_nnz, b.rowstat, b.ctl, 2, &lg, nullptr, s));
       a.path = lg;
       SP2_TRY(multiply_async(a, b.rowstat, b.ctl, s));
@@ -419,6 +429,7 @@ extern "C" int sp2_step(const ellpack_t *X, ellpack_t *Xn, double nocc, double t
   const bool up = fabs(2.0 * trX - trX2 - nocc) < fabs(trX2 - nocc);
   info->branch = up ? 2 : 1;
   MultiplyArgs a{X, X, up ? X : nullptr, Xn, up ? -1.0 : 1.0, up ? 2.0 : 0.0, tau, info->spgemm_path};
+  a.sym = info->symmetric != 0;
   if (a.path == SP2_PATH_TUNED) {
     double mean = 0.0;
     SP2_TRY(mean_row_nnz(X, &mean, s));

@@ -92,9 +92,10 @@ __device__ __forceinline__ int find_or_insert(int *keys, T *vals, int j, int &in
 }
 
 template <typename T, int QM>
-__device__ __forceinline__ void load_brow(const EllView<T> &B, int k, int nb, int lane, int (&jr)[QM], T (&vr)[QM]) {
-  const int *bi = B.idx + (size_t)k * B.w;
-  const T *bv = B.val + (size_t)k * B.w;
+__device__ __forceinline__ void load_brow(const EllView<T> &B, int k, int st, int nb, int lane, int (&jr)[QM],
+                                          T (&vr)[QM]) {
+  const int *bi = B.idx + (size_t)k * B.w + st;
+  const T *bv = B.val + (size_t)k * B.w + st;
 #pragma unroll
   for (int u = 0; u < QM; ++u) {
     const int q = lane + 32 * u;
@@ -194,7 +195,7 @@ struct HashCfg {
 template <typename T, int LOG2T, int QM>
 __global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32, 1)
     spgemm_hash_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
-                       int use_add, BatchView bv, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
+                       int use_add, BatchView bv, Upper up, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
                        const int *__restrict__ row_list, const int *__restrict__ row_count,
                        int *__restrict__ fb_list, int *__restrict__ fb_count) {
   using Cfg = HashCfg<T, LOG2T>;
@@ -226,7 +227,8 @@ __global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32, 1)
     int bad = 0;
     if (add_r) {
       const int nc = min(Add.nnz[r], Add.w);
-      for (int s = lane; s < nc; s += 32) {
+      const int d0 = up.tpd ? min(max(up.tpd[r], 0), nc) : 0;  // upper-triangle mode: from column r on
+      for (int s = d0 + lane; s < nc; s += 32) {
         const int j = Add.idx[(size_t)r * Add.w + s];
         if ((unsigned)j >= (unsigned)ncol) continue;  // invalid column: ignored, never dereferenced
         const T c = Add.val[(size_t)r * Add.w + s];
@@ -242,13 +244,15 @@ __global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32, 1)
     const T *avp = A.val + (size_t)r * A.w;
     for (int base = 0; base < na && !aborted; base += 32) {
       const int s = base + lane;
-      int kk = 0, nbk = 0;
+      int kk = 0, nbk = 0, sk = 0;
       T av = T(0);
       if (s < na) {
         kk = __ldg(ai + s);
         if ((unsigned)kk < (unsigned)B.n) {
           av = alpha_r * __ldg(avp + s);
           nbk = min(__ldg(B.nnz + kk), B.w);
+          if (up.tp) sk = min(max(__ldg(up.tp + (size_t)r * A.w + s), 0), nbk);
+          nbk -= sk;
         } else {
           kk = 0;  // invalid column of A: contributes nothing
         }
@@ -256,18 +260,21 @@ __global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32, 1)
       const int cnt = min(32, na - base);
       int jr[QM];
       T vr[QM];
-      load_brow<T, QM>(B, __shfl_sync(kFull, kk, 0), __shfl_sync(kFull, nbk, 0), lane, jr, vr);
+      load_brow<T, QM>(B, __shfl_sync(kFull, kk, 0), __shfl_sync(kFull, sk, 0), __shfl_sync(kFull, nbk, 0), lane,
+                       jr, vr);
       for (int t = 0; t < cnt; ++t) {
         const T a = __shfl_sync(kFull, av, t);
         const int k = __shfl_sync(kFull, kk, t);
+        const int st = __shfl_sync(kFull, sk, t);
         const int nb = __shfl_sync(kFull, nbk, t);
         const int nu = (nb + 31) >> 5;  // warp-uniform: register slots in use this step
         const int tn = t + 1 < cnt ? t + 1 : t;
         const int k1 = __shfl_sync(kFull, kk, tn);
+        const int st1 = __shfl_sync(kFull, sk, tn);
         const int nb1 = (t + 1 < cnt) ? __shfl_sync(kFull, nbk, tn) : 0;
         int jn[QM];
         T vn[QM];
-        load_brow<T, QM>(B, k1, nb1, lane, jn, vn);
+        load_brow<T, QM>(B, k1, st1, nb1, lane, jn, vn);
         // The QM columns a lane holds in this step are distinct, so their slots are too.
         // Phase 1 probes every home slot; phase 2 accumulates the hits (loads first,
         // then FMAs and stores: QM independent chains); phase 3 resolves the misses
@@ -304,9 +311,9 @@ __global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32, 1)
           if (h >= 0) vals[h] = fmadd(a, vv, vals[h]); else bad = 1;
         }
         for (int q = lane + 32 * QM; q < nb; q += 32) {  // rows longer than 32*QM
-          const int j = __ldg(B.idx + (size_t)k * B.w + q);
+          const int j = __ldg(B.idx + (size_t)k * B.w + st + q);
           if ((unsigned)j >= (unsigned)ncol) continue;
-          const T v = __ldg(B.val + (size_t)k * B.w + q);
+          const T v = __ldg(B.val + (size_t)k * B.w + st + q);
           const int h = find_or_insert<LOG2T>(keys, vals, j, ins);
           if (h >= 0) vals[h] = fmadd(a, v, vals[h]); else bad = 1;
         }
@@ -482,7 +489,7 @@ __device__ __forceinline__ bool group_sync_or(int grp, bool pred) {
 template <typename T, int R, int QW, bool KEEPZ>
 __global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
     spgemm_block_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
-                        int use_add, BatchView bv, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
+                        int use_add, BatchView bv, Upper up, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
                         int *__restrict__ fb_list, int *__restrict__ fb_count) {
   using Geo = BlockGeo<T, R>;
   constexpr int GW = Geo::GW, GSH = Geo::GSH, G = Geo::G;
@@ -530,32 +537,38 @@ __global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
     const int na = min(A.nnz[r], A.w);
     const int *arow_i = A.idx + (size_t)r * A.w;
     const T *arow_v = A.val + (size_t)r * A.w;
-    int ck, cnb, nk_, nnb;
+    // per entry of A: source row k, its first position read (upper-triangle mode: the
+    // first column >= r, else 0) and the count of entries read from there
+    int ck, cnb, nk_, nnb, cst, nst;
     T ca, na_;
-    auto load_chunk = [&](int cb, int &kk, int &nbk, T &av) {
+    auto load_chunk = [&](int cb, int &kk, int &nbk, T &av, int &st) {
       const int s = cb + lane;
-      kk = 0; nbk = 0; av = T(0);
+      kk = 0; nbk = 0; av = T(0); st = 0;
       if (s < na) {
         const int k = __ldg(arow_i + s);
         if ((unsigned)k < (unsigned)B.n) {
           kk = k;
           av = alpha_r * __ldg(arow_v + s);
           nbk = min(__ldg(B.nnz + k), B.w);
+          if (up.tp) st = min(max(__ldg(up.tp + (size_t)r * A.w + s), 0), nbk);
+          nbk -= st;
         }
       }
     };
-    load_chunk(0, ck, cnb, ca);
-    load_chunk(32, nk_, nnb, na_);
+    load_chunk(0, ck, cnb, ca, cst);
+    load_chunk(32, nk_, nnb, na_, nst);
     int cbase = 0;
-    auto info = [&](int t, int &k, int &nb, T &a) {  // t in [cbase, cbase + 64)
+    auto info = [&](int t, int &k, int &nb, T &a, int &st) {  // t in [cbase, cbase + 64)
       if (t < cbase + 32) {
         k = __shfl_sync(kFull, ck, t & 31);
         nb = __shfl_sync(kFull, cnb, t & 31);
         a = __shfl_sync(kFull, ca, t & 31);
+        st = __shfl_sync(kFull, cst, t & 31);
       } else {
         k = __shfl_sync(kFull, nk_, t & 31);
         nb = __shfl_sync(kFull, nnb, t & 31);
         a = __shfl_sync(kFull, na_, t & 31);
+        st = __shfl_sync(kFull, nst, t & 31);
       }
     };
     auto fetch = [&](const int *ri, const T *rv, int nb, int (&jr)[QW], T (&vr)[QW]) {
@@ -566,9 +579,11 @@ __global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
         vr[u] = q < nb ? __ldg(rv + q) : T(0);
       }
     };
-    auto fetch_step = [&](int t, int (&jr)[QW], T (&vr)[QW], int &nb, T &a, int &k) {
-      info(t, k, nb, a);
-      fetch(B.idx + (size_t)k * B.w, B.val + (size_t)k * B.w, nb, jr, vr);
+    auto fetch_step = [&](int t, int (&jr)[QW], T (&vr)[QW], int &nb, T &a, size_t &off) {
+      int k, st;
+      info(t, k, nb, a, st);
+      off = (size_t)k * B.w + st;
+      fetch(B.idx + off, B.val + off, nb, jr, vr);
     };
     // accumulate one step from registers, body instantiated per number NU of occupied
     // register slots of this warp (warp-uniform switch: empty slots cost nothing)
@@ -647,12 +662,15 @@ __global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
 
     int j0[QW], j1[QW], j2[QW];
     T v0[QW], v1[QW], v2[QW];
-    int nb0 = 0, nb1 = 0, nb2 = 0, k0 = 0, k1 = 0, k2 = 0;
+    int nb0 = 0, nb1 = 0, nb2 = 0;
+    size_t k0 = 0, k1 = 0, k2 = 0;  // offsets of the source rows in B's arrays
     T a0 = T(0), a1 = T(0), a2 = T(0);
     if (add_r) {
-      const int nc = min(Add.nnz[r], Add.w);
-      const int *ci = Add.idx + (size_t)r * Add.w;
-      const T *cv = Add.val + (size_t)r * Add.w;
+      int nc = min(Add.nnz[r], Add.w);
+      const int d0 = up.tpd ? min(max(up.tpd[r], 0), nc) : 0;
+      const int *ci = Add.idx + (size_t)r * Add.w + d0;
+      const T *cv = Add.val + (size_t)r * Add.w + d0;
+      nc -= d0;
       fetch(ci, cv, nc, j2, v2);
       if (na > 0) fetch_step(0, j0, v0, nb0, a0, k0);
       if (na > 1) fetch_step(1, j1, v1, nb1, a1, k1);
@@ -663,18 +681,18 @@ __global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
     }
     for (int t = 0; t < na && !aborted; t += 3) {
       if (t >= cbase + 32) {  // next chunk of A's entries becomes current
-        ck = nk_; cnb = nnb; ca = na_;
+        ck = nk_; cnb = nnb; ca = na_; cst = nst;
         cbase += 32;
-        load_chunk(cbase + 32, nk_, nnb, na_);
+        load_chunk(cbase + 32, nk_, nnb, na_, nst);
       }
       if (t + 2 < na) fetch_step(t + 2, j2, v2, nb2, a2, k2);
-      step(j0, v0, nb0, a0, B.idx + (size_t)k0 * B.w, B.val + (size_t)k0 * B.w);
+      step(j0, v0, nb0, a0, B.idx + k0, B.val + k0);
       if (t + 1 >= na || aborted) break;
       if (t + 3 < na) fetch_step(t + 3, j0, v0, nb0, a0, k0);
-      step(j1, v1, nb1, a1, B.idx + (size_t)k1 * B.w, B.val + (size_t)k1 * B.w);
+      step(j1, v1, nb1, a1, B.idx + k1, B.val + k1);
       if (t + 2 >= na || aborted) break;
       if (t + 4 < na) fetch_step(t + 4, j1, v1, nb1, a1, k1);
-      step(j2, v2, nb2, a2, B.idx + (size_t)k2 * B.w, B.val + (size_t)k2 * B.w);
+      step(j2, v2, nb2, a2, B.idx + k2, B.val + k2);
     }
     if (aborted) {
       if (gt == 0) {
@@ -769,7 +787,7 @@ __global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
 template <typename T, int QM, int S, bool KEEPZ>
 __global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
     spgemm_super_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
-                        int use_add, BatchView bv, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
+                        int use_add, BatchView bv, Upper up, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
                         int *__restrict__ fb_list, int *__restrict__ fb_count) {
   using Geo = BlockGeo<T, 1>;
   constexpr int GW = Geo::GW, GSH = Geo::GSH, G = Geo::G;
@@ -802,42 +820,48 @@ __global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
     __syncwarp();
     bool aborted = false;
     const int na = min(A.nnz[r], A.w);
-    const int nc = add_r ? min(Add.nnz[r], Add.w) : 0;
+    const int nc0 = add_r ? min(Add.nnz[r], Add.w) : 0;
+    const int d0 = (add_r && up.tpd) ? min(max(up.tpd[r], 0), nc0) : 0;  // upper-triangle mode: from column r on
+    const int nc = nc0 - d0;
     const int nsteps = na + (add_r ? 1 : 0);  // step 0 is the addend row, if any
     const int *arow_i = A.idx + (size_t)r * A.w;
     const T *arow_v = A.val + (size_t)r * A.w;
     // A's entries for 32 steps at a time (k, nnz(B_k), alpha*a_ik), next chunk preloaded
-    int ck, cnb, nk_, nnb;
+    int ck, cnb, nk_, nnb, cst, nst;
     T ca, na_;
-    auto load_chunk = [&](int cb, int &kk, int &nbk, T &av) {
+    auto load_chunk = [&](int cb, int &kk, int &nbk, T &av, int &st) {
       const int s0 = cb + lane;
-      kk = 0; nbk = 0; av = T(0);
+      kk = 0; nbk = 0; av = T(0); st = 0;
       if (s0 < na) {
         const int k = __ldg(arow_i + s0);
         if ((unsigned)k < (unsigned)B.n) {
           kk = k;
           av = alpha_r * __ldg(arow_v + s0);
           nbk = min(__ldg(B.nnz + k), B.w);
+          if (up.tp) st = min(max(__ldg(up.tp + (size_t)r * A.w + s0), 0), nbk);
+          nbk -= st;
         }
       }
     };
-    load_chunk(0, ck, cnb, ca);
-    load_chunk(32, nk_, nnb, na_);
+    load_chunk(0, ck, cnb, ca, cst);
+    load_chunk(32, nk_, nnb, na_, nst);
     int cbase = 0;
     // source row of step t (t in [cbase, cbase+64) for the A part)
     auto src = [&](int t, const int *&ri, const T *&rv, int &nb, T &a) {
       if (add_r && t == 0) {
-        ri = Add.idx + (size_t)r * Add.w; rv = Add.val + (size_t)r * Add.w; nb = nc; a = beta_r;
+        ri = Add.idx + (size_t)r * Add.w + d0; rv = Add.val + (size_t)r * Add.w + d0; nb = nc; a = beta_r;
         return;
       }
       const int ta = t - (add_r ? 1 : 0);
-      int k;
+      int k, st;
       if (ta < cbase + 32) {
         k = __shfl_sync(kFull, ck, ta & 31); nb = __shfl_sync(kFull, cnb, ta & 31); a = __shfl_sync(kFull, ca, ta & 31);
+        st = __shfl_sync(kFull, cst, ta & 31);
       } else {
         k = __shfl_sync(kFull, nk_, ta & 31); nb = __shfl_sync(kFull, nnb, ta & 31); a = __shfl_sync(kFull, na_, ta & 31);
+        st = __shfl_sync(kFull, nst, ta & 31);
       }
-      ri = B.idx + (size_t)k * B.w; rv = B.val + (size_t)k * B.w;
+      ri = B.idx + (size_t)k * B.w + st; rv = B.val + (size_t)k * B.w + st;
     };
     int jc[S][QM], jn[S][QM];
     T vc[S][QM], vn[S][QM];
@@ -864,9 +888,9 @@ __global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
       // chunk of A entries: steps t0 .. t0+2S-1 must lie in [cbase, cbase+64)
       const int ta_next = t0 + S + S - 1 - (add_r ? 1 : 0);
       if (ta_next >= cbase + 64) {
-        ck = nk_; cnb = nnb; ca = na_;
+        ck = nk_; cnb = nnb; ca = na_; cst = nst;
         cbase += 32;
-        load_chunk(cbase + 32, nk_, nnb, na_);
+        load_chunk(cbase + 32, nk_, nnb, na_, nst);
       }
       load_super(t0 + S, jn, vn, nbn, an, rin, rvn);  // prefetch the next super-step
       // phase A: every held column of the S rows -> accumulator index
@@ -1081,7 +1105,7 @@ struct RunBuf {
 template <typename T, bool KEEPZ>
 __global__ void __launch_bounds__(RunGeo<T>::ROWS * 32, 1)
     spgemm_run_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
-                      int use_add, BatchView bv, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
+                      int use_add, BatchView bv, Upper up, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
                       int *__restrict__ fb_list, int *__restrict__ fb_count) {
   using Geo = RunGeo<T>;
   constexpr int GW = Geo::GW, GSH = Geo::GSH, G = Geo::G;
@@ -1122,7 +1146,7 @@ __global__ void __launch_bounds__(RunGeo<T>::ROWS * 32, 1)
     const int ns = na + (add_r ? 1 : 0);  // sources: [addend row], then the rows of B
     const int *arow_i = A.idx + (size_t)r * A.w;
     const T *arow_v = A.val + (size_t)r * A.w;
-    int pk = 0, pnb = 0, pbase = -32;  // A entries pbase .. pbase+31 (k, nb(B_k), alpha*a), one per lane
+    int pk = 0, pnb = 0, pst = 0, pbase = -32;  // A entries pbase .. pbase+31 (k, count, start, alpha*a)
     T pa = T(0);
 
     // run of this lane in a round of n entries starting at entry off of row (ri, rv)
@@ -1142,30 +1166,35 @@ __global__ void __launch_bounds__(RunGeo<T>::ROWS * 32, 1)
       bf.nb = 0; bf.a = T(0); bf.ri = B.idx; bf.rv = B.val;
       if (s < ns) {
         if (add_r && s == 0) {
-          bf.ri = Add.idx + (size_t)r * Add.w;
-          bf.rv = Add.val + (size_t)r * Add.w;
-          bf.nb = min(Add.nnz[r], Add.w);
+          const int nc = min(Add.nnz[r], Add.w);
+          const int d0 = up.tpd ? min(max(up.tpd[r], 0), nc) : 0;  // upper-triangle mode
+          bf.ri = Add.idx + (size_t)r * Add.w + d0;
+          bf.rv = Add.val + (size_t)r * Add.w + d0;
+          bf.nb = nc - d0;
           bf.a = beta_r;
         } else {
           const int t = s - add_r;
           if (t >= pbase + 32) {
             pbase = t & ~31;
             const int q = pbase + lane;
-            pk = 0; pnb = 0; pa = T(0);
+            pk = 0; pnb = 0; pst = 0; pa = T(0);
             if (q < na) {
               const int k = __ldg(arow_i + q);
               if ((unsigned)k < (unsigned)B.n) {
                 pk = k;
                 pa = alpha_r * __ldg(arow_v + q);
                 pnb = min(__ldg(B.nnz + k), B.w);
+                if (up.tp) pst = min(max(__ldg(up.tp + (size_t)r * A.w + q), 0), pnb);
+                pnb -= pst;
               }
             }
           }
           const int k = __shfl_sync(kFull, pk, t & 31);
+          const int st = __shfl_sync(kFull, pst, t & 31);
           bf.nb = __shfl_sync(kFull, pnb, t & 31);
           bf.a = __shfl_sync(kFull, pa, t & 31);
-          bf.ri = B.idx + (size_t)k * B.w;
-          bf.rv = B.val + (size_t)k * B.w;
+          bf.ri = B.idx + (size_t)k * B.w + st;
+          bf.rv = B.val + (size_t)k * B.w + st;
         }
       }
       load_run(bf.ri, bf.rv, 0, min(bf.nb, ROUND), bf.per, bf.cnt, bf.j, bf.v);
@@ -1376,7 +1405,7 @@ __device__ __forceinline__ int block_exclusive_scan_ballot(bool flag, int *s_war
 template <typename T>
 __global__ void __launch_bounds__(kDenseThreads)
     spgemm_dense_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
-                        int use_add, BatchView bv, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
+                        int use_add, BatchView bv, Upper up, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
                         const int *__restrict__ fb_list, const int *__restrict__ fb_count, T *__restrict__ acc_all,
                         int *__restrict__ mark_all) {
   __shared__ int s_warp[kDenseThreads / 32];
@@ -1399,7 +1428,8 @@ __global__ void __launch_bounds__(kDenseThreads)
     }
     if (add_r) {
       const int nc = min(Add.nnz[r], Add.w);
-      for (int s = threadIdx.x; s < nc; s += blockDim.x) {
+      const int d0 = up.tpd ? min(max(up.tpd[r], 0), nc) : 0;  // upper-triangle mode: from column r on
+      for (int s = d0 + threadIdx.x; s < nc; s += blockDim.x) {
         const int j = Add.idx[(size_t)r * Add.w + s];
         if ((unsigned)j >= (unsigned)n) continue;
         mark[j] = 1;
@@ -1415,7 +1445,8 @@ __global__ void __launch_bounds__(kDenseThreads)
       if ((unsigned)k < (unsigned)B.n) {
         const T a = alpha_r * A.val[(size_t)r * A.w + t];
         const int nb = min(B.nnz[k], B.w);
-        for (int s = threadIdx.x; s < nb; s += blockDim.x) {
+        const int st = up.tp ? min(max(up.tp[(size_t)r * A.w + t], 0), nb) : 0;
+        for (int s = st + threadIdx.x; s < nb; s += blockDim.x) {
           const int j = B.idx[(size_t)k * B.w + s];
           if ((unsigned)j >= (unsigned)n) continue;
           mark[j] = 1;
@@ -1651,7 +1682,7 @@ int launch_hash(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, const i
   const int cls = row_list ? SP2_PROF_LARGE : SP2_PROF_SPGEMM;
   prof_begin(cls, s);
   kern<<<grid, Cfg::WARPS * 32, Cfg::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
-                                               (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv,
+                                               (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv, a.up,
                                                rowstat, ctl, row_list, row_count, fb, fb_count);
   note_launch();
   prof_end(cls, s);
@@ -1682,7 +1713,7 @@ int launch_block(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
   const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
   prof_begin(SP2_PROF_SPGEMM, s);
   kern<<<grid, Geo::WARPS * 32, Geo::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
-                                               (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv,
+                                               (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv, a.up,
                                                rowstat, ctl, fb, fb_count);
   note_launch();
   prof_end(SP2_PROF_SPGEMM, s);
@@ -1713,7 +1744,7 @@ int launch_super(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
   const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
   prof_begin(SP2_PROF_SPGEMM, s);
   kern<<<grid, Geo::WARPS * 32, Geo::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
-                                               (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv,
+                                               (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv, a.up,
                                                rowstat, ctl, fb, fb_count);
   note_launch();
   prof_end(SP2_PROF_SPGEMM, s);
@@ -1744,7 +1775,7 @@ int launch_run(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb,
   const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
   prof_begin(SP2_PROF_SPGEMM, s);
   kern<<<grid, Geo::ROWS * 32, Geo::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
-                                              (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv,
+                                              (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv, a.up,
                                               rowstat, ctl, fb, fb_count);
   note_launch();
   prof_end(SP2_PROF_SPGEMM, s);
@@ -1801,7 +1832,71 @@ int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
 }
 
 template <typename T>
+int multiply_t(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStream_t s);
+
+// Symmetric product: upper rows into a scratch matrix U, then mirrored into a.Out.  U is
+// as wide as the output; if an upper row does not fit (so the output cannot fit either),
+// the first pass is repeated with U as wide as the longest upper row, so that the
+// reported required width stays exact -- except while a stream is being captured (the
+// batched loop regrows on its own), where the report is then a lower bound.
+template <typename T>
+int multiply_sym_t(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStream_t s) {
+  const int n = a.A->n;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  SP2_CUDA(cudaStreamIsCapturing(s, &cap));
+  int uw = a.Out->width;
+  for (int attempt = 0;; ++attempt) {
+    const size_t bytes = sym_scratch_bytes(n, a.A->width, uw, a.A->dtype);
+    unsigned char *scr = static_cast<unsigned char *>(a.sym_prealloc);
+    const bool own = !scr || a.sym_prealloc_bytes < bytes;
+    if (own && cap != cudaStreamCaptureStatusNone) return fail(SP2E_ARG, "multiply: symmetric scratch too small");
+    if (own) SP2_TRY(dev_alloc((void **)&scr, bytes, s));
+    // layout: U.val, U.idx, U.nnz, tp, tpd, work (each 256-byte aligned)
+    size_t off = 0;
+    auto take = [&](size_t b) { unsigned char *q = scr + off; off += round_up_sz(b, 256); return q; };
+    ellpack_t U{};
+    U.n = n;
+    U.width = uw;
+    U.dtype = a.A->dtype;
+    U.owner = 0;
+    U.val = take(sizeof(T) * (size_t)n * uw);
+    U.idx = reinterpret_cast<int *>(take(sizeof(int) * (size_t)n * uw));
+    U.nnz = reinterpret_cast<int *>(take(sizeof(int) * (size_t)n));
+    int *tp = reinterpret_cast<int *>(take(sizeof(int) * (size_t)n * a.A->width));
+    int *tpd = reinterpret_cast<int *>(take(sizeof(int) * (size_t)n));
+    int *work = reinterpret_cast<int *>(take(sizeof(int) * (3 * (size_t)n + 1)));
+    int rc = SP2_OK;
+    cudaError_t e = cudaMemsetAsync(U.nnz, 0, sizeof(int) * (size_t)n, s);
+    if (e == cudaSuccess && attempt > 0) e = cudaMemsetAsync(ctl, 0, sizeof(SpgemmCtl), s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "multiply (symmetric)", __FILE__, __LINE__);
+    if (rc == SP2_OK) rc = upper_start_async(a.A, tp, tpd, s);
+    if (rc == SP2_OK) {
+      MultiplyArgs a1 = a;
+      a1.sym = false;
+      a1.Out = &U;
+      a1.up = Upper{tp, tpd};
+      rc = multiply_t<T>(a1, rowstat, ctl, s);
+    }
+    SpgemmCtl h{};
+    if (rc == SP2_OK && cap == cudaStreamCaptureStatusNone && attempt == 0) {
+      e = cudaMemcpyAsync(&h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) rc = cuda_fail(e, "multiply (symmetric)", __FILE__, __LINE__);
+    }
+    if (rc == SP2_OK && h.overflow_rows > 0 && h.max_count > uw) {  // an upper row did not fit: widen U, redo
+      if (own) dev_free(scr, s);
+      uw = round_up(h.max_count, 32);
+      continue;
+    }
+    if (rc == SP2_OK) rc = mirror_async(&U, a.Out, a.bv, work, rowstat, ctl, s);
+    if (own) dev_free(scr, s);
+    return rc;
+  }
+}
+
+template <typename T>
 int multiply_t(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStream_t s) {
+  if (a.sym) return multiply_sym_t<T>(a, rowstat, ctl, s);
   const int n = a.A->n;
   int *fb = a.fb_prealloc;
   if (!fb) SP2_TRY(dev_alloc((void **)&fb, 2 * sizeof(int) * (size_t)n, s));
@@ -1820,7 +1915,7 @@ int multiply_t(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStre
       const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
       spgemm_dense_kernel<T><<<slots, kDenseThreads, 0, s>>>(
           view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha, (T)a.beta, (T)a.tau,
-          a.Add != nullptr && a.beta != 0.0, a.bv, rowstat, ctl, fb2, &ctl->n_fallback2, (T *)acc, mark);
+          a.Add != nullptr && a.beta != 0.0, a.bv, a.up, rowstat, ctl, fb2, &ctl->n_fallback2, (T *)acc, mark);
       note_launch();
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) rc = cuda_fail(e, "spgemm_dense_kernel", __FILE__, __LINE__);

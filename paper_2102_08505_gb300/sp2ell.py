@@ -48,7 +48,8 @@ class sp2_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("stall_rule", ctypes.c_int32),
                 ("n_fp64_tail", ctypes.c_int32), ("max_width", ctypes.c_int32), ("spgemm_path", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("switch_tol", ctypes.c_double), ("graph", ctypes.c_int32),
-                ("sizing", ctypes.c_int32), ("predictor", ctypes.POINTER(nnzpred_t)), ("stall_arm", ctypes.c_double)]
+                ("sizing", ctypes.c_int32), ("predictor", ctypes.POINTER(nnzpred_t)), ("stall_arm", ctypes.c_double),
+                ("symmetric", ctypes.c_int32)]
 
 
 class sp2_stats(ctypes.Structure):
@@ -69,7 +70,7 @@ class sp2_step_info(ctypes.Structure):
                 ("trXn2", ctypes.c_double), ("nnz_total", ctypes.c_int64), ("max_row_nnz", ctypes.c_int32),
                 ("required_width", ctypes.c_int32), ("spgemm_path", ctypes.c_int32),
                 ("rows_deferred", ctypes.c_int32), ("rows_dense", ctypes.c_int32),
-                ("spgemm_path_used", ctypes.c_int32)]
+                ("spgemm_path_used", ctypes.c_int32), ("symmetric", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 SP2_PROF_CLASSES = 4
@@ -378,10 +379,12 @@ def sp2_x0(H, X0, tau, stream=None):
     return lo.value, hi.value
 
 
-def sp2_step(X, Xn, nocc, tau, traces=None, spgemm_path=0, stream=None, raise_on_overflow=True):
-    """One SP2 iteration X -> Xn.  traces = (trX, trX2) of X if known.  Returns the
-    sp2_step_info record (and the status when raise_on_overflow=False)."""
+def sp2_step(X, Xn, nocc, tau, traces=None, spgemm_path=0, stream=None, raise_on_overflow=True, symmetric=False):
+    """One SP2 iteration X -> Xn.  traces = (trX, trX2) of X if known.  symmetric: X is
+    exactly symmetric (the product's upper triangle is computed and mirrored).  Returns
+    the sp2_step_info record (and the status when raise_on_overflow=False)."""
     info = sp2_step_info()
+    info.symmetric = 1 if symmetric else 0
     if traces is not None:
         info.trX, info.trX2 = traces
         info.have_traces = 1

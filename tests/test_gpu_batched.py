@@ -97,3 +97,21 @@ def test_batched_argument_errors(gpu):
     with pytest.raises(S.Sp2Error) as e:
         S.sp2_purify_batched([F], [10.0], 1e-10)
     assert e.value.code == S.SP2E_ARG
+
+
+def test_batched_symmetric_mode_is_bitwise_the_full_product(gpu):
+    S = gpu
+    sizes = [700, 1300, 520]
+    Hs = [S.Ellpack.from_numpy(*I.tight_binding(m, seed=60 + k, delta=10.0, periodic=False))
+          for k, m in enumerate(sizes)]
+    noccs = [(m + 1) // 2 for m in sizes]
+    for prec in (S.SP2_PREC_F64, S.SP2_PREC_MIXED):
+        Da, sa = S.sp2_purify_batched(Hs, noccs, 1e-10, S.sp2_options_default(precision=prec, symmetric=1))
+        Db, sb = S.sp2_purify_batched(Hs, noccs, 1e-10, S.sp2_options_default(precision=prec, symmetric=0))
+        for m in range(len(sizes)):
+            assert sa[m]["iterations"] == sb[m]["iterations"] and sa[m]["branch"] == sb[m]["branch"]
+            ia, va, na = Da[m].to_numpy()
+            ib, vb, nb = Db[m].to_numpy()
+            assert np.array_equal(na, nb)
+            live = np.arange(ia.shape[1])[None, :] < na[:, None]
+            assert np.array_equal(np.where(live, va, 0), np.where(live, vb[:, :ia.shape[1]], 0))

@@ -291,6 +291,24 @@ def test_first_pass_variants(gpu, first_pass, fp32):
     S.sp2_step(d1, again, n / 2, 1e-5, spgemm_path=first_pass)
     for a, b in zip(out.to_numpy(), again.to_numpy()):
         assert np.array_equal(np.nan_to_num(a), np.nan_to_num(b))
+    # X1 is exactly symmetric: the upper-triangle product mirrored gives the same bits
+    sym = S.Ellpack.empty(n, out.width, dt)
+    info_s = S.sp2_step(d1, sym, n / 2, 1e-5, spgemm_path=first_pass, symmetric=True)
+    assert rows_equal(out.to_numpy(), sym.to_numpy())
+    assert (info_s.trXn, info_s.nnz_total, info_s.max_row_nnz) == (info.trXn, info.nnz_total, info.max_row_nnz)
+    assert info_s.trXn2 == pytest.approx(info.trXn2, rel=1e-13)
+
+
+def rows_equal(g1, g2):
+    """Stored entries of two ELLPACK results (idx, val, nnz) identical bit for bit."""
+    i1, v1, n1 = g1
+    i2, v2, n2 = g2
+    if not np.array_equal(n1, n2):
+        return False
+    w = min(i1.shape[1], i2.shape[1])
+    live = np.arange(w)[None, :] < n1[:, None]
+    return (np.array_equal(np.where(live, i1[:, :w], 0), np.where(live, i2[:, :w], 0)) and
+            np.array_equal(np.where(live, v1[:, :w], 0).view(np.int64), np.where(live, v2[:, :w], 0).view(np.int64)))
 
 
 def hub_matrix(n, hubs, hub_nnz, other_nnz, seed):
@@ -326,3 +344,33 @@ def test_all_three_passes(gpu, first_pass):
     rng = np.random.default_rng(4)
     rows = np.unique(np.concatenate([sorted(hubs), rng.choice(n, 300, replace=False)]))
     compare_spgemm(out.to_numpy(), X, X, X, -1.0 if up else 1.0, 2.0 if up else 0.0, 0.0, rows=rows)
+
+
+def test_symmetric_product_with_long_rows(gpu):
+    """The upper-triangle product on a symmetric matrix with hub rows (deferred to the
+    2^14-slot table and the dense pass, both in upper-triangle mode; lower parts longer
+    than the shared-memory sorts): the same bits as full rows, and the oracle's values."""
+    S = gpu
+    n = 12000
+    hubs = set(range(0, n, 1500)) | {n - 1}
+    X = hub_matrix(n, hubs, 700, 30, seed=5)
+    Xs = O.add(X, O.transpose(X), 1.0, 1.0)  # symmetric: X + X^T
+    dX = dev(S, Xs)
+    probe = S.Ellpack.empty(n, 32)
+    rc, info = S.sp2_step(dX, probe, n / 2, 0.0, raise_on_overflow=False)
+    w = ((info.required_width + 31) // 32) * 32
+    full = S.Ellpack.empty(n, w)
+    info_f = S.sp2_step(dX, full, n / 2, 0.0)
+    sym = S.Ellpack.empty(n, w)
+    info_s = S.sp2_step(dX, sym, n / 2, 0.0, symmetric=True)
+    assert info_f.rows_deferred > 0
+    assert rows_equal(full.to_numpy(), sym.to_numpy())
+    assert info_s.nnz_total == info_f.nnz_total and info_s.trXn == info_f.trXn
+    # too narrow an output: the same overflow report as full rows
+    narrow = S.Ellpack.empty(n, 64)
+    rc_s, inf_s = S.sp2_step(dX, narrow, n / 2, 0.0, symmetric=True, raise_on_overflow=False)
+    assert rc_s == S.SP2E_OVERFLOW and inf_s.required_width == info_f.max_row_nnz
+    up = info_s.branch == 2
+    rng = np.random.default_rng(6)
+    rows = np.unique(np.concatenate([sorted(hubs), rng.choice(n, 200, replace=False)]))
+    compare_spgemm(sym.to_numpy(), Xs, Xs, Xs, -1.0 if up else 1.0, 2.0 if up else 0.0, 0.0, rows=rows)

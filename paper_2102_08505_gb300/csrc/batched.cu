@@ -465,7 +465,7 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
     SP2_TRY(db.get(&d_views, sizeof(EllView<double>) * count));
     SP2_TRY(db.get(&d_off, sizeof(int) * (count + 1)));
     SP2_TRY(db.get(&d_rowmat, sizeof(int) * ntot));
-    SP2_TRY(db.get(&d_fb, sizeof(int) * 2 * (size_t)ntot));
+    SP2_TRY(db.get(&d_fb, sizeof(int) * 3 * (size_t)ntot));
     SP2_TRY(db.get(&d_bounds, sizeof(double) * 2 * count));
     SP2_TRY(db.get(&d_a32, sizeof(double) * count));
     SP2_TRY(db.get(&d_b32, sizeof(double) * count));

@@ -102,6 +102,7 @@ struct SpgemmCtl {
   int max_count;
   int n_fallback;   // count of the first deferred-row list
   int n_fallback2;  // count of the second deferred-row list
+  int n_fallbackw;  // count of the rows the window bin passes on
 };
 
 // rowstat[r] = {diagonal value, sum of squares} of output row r (post-threshold).
@@ -138,7 +139,7 @@ struct MultiplyArgs {
   double alpha, beta, tau;
   int path;  // first pass: 0 automatic, 1..4 column blocks, 10..12 hash table
   BatchView bv{};              // per-row coefficients for batched multiplies
-  int *fb_prealloc = nullptr;  // 2*n ints for the deferred-row lists (null: allocated per call)
+  int *fb_prealloc = nullptr;  // 3*n ints for the deferred-row lists (null: allocated per call)
   // X*X (+ X) with X symmetric (A == B, Add null or A): compute the upper triangle and
   // mirror it (bitwise the same result as full rows, about half the products)
   bool sym = false;

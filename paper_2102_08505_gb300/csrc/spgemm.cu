@@ -1499,6 +1499,160 @@ __global__ void __launch_bounds__(kDenseThreads)
   }
 }
 
+// ------------------------------------------------------------------ window bin
+// One CTA per deferred row whose product columns span at most WIN (banded rows: the
+// paper's chain model Hamiltonians).  The row accumulates in a dense window of shared
+// memory indexed by column - lo (no lookup), one source row at a time with a barrier
+// between them (deterministic), a bit per column marking the structural entries; then
+// the window is scanned in column order.  Rows with a wider span go on to the next bin.
+constexpr int kWinThreads = 512;
+template <typename T>
+struct WinCfg {
+  static constexpr int WIN = (192 * 1024) / (int)sizeof(T);
+  static constexpr int SMEM = WIN * (int)sizeof(T) + (WIN / 32) * 4;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kWinThreads)
+    spgemm_window_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
+                         int use_add, BatchView bv, Upper up, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
+                         const int *__restrict__ in_list, const int *__restrict__ in_count, int *__restrict__ out_list,
+                         int *__restrict__ out_count) {
+  using Cfg = WinCfg<T>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *acc = reinterpret_cast<T *>(smem);
+  unsigned *touched = reinterpret_cast<unsigned *>(smem + (size_t)Cfg::WIN * sizeof(T));
+  __shared__ int s_warp[kWinThreads / 32];
+  __shared__ int s_lo[kWinThreads / 32], s_hi[kWinThreads / 32];
+  __shared__ double s_d[kWinThreads / 32], s_f[kWinThreads / 32];
+  const int ncol = Out.n;
+  const int nrows = *((volatile const int *)in_count);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const auto tb = mag_bits(tau);
+  int lmax = 0, lover = 0;
+  for (int q = blockIdx.x; q < nrows; q += gridDim.x) {
+    const int r = in_list[q];
+    T alpha_r = alpha, beta_r = beta;
+    int add_r = use_add;
+    if (bv.row_mat) {  // deferred rows belong to active matrices
+      const int m = bv.row_mat[r];
+      alpha_r = (T)bv.alpha[m];
+      beta_r = (T)bv.beta[m];
+      add_r = beta_r != T(0);
+    }
+    const int na = min(A.nnz[r], A.w);
+    const int nc = add_r ? min(Add.nnz[r], Add.w) : 0;
+    const int d0 = (add_r && up.tpd) ? min(max(up.tpd[r], 0), nc) : 0;
+    // column span of the row: first and last column of every source row (sorted rows)
+    int lo = INT_MAX, hi = -1;
+    for (int t = threadIdx.x; t < na; t += blockDim.x) {
+      const int k = A.idx[(size_t)r * A.w + t];
+      if ((unsigned)k >= (unsigned)B.n) continue;
+      const int nb = min(B.nnz[k], B.w);
+      const int st = up.tp ? min(max(up.tp[(size_t)r * A.w + t], 0), nb) : 0;
+      if (st < nb) {
+        lo = min(lo, B.idx[(size_t)k * B.w + st]);
+        hi = max(hi, B.idx[(size_t)k * B.w + nb - 1]);
+      }
+    }
+    if (threadIdx.x == 0 && d0 < nc) {
+      lo = min(lo, Add.idx[(size_t)r * Add.w + d0]);
+      hi = max(hi, Add.idx[(size_t)r * Add.w + nc - 1]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = min(lo, __shfl_xor_sync(kFull, lo, o));
+      hi = max(hi, __shfl_xor_sync(kFull, hi, o));
+    }
+    if (lane == 0) { s_lo[wid] = lo; s_hi[wid] = hi; }
+    __syncthreads();
+    lo = INT_MAX; hi = -1;
+    for (int w = 0; w < nwarp; ++w) { lo = min(lo, s_lo[w]); hi = max(hi, s_hi[w]); }
+    lo = max(lo, 0);
+    hi = min(hi, ncol - 1);
+    __syncthreads();
+    if (hi >= lo && hi - lo + 1 > Cfg::WIN) {  // too wide: the next bin
+      if (threadIdx.x == 0) out_list[atomicAdd(out_count, 1)] = r;
+      continue;
+    }
+    const int span = hi >= lo ? hi - lo + 1 : 0;
+    for (int c = threadIdx.x; c < span; c += blockDim.x) acc[c] = T(0);
+    for (int c = threadIdx.x; c < (span + 31) / 32; c += blockDim.x) touched[c] = 0u;
+    __syncthreads();
+    if (d0 < nc) {
+      for (int s = d0 + threadIdx.x; s < nc; s += blockDim.x) {
+        const int j = Add.idx[(size_t)r * Add.w + s];
+        if (j < lo || j > hi) continue;
+        acc[j - lo] = fmadd(beta_r, Add.val[(size_t)r * Add.w + s], acc[j - lo]);
+        atomicOr(touched + ((j - lo) >> 5), 1u << ((j - lo) & 31));
+      }
+      __syncthreads();
+    }
+    // one source row at a time in A's row order: its columns are distinct, so threads
+    // update distinct accumulators; the barrier orders the source rows
+    for (int t = 0; t < na; ++t) {
+      const int k = A.idx[(size_t)r * A.w + t];
+      if ((unsigned)k < (unsigned)B.n) {
+        const T a = alpha_r * A.val[(size_t)r * A.w + t];
+        const int nb = min(B.nnz[k], B.w);
+        const int st = up.tp ? min(max(up.tp[(size_t)r * A.w + t], 0), nb) : 0;
+        for (int s = st + threadIdx.x; s < nb; s += blockDim.x) {
+          const int j = B.idx[(size_t)k * B.w + s];
+          if (j < lo || j > hi) continue;
+          acc[j - lo] = fmadd(a, B.val[(size_t)k * B.w + s], acc[j - lo]);
+          atomicOr(touched + ((j - lo) >> 5), 1u << ((j - lo) & 31));
+        }
+      }
+      __syncthreads();
+    }
+    // scan the window in column order: structural entries that pass the drop rule
+    int base = 0;
+    double d = 0.0, f = 0.0;
+    for (int c0 = 0; c0 < span; c0 += blockDim.x) {
+      const int c = c0 + threadIdx.x;
+      bool keep = false;
+      T v = T(0);
+      if (c < span && ((touched[c >> 5] >> (c & 31)) & 1u)) {
+        v = acc[c];
+        keep = tau == T(0) || mag_bits(v) > tb;
+      }
+      int total;
+      const int pos = base + block_exclusive_scan_ballot<T>(keep, s_warp, total);
+      if (keep) {
+        const int j = lo + c;
+        if (pos < Out.w) {
+          Out.idx[(size_t)r * Out.w + pos] = j;
+          Out.val[(size_t)r * Out.w + pos] = v;
+        }
+        const double dv = (double)v;
+        if (j == r) d += dv;
+        f = fma(dv, dv, f);
+      }
+      base += total;
+    }
+    d = warp_sum(d);
+    f = warp_sum(f);
+    if (lane == 0) { s_d[wid] = d; s_f[wid] = f; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double dd = 0.0, ff = 0.0;
+      for (int w = 0; w < nwarp; ++w) { dd += s_d[w]; ff += s_f[w]; }
+      lmax = max(lmax, base);
+      if (base > Out.w) {
+        ++lover;
+        rowstat[r] = make_double2(0.0, 0.0);
+      } else {
+        Out.nnz[r] = base;
+        rowstat[r] = make_double2(dd, ff);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (lmax) atomicMax(&ctl->max_count, lmax);
+    if (lover) atomicAdd(&ctl->overflow_rows, lover);
+  }
+}
+
 // ------------------------------------------------------------------ add
 // A <- drop_tau(alpha*A + beta*B), warp per row, table of 2^11 slots.
 template <typename T>
@@ -1807,8 +1961,33 @@ int launch_block_r(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int 
 // First pass over every row (path: 0 automatic, 1/2/4 column blocks with that many
 // warps per row, 10..12 hash table of 2^path slots per warp), then the deferred rows in
 // a one-warp 2^14-slot hash table.
+// Window bin over the rows of a device-side list; rows wider than the window go to out.
+template <typename T>
+int launch_window(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, const int *in, const int *in_count, int *out,
+                  int *out_count, cudaStream_t s) {
+  using Cfg = WinCfg<T>;
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!attr_set[dev]) {
+    SP2_TRY(set_smem(spgemm_window_kernel<T>, Cfg::SMEM));
+    attr_set[dev] = true;
+  }
+  const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
+  prof_begin(SP2_PROF_LARGE, s);
+  spgemm_window_kernel<T><<<num_sms(), kWinThreads, Cfg::SMEM, s>>>(
+      view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha, (T)a.beta, (T)a.tau,
+      a.Add != nullptr && a.beta != 0.0, a.bv, a.up, rowstat, ctl, in, in_count, out, out_count);
+  note_launch();
+  prof_end(SP2_PROF_LARGE, s);
+  SP2_CUDA(cudaGetLastError());
+  return SP2_OK;
+}
+
 template <typename T, int QM>
-int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb1, int *fb2, int path, cudaStream_t s) {
+int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb1, int *fbw, int *fb2, int path,
+                cudaStream_t s) {
   int rc;
   switch (path) {
     case 1: rc = launch_block_r<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
@@ -1826,8 +2005,11 @@ int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
                           : launch_super_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s);
       break;
   }
+  // deferred rows: a dense window per CTA when the row's span fits it, then the 2^14-slot
+  // table, then dense global rows
+  if (rc == SP2_OK) rc = launch_window<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, fbw, &ctl->n_fallbackw, s);
   if (rc == SP2_OK)
-    rc = launch_hash<T, 14, QM>(a, rowstat, ctl, fb1, &ctl->n_fallback, fb2, &ctl->n_fallback2, s);
+    rc = launch_hash<T, 14, QM>(a, rowstat, ctl, fbw, &ctl->n_fallbackw, fb2, &ctl->n_fallback2, s);
   return rc;
 }
 
@@ -1899,11 +2081,11 @@ int multiply_t(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStre
   if (a.sym) return multiply_sym_t<T>(a, rowstat, ctl, s);
   const int n = a.A->n;
   int *fb = a.fb_prealloc;
-  if (!fb) SP2_TRY(dev_alloc((void **)&fb, 2 * sizeof(int) * (size_t)n, s));
-  int *fb1 = fb, *fb2 = fb + n;
+  if (!fb) SP2_TRY(dev_alloc((void **)&fb, 3 * sizeof(int) * (size_t)n, s));
+  int *fb1 = fb, *fbw = fb + n, *fb2 = fb + 2 * (size_t)n;
   const int qm_need = (a.B->width + 31) / 32;
-  int rc = qm_need <= 4 ? launch_bins<T, 4>(a, rowstat, ctl, fb1, fb2, a.path, s)
-                        : launch_bins<T, 8>(a, rowstat, ctl, fb1, fb2, a.path, s);
+  int rc = qm_need <= 4 ? launch_bins<T, 4>(a, rowstat, ctl, fb1, fbw, fb2, a.path, s)
+                        : launch_bins<T, 8>(a, rowstat, ctl, fb1, fbw, fb2, a.path, s);
   if (rc == SP2_OK) {
     // bin 2: rows beyond the largest table, dense global-memory rows
     void *acc = nullptr;

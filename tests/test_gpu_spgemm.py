@@ -326,12 +326,12 @@ def hub_matrix(n, hubs, hub_nnz, other_nnz, seed):
 
 @pytest.mark.parametrize("first_pass", [0, 5])
 def test_all_three_passes(gpu, first_pass):
-    """Rows with more column groups than the block accumulator holds go to the 2^14-slot
-    table; rows with more distinct columns than that go to the dense global-row pass.
-    Sampled rows (all hubs included) against the oracle (tau = 0: every structural entry
-    is kept)."""
+    """Rows with more column groups than the block accumulator holds and a column span
+    wider than the shared-memory window go to the 2^14-slot table; rows with more
+    distinct columns than that go to the dense global-row pass.  Sampled rows (all hubs
+    included) against the oracle (tau = 0: every structural entry is kept)."""
     S = gpu
-    n = 20000
+    n = 60000
     hubs = set(range(0, n, 2000)) | {n - 1}
     X = hub_matrix(n, hubs, 1000, 40, seed=3)
     dX = dev(S, X)
@@ -346,12 +346,13 @@ def test_all_three_passes(gpu, first_pass):
     compare_spgemm(out.to_numpy(), X, X, X, -1.0 if up else 1.0, 2.0 if up else 0.0, 0.0, rows=rows)
 
 
-def test_symmetric_product_with_long_rows(gpu):
-    """The upper-triangle product on a symmetric matrix with hub rows (deferred to the
-    2^14-slot table and the dense pass, both in upper-triangle mode; lower parts longer
-    than the shared-memory sorts): the same bits as full rows, and the oracle's values."""
+@pytest.mark.parametrize("n", [12000, 60000])
+def test_symmetric_product_with_long_rows(gpu, n):
+    """The upper-triangle product on a symmetric matrix with hub rows, deferred (n = 12000:
+    to the window bin; n = 60000: to the 2^14-slot table and the dense pass, all in
+    upper-triangle mode; lower parts longer than the shared-memory sorts): the same bits
+    as full rows, and the oracle's values."""
     S = gpu
-    n = 12000
     hubs = set(range(0, n, 1500)) | {n - 1}
     X = hub_matrix(n, hubs, 700, 30, seed=5)
     Xs = O.add(X, O.transpose(X), 1.0, 1.0)  # symmetric: X + X^T
@@ -374,3 +375,28 @@ def test_symmetric_product_with_long_rows(gpu):
     rng = np.random.default_rng(6)
     rows = np.unique(np.concatenate([sorted(hubs), rng.choice(n, 200, replace=False)]))
     compare_spgemm(sym.to_numpy(), Xs, Xs, Xs, -1.0 if up else 1.0, 2.0 if up else 0.0, 0.0, rows=rows)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_window_bin_banded_long_rows(gpu, dtype):
+    """A banded matrix with rows of ~1600 entries: every product row outgrows the block
+    accumulator and is deferred to the dense-window bin (span ~3200 columns).  Sampled rows
+    against the oracle; symmetric and full products bit for bit equal."""
+    S = gpu
+    n, band = 20000, 800
+    H = ell(I.banded(n, band=band, seed=4, delta=10.0))
+    dt = S.SP2_F64 if dtype == "f64" else S.SP2_F32
+    Hq = f32_input(H) if dt == S.SP2_F32 else H
+    dH = dev(S, Hq, dt)
+    rc, info = S.sp2_step(dH, S.Ellpack.empty(n, 32, dt), n / 2, 1e-5, raise_on_overflow=False)
+    w = ((info.required_width + 31) // 32) * 32
+    full = S.Ellpack.empty(n, w, dt)
+    info = S.sp2_step(dH, full, n / 2, 1e-5)
+    assert info.rows_deferred > n // 2 and info.rows_dense == 0
+    sym = S.Ellpack.empty(n, w, dt)
+    S.sp2_step(dH, sym, n / 2, 1e-5, symmetric=True)
+    assert rows_equal(full.to_numpy(), sym.to_numpy())
+    up = info.branch == 2
+    rows = np.unique(np.concatenate([[0, 1, band, n // 2, n - 1], np.random.default_rng(8).choice(n, 60, replace=False)]))
+    compare_spgemm(full.to_numpy(), Hq, Hq, Hq, -1.0 if up else 1.0, 2.0 if up else 0.0, 1e-5, fp32=dt == S.SP2_F32,
+                   rows=rows)

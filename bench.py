@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--path", type=int, default=0,
                    help="SpGEMM first pass: 0 automatic, 1/2/4/6 column blocks with 1/2/4/5 warps per row, 3 two-step, "
                         "5 runs, 10-12 hash, -1 tuned")
+    p.add_argument("--symmetric", action="store_true",
+                   help="SP2 steps compute the upper triangle of the symmetric product and mirror it")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
@@ -288,7 +290,7 @@ def run_ours(a):
     w1 = 4 * X0.width
     while True:
         X1 = S.Ellpack.empty(a.n, w1, DT)
-        rc, info = S.sp2_step(X0, X1, nocc, a.tau, raise_on_overflow=False, symmetric=True)
+        rc, info = S.sp2_step(X0, X1, nocc, a.tau, raise_on_overflow=False, symmetric=a.symmetric)
         if rc == 0:
             break
         w1 = ((info.required_width + 31) // 32) * 32
@@ -299,22 +301,23 @@ def run_ours(a):
     traces = (info.trXn, info.trXn2)
     del X0, H
     X2 = S.Ellpack.empty(a.n, 32, DT)
-    rc, info = S.sp2_step(X1, X2, nocc, a.tau, traces=traces, raise_on_overflow=False, symmetric=True)
+    rc, info = S.sp2_step(X1, X2, nocc, a.tau, traces=traces, raise_on_overflow=False, symmetric=a.symmetric)
     w2 = ((info.required_width + 31) // 32) * 32
     X2 = S.Ellpack.empty(a.n, w2, DT)
-    info = S.sp2_step(X1, X2, nocc, a.tau, traces=traces, spgemm_path=a.path, symmetric=True)
+    info = S.sp2_step(X1, X2, nocc, a.tau, traces=traces, spgemm_path=a.path, symmetric=a.symmetric)
     torch.cuda.synchronize()
     h_idx, h_val, h_nnz = [t.cpu().numpy() for t in (X1.idx, X1.val, X1.nnz)]
     nnz_in = int(h_nnz.sum())
     fmas = fma_count(h_idx, h_nnz)
-    fmas_exec = fma_count_upper(h_idx, h_nnz)  # the symmetric product computes the upper triangle
+    # products executed: the upper triangle only when the symmetric product is used
+    fmas_exec = fma_count_upper(h_idx, h_nnz) if a.symmetric else fmas
     nnz_out = int(info.nnz_total)
     alg_bytes = (4 + esz) * (2 * nnz_in + nnz_out) + 12 * a.n  # A, B, C read/written once + 3 nnz arrays
     in_bytes = X1.idx.numel() * 4 + X1.val.numel() * esz + a.n * 4
 
     # ---------------- device-timed steps
     for _ in range(a.warmup):
-        S.sp2_step(X1, X2, nocc, a.tau, traces=traces, spgemm_path=a.path, symmetric=True)
+        S.sp2_step(X1, X2, nocc, a.tau, traces=traces, spgemm_path=a.path, symmetric=a.symmetric)
     torch.cuda.synchronize()
     clocks = Clocks(local, enabled=not a.no_clocks)
     shard.barrier()
@@ -324,7 +327,7 @@ def run_ours(a):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(a.steps):
-        S.sp2_step(X1, X2, nocc, a.tau, traces=traces, spgemm_path=a.path, symmetric=True)
+        S.sp2_step(X1, X2, nocc, a.tau, traces=traces, spgemm_path=a.path, symmetric=a.symmetric)
     e1.record(stream)
     torch.cuda.synchronize()
     prof = S.sp2_profile_stop()
@@ -348,7 +351,7 @@ def run_ours(a):
                 "peak_source": "derived: 152 SMs x %s FMA/clk x 2 flop x 2.07 GHz" % (
                     "2 FP64" if a.dtype == "f64" else "128 FP32"),
                 "flops_per_launch": 2.0 * fmas_exec,
-                "flops": "2 x the products executed (upper triangle of the symmetric product)"}
+                "flops": "2 x the products executed" + (" (upper triangle of the symmetric product)" if a.symmetric else "")}
     hbm_view = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                 "peak_source": "of measured" if "fallback" not in pk else "of fallback",
                 "algorithmic_bytes_per_launch": alg_bytes}
@@ -374,7 +377,7 @@ def run_ours(a):
 
         def e2e_step():
             S._check(S.lib.ellpack_upload(S._d(Xin), hi.data_ptr(), hv.data_ptr(), hn.data_ptr(), S._stream(stream)))
-            S.sp2_step(Xin, X2, nocc, a.tau, traces=traces, spgemm_path=a.path, symmetric=True)
+            S.sp2_step(Xin, X2, nocc, a.tau, traces=traces, spgemm_path=a.path, symmetric=a.symmetric)
             S._check(S.lib.ellpack_download(S._d(X2), oi.data_ptr(), ov.data_ptr(), on.data_ptr(), S._stream(stream)))
 
         for _ in range(max(1, a.warmup)):
@@ -405,7 +408,7 @@ def run_ours(a):
             "config": workload_config(a, {
                 "width_in": w1, "width_out": w2, "nnz_per_row_in": nnz_in / a.n, "nnz_per_row_out": nnz_out / a.n,
                 "fma_per_row": fmas / a.n, "fma_per_row_executed": fmas_exec / a.n,
-                "symmetric_product": "upper triangle computed and mirrored",
+                "symmetric_product": "upper triangle computed and mirrored" if a.symmetric else "full rows",
                 "branch": "2X-X^2" if info.branch == 2 else "X^2",
                 "l2": "no flush: inputs %.2f GB > 129 MB L2" % (in_bytes / 1e9),
                 "parallelism": "replicas" if world > 1 else "single GPU"}),

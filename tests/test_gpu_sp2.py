@@ -146,7 +146,7 @@ def test_sp2_stall_arm_matches_oracle(gpu, arm):
 
 
 def test_sp2_symmetric_mode_is_bitwise_the_full_product(gpu):
-    """sp2_purify with the upper-triangle products (default) and with full rows: the same
+    """sp2_purify with the upper-triangle products and with full rows (default): the same
     iterations, traces and density matrix bit for bit, in FP64 and mixed precision; a
     Hamiltonian that is not exactly symmetric is refused in symmetric mode."""
     S = gpu
@@ -167,7 +167,7 @@ def test_sp2_symmetric_mode_is_bitwise_the_full_product(gpu):
     i0 = int(np.argmax(H.nnz > 1))
     bad[i0, 0 if H.idx[i0, 0] != i0 else 1] *= 1.0 + 1e-12
     with pytest.raises(S.Sp2Error) as e:
-        S.sp2_purify(S.Ellpack.from_numpy(H.idx, bad, H.nnz), n // 2, 1e-10)
+        S.sp2_purify(S.Ellpack.from_numpy(H.idx, bad, H.nnz), n // 2, 1e-10, S.sp2_options_default(symmetric=1))
     assert e.value.code == S.SP2E_ARG
     S.sp2_purify(S.Ellpack.from_numpy(H.idx, bad, H.nnz), n // 2, 1e-10, S.sp2_options_default(symmetric=0),
                  allow_notconv=True)

@@ -75,6 +75,11 @@ int sp2_version(void);
 /* Message of the last failing call on this thread ("" if none). */
 const char *sp2_last_error_string(void);
 
+/* Returns to the driver the device memory the library keeps for reuse on the current
+ * device (its stream-ordered allocations come from a library-owned pool that keeps freed
+ * memory).  Synchronises the device.  Errors: SP2E_CUDA. */
+int sp2_release_memory(void);
+
 /*
  * Allocates an n x n ELLPACK matrix of the given width and dtype on the current device
  * (stream-ordered allocation on `stream`) and sets every nnz[i] to 0.  width >= 1 is

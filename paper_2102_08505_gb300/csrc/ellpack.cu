@@ -61,10 +61,41 @@ int check_matrix(const ellpack_t *m, const char *name) {
 }
 
 // ------------------------------------------------------------------ device memory
+// The library's stream-ordered allocations come from its own pool per device, which keeps
+// freed memory for reuse (release threshold: unlimited) instead of handing it back to the
+// driver at every synchronisation; sp2_release_memory() returns it.
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[64] = {};
+
+int library_pool(cudaMemPool_t *pool) {
+  int dev = 0;
+  SP2_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(SP2E_ARG, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    SP2_CUDA(cudaMemPoolCreate(&p, &props));
+    uint64_t keep = UINT64_MAX;
+    SP2_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pool[dev] = p;
+  }
+  *pool = g_pool[dev];
+  return SP2_OK;
+}
+}  // namespace
+
 int dev_alloc(void **p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  cudaMemPool_t pool = nullptr;
+  SP2_TRY(library_pool(&pool));
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -576,5 +607,17 @@ extern "C" int ellpack_copy(const ellpack_t *src, ellpack_t *dst, void *stream) 
   dev_free(dov, s);
   SP2_TRY(rc);
   if (hov > 0) return fail(SP2E_OVERFLOW, "ellpack_copy: %d row(s) longer than dst width %d", hov, dst->width);
+  return SP2_OK;
+}
+
+extern "C" int sp2_release_memory(void) {
+  int dev = 0;
+  SP2_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(SP2E_ARG, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (g_pool[dev]) {
+    SP2_CUDA(cudaDeviceSynchronize());
+    SP2_CUDA(cudaMemPoolTrimTo(g_pool[dev], 0));
+  }
   return SP2_OK;
 }

@@ -92,6 +92,7 @@ def _load():
     sig = {
         "sp2_version": ([], ctypes.c_int),
         "sp2_last_error_string": ([], ctypes.c_char_p),
+        "sp2_release_memory": ([], ctypes.c_int),
         "ellpack_create": ([I, I, I, V, E], ctypes.c_int),
         "ellpack_wrap": ([I, I, I, V, V, V, E], ctypes.c_int),
         "ellpack_destroy": ([E, V], ctypes.c_int),

@@ -379,11 +379,12 @@ def test_symmetric_product_with_long_rows(gpu, n):
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_window_bin_banded_long_rows(gpu, dtype):
-    """A banded matrix with rows of ~1600 entries: every product row outgrows the block
-    accumulator and is deferred to the dense-window bin (span ~3200 columns).  Sampled rows
-    against the oracle; symmetric and full products bit for bit equal."""
+    """A banded matrix with rows of ~3600 entries: every product row (~450 column groups)
+    outgrows the block accumulator and is deferred to the dense-window bin (span ~7200
+    columns).  Sampled rows against the oracle; symmetric and full products bit for bit
+    equal."""
     S = gpu
-    n, band = 20000, 800
+    n, band = 12000, 1800
     H = ell(I.banded(n, band=band, seed=4, delta=10.0))
     dt = S.SP2_F64 if dtype == "f64" else S.SP2_F32
     Hq = f32_input(H) if dt == S.SP2_F32 else H

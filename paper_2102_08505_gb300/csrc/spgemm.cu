@@ -1529,6 +1529,20 @@ __global__ void __launch_bounds__(kWinThreads)
   const int nrows = *((volatile const int *)in_count);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const auto tb = mag_bits(tau);
+  // structural entries need marks only when tau = 0 (a slot nothing reached holds 0,
+  // which any tau > 0 drops)
+  const bool marks = tau == T(0);
+  // marks of one pass: the lanes of a warp that share a mark word OR their bits and one
+  // of them sets them (consecutive columns share words)
+  auto mark = [&](bool on, int c) {
+    const unsigned act = __ballot_sync(kFull, on);
+    if (on) {
+      const unsigned word = (unsigned)c >> 5;
+      const unsigned peers = __match_any_sync(act, word);
+      const unsigned bits = __reduce_or_sync(peers, 1u << (c & 31));
+      if (lane == __ffs(peers) - 1) atomicOr(touched + word, bits);
+    }
+  };
   int lmax = 0, lover = 0;
   for (int q = blockIdx.x; q < nrows; q += gridDim.x) {
     const int r = in_list[q];
@@ -1576,14 +1590,16 @@ __global__ void __launch_bounds__(kWinThreads)
     }
     const int span = hi >= lo ? hi - lo + 1 : 0;
     for (int c = threadIdx.x; c < span; c += blockDim.x) acc[c] = T(0);
-    for (int c = threadIdx.x; c < (span + 31) / 32; c += blockDim.x) touched[c] = 0u;
+    if (marks)
+      for (int c = threadIdx.x; c < (span + 31) / 32; c += blockDim.x) touched[c] = 0u;
     __syncthreads();
     if (d0 < nc) {
-      for (int s = d0 + threadIdx.x; s < nc; s += blockDim.x) {
-        const int j = Add.idx[(size_t)r * Add.w + s];
-        if (j < lo || j > hi) continue;
-        acc[j - lo] = fmadd(beta_r, Add.val[(size_t)r * Add.w + s], acc[j - lo]);
-        atomicOr(touched + ((j - lo) >> 5), 1u << ((j - lo) & 31));
+      for (int s0 = d0; s0 < nc; s0 += blockDim.x) {  // warp-uniform trip count (the marks vote)
+        const int s = s0 + threadIdx.x;
+        const int j = s < nc ? Add.idx[(size_t)r * Add.w + s] : -1;
+        const bool in = s < nc && j >= lo && j <= hi;
+        if (in) acc[j - lo] = fmadd(beta_r, Add.val[(size_t)r * Add.w + s], acc[j - lo]);
+        if (marks) mark(in, j - lo);
       }
       __syncthreads();
     }
@@ -1595,11 +1611,20 @@ __global__ void __launch_bounds__(kWinThreads)
         const T a = alpha_r * A.val[(size_t)r * A.w + t];
         const int nb = min(B.nnz[k], B.w);
         const int st = up.tp ? min(max(up.tp[(size_t)r * A.w + t], 0), nb) : 0;
-        for (int s = st + threadIdx.x; s < nb; s += blockDim.x) {
-          const int j = B.idx[(size_t)k * B.w + s];
-          if (j < lo || j > hi) continue;
-          acc[j - lo] = fmadd(a, B.val[(size_t)k * B.w + s], acc[j - lo]);
-          atomicOr(touched + ((j - lo) >> 5), 1u << ((j - lo) & 31));
+        if (marks) {
+          for (int s0 = st; s0 < nb; s0 += blockDim.x) {  // warp-uniform trip count (the marks vote)
+            const int s = s0 + threadIdx.x;
+            const int j = s < nb ? B.idx[(size_t)k * B.w + s] : -1;
+            const bool in = s < nb && j >= lo && j <= hi;
+            if (in) acc[j - lo] = fmadd(a, B.val[(size_t)k * B.w + s], acc[j - lo]);
+            mark(in, j - lo);
+          }
+        } else {
+          for (int s = st + threadIdx.x; s < nb; s += blockDim.x) {
+            const int j = B.idx[(size_t)k * B.w + s];
+            if (j < lo || j > hi) continue;
+            acc[j - lo] = fmadd(a, B.val[(size_t)k * B.w + s], acc[j - lo]);
+          }
         }
       }
       __syncthreads();
@@ -1611,9 +1636,9 @@ __global__ void __launch_bounds__(kWinThreads)
       const int c = c0 + threadIdx.x;
       bool keep = false;
       T v = T(0);
-      if (c < span && ((touched[c >> 5] >> (c & 31)) & 1u)) {
+      if (c < span && (!marks || ((touched[c >> 5] >> (c & 31)) & 1u))) {
         v = acc[c];
-        keep = tau == T(0) || mag_bits(v) > tb;
+        keep = marks || mag_bits(v) > tb;
       }
       int total;
       const int pos = base + block_exclusive_scan_ballot<T>(keep, s_warp, total);

@@ -51,8 +51,9 @@ def parse():
     p.add_argument("--path", type=int, default=0,
                    help="SpGEMM first pass: 0 automatic, 1/2/4/6 column blocks with 1/2/4/5 warps per row, 3 two-step, "
                         "5 runs, 10-12 hash, -1 tuned")
-    p.add_argument("--symmetric", action="store_true",
-                   help="SP2 steps compute the upper triangle of the symmetric product and mirror it")
+    p.add_argument("--full-rows", dest="symmetric", action="store_false",
+                   help="SP2 steps compute full product rows instead of the upper triangle of the "
+                        "symmetric product mirrored (the default)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")

@@ -369,10 +369,10 @@ typedef struct sp2_options {
                            overflow the multiply is repeated at the exact width it counted) */
   const nnzpred_t *predictor;  /* for sizing 2 */
   double stall_arm;     /* the stall rule arms once |trX - trX2| < stall_arm (default 0.1) */
-  int32_t symmetric;    /* 1: H must be exactly symmetric (checked: SP2E_ARG otherwise);
-                           every product computes its upper triangle and mirrors it (the
-                           same result bit for bit, about half the products).  0 (default):
-                           full rows, no check */
+  int32_t symmetric;    /* 1 (default): H must be exactly symmetric (checked: SP2E_ARG
+                           otherwise); every product computes its upper triangle and mirrors
+                           it (the same result bit for bit, about half the products).
+                           0: full rows, no check */
 } sp2_options;
 
 typedef struct sp2_stats {

@@ -75,7 +75,7 @@ extern "C" void sp2_options_default(sp2_options *o) {
   o->sizing = 0;
   o->predictor = nullptr;
   o->stall_arm = 0.1;
-  o->symmetric = 0;
+  o->symmetric = 1;
 }
 
 extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2_options *opt_in, ellpack_t *D,

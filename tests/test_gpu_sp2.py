@@ -146,7 +146,7 @@ def test_sp2_stall_arm_matches_oracle(gpu, arm):
 
 
 def test_sp2_symmetric_mode_is_bitwise_the_full_product(gpu):
-    """sp2_purify with the upper-triangle products and with full rows (default): the same
+    """sp2_purify with the upper-triangle products (default) and with full rows: the same
     iterations, traces and density matrix bit for bit, in FP64 and mixed precision; a
     Hamiltonian that is not exactly symmetric is refused in symmetric mode."""
     S = gpu

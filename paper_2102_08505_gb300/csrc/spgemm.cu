@@ -1506,6 +1506,7 @@ __global__ void __launch_bounds__(kDenseThreads)
 // between them (deterministic), a bit per column marking the structural entries; then
 // the window is scanned in column order.  Rows with a wider span go on to the next bin.
 constexpr int kWinThreads = 512;
+constexpr int kWinPre = 8;  // entries of the next source row each thread holds in registers
 template <typename T>
 struct WinCfg {
   static constexpr int WIN = (192 * 1024) / (int)sizeof(T);
@@ -1605,13 +1606,13 @@ __global__ void __launch_bounds__(kWinThreads)
     }
     // one source row at a time in A's row order: its columns are distinct, so threads
     // update distinct accumulators; the barrier orders the source rows
-    for (int t = 0; t < na; ++t) {
-      const int k = A.idx[(size_t)r * A.w + t];
-      if ((unsigned)k < (unsigned)B.n) {
-        const T a = alpha_r * A.val[(size_t)r * A.w + t];
-        const int nb = min(B.nnz[k], B.w);
-        const int st = up.tp ? min(max(up.tp[(size_t)r * A.w + t], 0), nb) : 0;
-        if (marks) {
+    if (marks) {
+      for (int t = 0; t < na; ++t) {
+        const int k = A.idx[(size_t)r * A.w + t];
+        if ((unsigned)k < (unsigned)B.n) {
+          const T a = alpha_r * A.val[(size_t)r * A.w + t];
+          const int nb = min(B.nnz[k], B.w);
+          const int st = up.tp ? min(max(up.tp[(size_t)r * A.w + t], 0), nb) : 0;
           for (int s0 = st; s0 < nb; s0 += blockDim.x) {  // warp-uniform trip count (the marks vote)
             const int s = s0 + threadIdx.x;
             const int j = s < nb ? B.idx[(size_t)k * B.w + s] : -1;
@@ -1619,15 +1620,61 @@ __global__ void __launch_bounds__(kWinThreads)
             if (in) acc[j - lo] = fmadd(a, B.val[(size_t)k * B.w + s], acc[j - lo]);
             mark(in, j - lo);
           }
-        } else {
-          for (int s = st + threadIdx.x; s < nb; s += blockDim.x) {
-            const int j = B.idx[(size_t)k * B.w + s];
-            if (j < lo || j > hi) continue;
-            acc[j - lo] = fmadd(a, B.val[(size_t)k * B.w + s], acc[j - lo]);
+        }
+        __syncthreads();
+      }
+    } else {
+      // the next source row is loaded into registers (kWinPre entries per thread) while
+      // the current one accumulates, so a step waits on no global load
+      int cj[kWinPre], nj[kWinPre];
+      T cv[kWinPre], nv[kWinPre];
+      T ca = T(0), an = T(0);
+      const int *crow = B.idx;
+      const T *cvrow = B.val;
+      int cnb = 0, cst = 0, nnb = 0, nst = 0;
+      const int *nrow = B.idx;
+      const T *nvrow = B.val;
+      auto fetch = [&](int t, int (&jr)[kWinPre], T (&vr)[kWinPre], T &a, const int *&ri, const T *&rv, int &nb,
+                       int &st) {
+        a = T(0); nb = 0; st = 0; ri = B.idx; rv = B.val;
+        if (t < na) {
+          const int k = A.idx[(size_t)r * A.w + t];
+          if ((unsigned)k < (unsigned)B.n) {
+            a = alpha_r * A.val[(size_t)r * A.w + t];
+            nb = min(B.nnz[k], B.w);
+            st = up.tp ? min(max(up.tp[(size_t)r * A.w + t], 0), nb) : 0;
+            ri = B.idx + (size_t)k * B.w;
+            rv = B.val + (size_t)k * B.w;
           }
         }
+#pragma unroll
+        for (int u = 0; u < kWinPre; ++u) {
+          const int q = st + threadIdx.x + u * kWinThreads;
+          jr[u] = q < nb ? __ldg(ri + q) : -1;
+          vr[u] = q < nb ? __ldg(rv + q) : T(0);
+        }
+      };
+      fetch(0, cj, cv, ca, crow, cvrow, cnb, cst);
+      for (int t = 0; t < na; ++t) {
+        fetch(t + 1, nj, nv, an, nrow, nvrow, nnb, nst);
+#pragma unroll
+        for (int u = 0; u < kWinPre; ++u) {
+          const int j = cj[u];
+          if (j >= lo && j <= hi) acc[j - lo] = fmadd(ca, cv[u], acc[j - lo]);
+        }
+        // entries beyond the prefetched ones (source rows longer than kWinPre * threads)
+        for (int q = cst + threadIdx.x + kWinPre * kWinThreads; q < cnb; q += kWinThreads) {
+          const int j = __ldg(crow + q);
+          if (j >= lo && j <= hi) acc[j - lo] = fmadd(ca, __ldg(cvrow + q), acc[j - lo]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kWinPre; ++u) {
+          cj[u] = nj[u];
+          cv[u] = nv[u];
+        }
+        ca = an; crow = nrow; cvrow = nvrow; cnb = nnb; cst = nst;
       }
-      __syncthreads();
     }
     // scan the window in column order: structural entries that pass the drop rule
     int base = 0;

@@ -106,6 +106,11 @@ int ellpack_upload(ellpack_t *m, const int32_t *h_idx, const void *h_val, const 
  * stream.  Errors: SP2E_ARG, SP2E_CUDA. */
 int ellpack_download(const ellpack_t *m, int32_t *h_idx, void *h_val, int32_t *h_nnz, void *stream);
 
+/* The same copies, enqueued on `stream` without waiting: the host arrays hold the matrix
+ * once the stream's work up to this point has completed (pinned host memory lets the
+ * copies run beside kernels of other streams).  Errors: SP2E_ARG, SP2E_CUDA. */
+int ellpack_download_async(const ellpack_t *m, int32_t *h_idx, void *h_val, int32_t *h_nnz, void *stream);
+
 /* Device-to-device copy of rows: dst row i <- src row i (values converted when the
  * dtypes differ).  Same n; dst must not share arrays with src; dst->width may be smaller
  * than src->width as long as every row fits, else SP2E_OVERFLOW (those rows are left

@@ -515,6 +515,18 @@ extern "C" int ellpack_upload(ellpack_t *m, const int32_t *h_idx, const void *h_
   return SP2_OK;
 }
 
+extern "C" int ellpack_download_async(const ellpack_t *m, int32_t *h_idx, void *h_val, int32_t *h_nnz,
+                                      void *stream) {
+  SP2_TRY(check_matrix(m, "ellpack_download_async"));
+  if (!h_idx || !h_val || !h_nnz) return fail(SP2E_ARG, "ellpack_download_async: null host pointer");
+  cudaStream_t s = as_stream(stream);
+  size_t cells = (size_t)m->n * (size_t)m->width;
+  SP2_CUDA(cudaMemcpyAsync(h_idx, m->idx, cells * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  SP2_CUDA(cudaMemcpyAsync(h_val, m->val, cells * dtype_size(m->dtype), cudaMemcpyDeviceToHost, s));
+  SP2_CUDA(cudaMemcpyAsync(h_nnz, m->nnz, (size_t)m->n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  return SP2_OK;
+}
+
 extern "C" int ellpack_download(const ellpack_t *m, int32_t *h_idx, void *h_val, int32_t *h_nnz, void *stream) {
   SP2_TRY(check_matrix(m, "ellpack_download"));
   if (!h_idx || !h_val || !h_nnz) return fail(SP2E_ARG, "ellpack_download: null host pointer");

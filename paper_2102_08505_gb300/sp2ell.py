@@ -98,6 +98,7 @@ def _load():
         "ellpack_destroy": ([E, V], ctypes.c_int),
         "ellpack_upload": ([E, V, V, V, V], ctypes.c_int),
         "ellpack_download": ([E, V, V, V, V], ctypes.c_int),
+        "ellpack_download_async": ([E, V, V, V, V], ctypes.c_int),
         "ellpack_copy": ([E, E, V], ctypes.c_int),
         "ellpack_multiply": ([E, E, E, D, D, D, V, P(I)], ctypes.c_int),
         "ellpack_add": ([E, E, D, D, D, V, P(I)], ctypes.c_int),

@@ -110,3 +110,21 @@ def test_dense_round_trip(gpu, dtype):
     E = S.Ellpack.empty(A.n, 32, dt)
     S.ellpack_from_dense(Dp, E)
     _rows_equal(E.to_numpy(), A, fp32=dt == S.SP2_F32)
+
+
+def test_download_async_matches_download(gpu):
+    import torch
+    S = gpu
+    A = O.Ell(*I.random_sparse(500, seed=9, min_nnz=0, max_nnz=20, width=32))
+    dA = S.Ellpack.from_numpy(A.idx, A.val, A.nnz)
+    bufs = [(torch.empty((500, 32), dtype=torch.int32).pin_memory(), torch.empty((500, 32), dtype=torch.float64).pin_memory(),
+             torch.empty(500, dtype=torch.int32).pin_memory()) for _ in range(2)]
+    s = torch.cuda.Stream()
+    (i1, v1, n1), (i2, v2, n2) = bufs
+    S._check(S.lib.ellpack_download(S._d(dA), i1.data_ptr(), v1.data_ptr(), n1.data_ptr(), S._stream(s)))
+    S._check(S.lib.ellpack_download_async(S._d(dA), i2.data_ptr(), v2.data_ptr(), n2.data_ptr(), S._stream(s)))
+    s.synchronize()
+    assert torch.equal(n1, n2) and np.array_equal(n2.numpy(), A.nnz)
+    live = np.arange(32)[None, :] < A.nnz[:, None]
+    assert np.array_equal(np.where(live, i2.numpy(), 0), np.where(live, A.idx, 0))
+    assert np.array_equal(np.where(live, v2.numpy(), 0), np.where(live, A.val, 0))

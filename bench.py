@@ -247,9 +247,11 @@ def spgemm_kernel_name(a):
     p = a.path
     if p == 0:
         p = 4 if a.dtype == "f64" else 3
-    if p in (1, 2, 4, 6):
-        w = 5 if p == 6 else p
-        return "spgemm_block_kernel (%d warp%s per row)" % (w, "s" if w > 1 else "")
+    if p in (1, 2, 4, 6, 7):
+        w = {6: 5, 7: 4}.get(p, p)
+        return "spgemm_block_kernel (%d warp%s per row%s)" % (w, "s" if w > 1 else "", ", compact" if p == 7 else "")
+    if p == 8:
+        return "spgemm_super_kernel (one warp per row, two k steps per pass, compact)"
     if p == 5:
         return "spgemm_run_kernel (one warp per row, a run of entries per lane)"
     if p == -1:

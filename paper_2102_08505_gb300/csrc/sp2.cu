@@ -46,7 +46,7 @@ int read_result(Buffers &b, StepResult *h) {
 }
 
 // (Re)allocates m with at least `width` slots and the given dtype; contents undefined.
-bool valid_path(int p) { return p == SP2_PATH_TUNED || (p >= 0 && p <= 6) || (p >= 10 && p <= 12); }
+bool valid_path(int p) { return p == SP2_PATH_TUNED || (p >= 0 && p <= 8) || (p >= 10 && p <= 12); }
 
 int ensure(ellpack_t *m, int n, int width, int dtype, cudaStream_t s) {
   if (m->owner && m->width >= width && m->dtype == dtype) return SP2_OK;
@@ -99,7 +99,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   if (opt.max_iter < 0 || opt.max_iter + opt.n_fp64_tail >= SP2_STATS_CAP)
     return fail(SP2E_ARG, "sp2_purify: max_iter + n_fp64_tail must be < %d", SP2_STATS_CAP);
   if (opt.n_fp64_tail < 0) return fail(SP2E_ARG, "sp2_purify: n_fp64_tail < 0");
-  if (!valid_path(opt.spgemm_path)) return fail(SP2E_ARG, "sp2_purify: spgemm_path must be -1, 0..6 or 10..12");
+  if (!valid_path(opt.spgemm_path)) return fail(SP2E_ARG, "sp2_purify: spgemm_path must be -1, 0..8 or 10..12");
   const int max_w = (opt.max_width > 0 && opt.max_width < n) ? opt.max_width : n;
   if (!(opt.switch_tol >= 0.0) || !isfinite(opt.switch_tol)) return fail(SP2E_ARG, "sp2_purify: bad switch_tol");
   if (opt.sizing < 0 || opt.sizing > 2) return fail(SP2E_ARG, "sp2_purify: sizing must be 0, 1 or 2");
@@ -406,7 +406,7 @@ extern "C" int sp2_step(const ellpack_t *X, ellpack_t *Xn, double nocc, double t
   if (X->idx == Xn->idx || X->val == Xn->val || X->nnz == Xn->nnz) return fail(SP2E_ARG, "sp2_step: Xn aliases X");
   if (!(tau >= 0.0) || !isfinite(tau)) return fail(SP2E_ARG, "sp2_step: tau must be finite and >= 0");
   if (!isfinite(nocc)) return fail(SP2E_ARG, "sp2_step: nocc not finite");
-  if (!valid_path(info->spgemm_path)) return fail(SP2E_ARG, "sp2_step: spgemm_path must be -1, 0..6 or 10..12");
+  if (!valid_path(info->spgemm_path)) return fail(SP2E_ARG, "sp2_step: spgemm_path must be -1, 0..8 or 10..12");
   const int n = X->n;
   Buffers b;
   b.s = as_stream(stream);

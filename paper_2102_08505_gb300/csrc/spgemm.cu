@@ -12,12 +12,12 @@
 //
 // First pass (one of several variants that compute the same product; the tuner or the
 // caller picks one):
-//  - column blocks (paths 1, 2, 4, 6 = 5 warps): a row's output columns are grouped in runs of GW (16
+//  - column blocks (paths 1, 2, 4, 6 = 5 warps, 7 = 4 warps compact): a row's output columns are grouped in runs of GW (16
 //    for FP64, 32 for FP32); a per-row group table in shared memory maps a group to a
 //    block of GW accumulator slots (claimed on first touch), so column j sits in bank
 //    j mod 32.  R warps share a row and split each source row's entries, with a named
 //    barrier between source rows.
-//  - two-step (path 3): one warp per row, two source rows per pass.
+//  - two-step (path 3; 8 = compact): one warp per row, two source rows per pass.
 //  - runs (path 5): one warp per row, each lane takes a run of consecutive entries of a
 //    source row and looks its group up once per change of group.
 //  - hash (paths 10..12): a per-warp open-addressing table of 2^path slots.
@@ -384,22 +384,31 @@ __global__ void __launch_bounds__(HashCfg<T, LOG2T>::WARPS * 32, 1)
 // sentinel when tau == 0 so that "structural" can be told from "zero"), so handing out
 // a block is a single CAS on the table.  The row comes out sorted by walking the groups
 // in ascending order: no sort of the entries is needed.
-template <typename T> struct BlockCfg;
-template <> struct BlockCfg<double> {
+// SZ = 0: blocks for a full product row; SZ = 1 (compact): about half as many, for the
+// upper-triangle rows of symmetric products, so that more rows fit on an SM.
+template <typename T, int SZ = 0> struct BlockCfg;
+template <> struct BlockCfg<double, 0> {
   static constexpr int GSH = 4, NB = 224, LOG2G = 10;
 };
-template <> struct BlockCfg<float> {
+template <> struct BlockCfg<float, 0> {
   static constexpr int GSH = 5, NB = 128, LOG2G = 9;
 };
-template <typename T, int R>
+template <> struct BlockCfg<double, 1> {
+  static constexpr int GSH = 4, NB = 160, LOG2G = 9;
+};
+template <> struct BlockCfg<float, 1> {
+  static constexpr int GSH = 5, NB = 80, LOG2G = 8;
+};
+template <typename T, int R, int SZ = 0>
 struct BlockGeo {
-  static constexpr int GSH = BlockCfg<T>::GSH, GW = 1 << GSH, NB = BlockCfg<T>::NB;
-  static constexpr int G = 1 << BlockCfg<T>::LOG2G;
+  static constexpr int GSH = BlockCfg<T, SZ>::GSH, GW = 1 << GSH, NB = BlockCfg<T, SZ>::NB;
+  static constexpr int LOG2G = BlockCfg<T, SZ>::LOG2G;
+  static constexpr int G = 1 << LOG2G;
   static constexpr int VAL_BYTES = NB * GW * (int)sizeof(T);
   static constexpr int BYTES_PER_GROUP = VAL_BYTES + G * 4 + 16;
   static constexpr int GROUPS_RAW = 232192 / BYTES_PER_GROUP;
   // at most 32 warps per CTA (1024 threads)
-  static constexpr int GROUPS_MAX0 = (sizeof(T) == 4 ? 12 : 16) / (R > 2 ? 2 : 1);
+  static constexpr int GROUPS_MAX0 = (SZ ? (sizeof(T) == 4 ? 20 : 32) : (sizeof(T) == 4 ? 12 : 16)) / (R > 2 ? 2 : 1);
   static constexpr int GROUPS_MAX = GROUPS_MAX0 < 32 / R ? GROUPS_MAX0 : 32 / R;
   static constexpr int GROUPS = GROUPS_RAW > GROUPS_MAX ? GROUPS_MAX : (GROUPS_RAW < 1 ? 1 : GROUPS_RAW);
   static constexpr int WARPS = GROUPS * R;
@@ -437,10 +446,10 @@ __device__ __forceinline__ int probe_block(const unsigned *gtab, unsigned g) {
 // Group -> block, taking a fresh (pre-cleared) block when the group is new.  Lanes of
 // different warps may race for the same group: the CAS keeps the first block, the other
 // one stays unused.  Returns -1 when the blocks are used up.
-template <typename T, int R>
+template <typename T, int R, int SZ = 0>
 __device__ __forceinline__ int group_block(unsigned *gtab, int *nblk, unsigned g) {
-  using Geo = BlockGeo<T, R>;
-  int h = ghash<BlockCfg<T>::LOG2G>(g);
+  using Geo = BlockGeo<T, R, SZ>;
+  int h = ghash<Geo::LOG2G>(g);
 #pragma unroll 1
   for (int p = 0; p < Geo::G; ++p) {
     const unsigned e = ((volatile unsigned *)gtab)[h];
@@ -486,12 +495,12 @@ __device__ __forceinline__ bool group_sync_or(int grp, bool pred) {
   return out != 0;
 }
 
-template <typename T, int R, int QW, bool KEEPZ>
-__global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
+template <typename T, int R, int QW, bool KEEPZ, int SZ>
+__global__ void __launch_bounds__(BlockGeo<T, R, SZ>::WARPS * 32, 1)
     spgemm_block_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
                         int use_add, BatchView bv, Upper up, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
                         int *__restrict__ fb_list, int *__restrict__ fb_count) {
-  using Geo = BlockGeo<T, R>;
+  using Geo = BlockGeo<T, R, SZ>;
   constexpr int GW = Geo::GW, GSH = Geo::GSH, G = Geo::G;
   constexpr int SPAN = 32 * R;  // entries of a B row covered by one register slot of the group
   extern __shared__ __align__(16) unsigned char smem[];
@@ -596,7 +605,7 @@ __global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
         sl[u] = -1;
         const unsigned g = (unsigned)jr[u] >> GSH;
         if ((unsigned)jr[u] < (unsigned)ncol) {
-          const unsigned e = ((volatile unsigned *)gtab)[ghash<BlockCfg<T>::LOG2G>(g)];
+          const unsigned e = ((volatile unsigned *)gtab)[ghash<Geo::LOG2G>(g)];
           if ((e >> 8) == g) sl[u] = (int)(e & 0xFFu) * GW + (jr[u] & (GW - 1));
           else miss |= 1u << u;
         }
@@ -614,7 +623,7 @@ __global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
           const unsigned peers = __match_any_sync(act, g);
           const int leader = __ffs(peers) - 1;
           int b = -1;
-          if (lane == leader) b = g < Geo::MAX_GROUP ? group_block<T, R>(gtab, nblk, g) : -1;
+          if (lane == leader) b = g < Geo::MAX_GROUP ? group_block<T, R, SZ>(gtab, nblk, g) : -1;
           b = __shfl_sync(peers, b, leader);
 #pragma unroll
           for (int w = 0; w < NU; ++w)
@@ -784,12 +793,12 @@ __global__ void __launch_bounds__(BlockGeo<T, R>::WARPS * 32, 1)
 // chains), misses are resolved once, then the S read-modify-write passes run back to
 // back separated only by __syncwarp (consecutive passes may touch the same accumulator).
 // Register slots are predicated instead of specialised, which keeps the code small.
-template <typename T, int QM, int S, bool KEEPZ>
-__global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
+template <typename T, int QM, int S, bool KEEPZ, int SZ>
+__global__ void __launch_bounds__(BlockGeo<T, 1, SZ>::WARPS * 32, 1)
     spgemm_super_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
                         int use_add, BatchView bv, Upper up, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
                         int *__restrict__ fb_list, int *__restrict__ fb_count) {
-  using Geo = BlockGeo<T, 1>;
+  using Geo = BlockGeo<T, 1, SZ>;
   constexpr int GW = Geo::GW, GSH = Geo::GSH, G = Geo::G;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -904,7 +913,7 @@ __global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
           const int j = jc[q][u];
           if ((unsigned)j < (unsigned)ncol) {
             const unsigned g = (unsigned)j >> GSH;
-            const unsigned e = ((volatile unsigned *)gtab)[ghash<BlockCfg<T>::LOG2G>(g)];
+            const unsigned e = ((volatile unsigned *)gtab)[ghash<Geo::LOG2G>(g)];
             if ((e >> 8) == g) sl[q][u] = (int)(e & 0xFFu) * GW + (j & (GW - 1));
             else miss |= 1u << (q * QM + u);
           }
@@ -923,7 +932,7 @@ __global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
           const unsigned peers = __match_any_sync(act, g);
           const int leader = __ffs(peers) - 1;
           int b = -1;
-          if (lane == leader) b = g < Geo::MAX_GROUP ? group_block<T, 1>(gtab, nblk, g) : -1;
+          if (lane == leader) b = g < Geo::MAX_GROUP ? group_block<T, 1, SZ>(gtab, nblk, g) : -1;
           b = __shfl_sync(peers, b, leader);
 #pragma unroll
           for (int q = 0; q < S; ++q)
@@ -954,7 +963,7 @@ __global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
           int slt = -1;
           if ((unsigned)j < (unsigned)ncol) {
             const unsigned g = (unsigned)j >> GSH;
-            const unsigned en = ((volatile unsigned *)gtab)[ghash<BlockCfg<T>::LOG2G>(g)];
+            const unsigned en = ((volatile unsigned *)gtab)[ghash<Geo::LOG2G>(g)];
             if ((en >> 8) == g) slt = (int)(en & 0xFFu) * GW + (j & (GW - 1));
           }
           unsigned tmiss = __ballot_sync(kFull, slt < 0 && (unsigned)j < (unsigned)ncol);
@@ -963,7 +972,7 @@ __global__ void __launch_bounds__(BlockGeo<T, 1>::WARPS * 32, 1)
             const unsigned peers = __match_any_sync(tmiss, g);
             const int leader = __ffs(peers) - 1;
             int b = -1;
-            if (lane == leader) b = g < Geo::MAX_GROUP ? group_block<T, 1>(gtab, nblk, g) : -1;
+            if (lane == leader) b = g < Geo::MAX_GROUP ? group_block<T, 1, SZ>(gtab, nblk, g) : -1;
             b = __shfl_sync(peers, b, leader);
             slt = b < 0 ? -1 : b * GW + (j & (GW - 1));
             if (b < 0) aborted = true;
@@ -1916,10 +1925,10 @@ int launch_hash(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, const i
   return SP2_OK;
 }
 
-template <typename T, int R, int QW, bool KEEPZ>
+template <typename T, int R, int QW, bool KEEPZ, int SZ = 0>
 int launch_block(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
-  using Geo = BlockGeo<T, R>;
-  auto kern = spgemm_block_kernel<T, R, QW, KEEPZ>;
+  using Geo = BlockGeo<T, R, SZ>;
+  auto kern = spgemm_block_kernel<T, R, QW, KEEPZ, SZ>;
   static bool attr_set[64] = {false};
   static int occ_cache[64] = {0};
   int dev = 0;
@@ -1947,10 +1956,10 @@ int launch_block(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
   return SP2_OK;
 }
 
-template <typename T, int QM, int S, bool KEEPZ>
+template <typename T, int QM, int S, bool KEEPZ, int SZ = 0>
 int launch_super(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
-  using Geo = BlockGeo<T, 1>;
-  auto kern = spgemm_super_kernel<T, QM, S, KEEPZ>;
+  using Geo = BlockGeo<T, 1, SZ>;
+  auto kern = spgemm_super_kernel<T, QM, S, KEEPZ, SZ>;
   static bool attr_set[64] = {false};
   static int occ_cache[64] = {0};
   int dev = 0;
@@ -2022,6 +2031,21 @@ int launch_super_auto(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, i
                       : launch_super<T, QM, 2, false>(a, rowstat, ctl, fb, fb_count, s);
 }
 
+// Compact variants for the upper-triangle rows of symmetric products: half the blocks
+// per row and register slots for the shorter source rows, more rows per SM.
+template <typename T>
+int launch_block_compact(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count,
+                         cudaStream_t s) {
+  return a.tau == 0.0 ? launch_block<T, 4, 1, true, 1>(a, rowstat, ctl, fb, fb_count, s)
+                      : launch_block<T, 4, 1, false, 1>(a, rowstat, ctl, fb, fb_count, s);
+}
+template <typename T>
+int launch_super_compact(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count,
+                         cudaStream_t s) {
+  return a.tau == 0.0 ? launch_super<T, 3, 2, true, 1>(a, rowstat, ctl, fb, fb_count, s)
+                      : launch_super<T, 3, 2, false, 1>(a, rowstat, ctl, fb, fb_count, s);
+}
+
 // Block first pass with R warps per row; the register slots per warp cover the width of B.
 template <typename T, int R>
 int launch_block_r(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
@@ -2071,6 +2095,8 @@ int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
     case 2: rc = launch_block_r<T, 2>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 3: rc = launch_super_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 5: rc = launch_run_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
+    case 7: rc = launch_block_compact<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
+    case 8: rc = launch_super_compact<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     default:  // automatic: the variant measured fastest on the 3D tight-binding products
               // (FP64: 4 warps per row; FP32: one warp per row, two k steps per pass)
       rc = sizeof(T) == 8 ? launch_block_r<T, 4>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)

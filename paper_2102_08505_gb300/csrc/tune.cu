@@ -22,7 +22,7 @@
 namespace sp2 {
 namespace {
 
-constexpr int kCandidates[] = {1, 2, 4, 6, 3, 5, 10, 11, 12};
+constexpr int kCandidates[] = {1, 2, 4, 6, 7, 3, 8, 5, 10, 11, 12};
 constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
 static_assert(kNumCandidates == SP2_TUNE_CANDIDATES, "candidate count");
 

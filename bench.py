@@ -660,7 +660,9 @@ def run_sizing(a):
     """Output sizing of the SP2 products: heuristic widths with regrow, exact structural
     counts before every multiply, and the row-length MLP (trained on about 50k rows of
     SP2 products of gapped 3D Hamiltonians of 4096 .. 16384 sites), each used for a mixed
-    precision SP2 run on a gapped 3D tight-binding H of N=1048576 sites (input width 128)."""
+    precision SP2 run on a gapped 3D tight-binding H of N=1048576 sites (input width 128);
+    beside them plain FP64 SP2 with heuristic widths, the form the others are measured
+    against."""
     import torch
     from paper_2102_08505_gb300 import inputs as I
     from paper_2102_08505_gb300 import learned
@@ -683,8 +685,9 @@ def run_sizing(a):
     pad_v[:, :idx.shape[1]] = val
     H = S.Ellpack.from_numpy(pad_i, pad_v, nnz)
     res, Ds = {}, {}
-    for mode, name in ((2, "mlp"), (1, "structural"), (0, "heuristic")):
-        kw = dict(tau=tau, precision=S.SP2_PREC_MIXED, sizing=mode, spgemm_path=a.path)
+    for mode, name, prec in ((2, "mlp", S.SP2_PREC_MIXED), (1, "structural", S.SP2_PREC_MIXED),
+                             (0, "heuristic", S.SP2_PREC_MIXED), (0, "plain_f64", S.SP2_PREC_F64)):
+        kw = dict(tau=tau, precision=prec, sizing=mode, spgemm_path=a.path)
         if mode == 2:
             kw["predictor"] = pred
         opt = S.sp2_options_default(**kw)
@@ -714,7 +717,9 @@ def run_sizing(a):
             "training": {"rows": int(counts.shape[0]), "collect_s": t_collect, "train_s": t_train,
                          "final_batch_loss": loss},
             **res,
-            **{"dD_%s_vs_mlp" % k: diff_fro(S, Ds[k], Ds["mlp"]) / np.sqrt(n) for k in Ds if k != "mlp" and "mlp" in Ds}}
+            **{"dD_%s_vs_mlp" % k: diff_fro(S, Ds[k], Ds["mlp"]) / np.sqrt(n) for k in Ds if k != "mlp" and "mlp" in Ds},
+            **({"speedup_mixed_mlp_vs_plain_f64": res["plain_f64"]["time_s"] / res["mlp"]["time_s"]}
+               if "time_s" in res.get("plain_f64", {}) and "time_s" in res.get("mlp", {}) else {})}
     print(json.dumps(line), flush=True)
 
 

@@ -246,7 +246,7 @@ def spgemm_kernel_name(a):
     """The first-pass SpGEMM kernel that the chosen path launches."""
     p = a.path
     if p == 0:
-        p = 4 if a.dtype == "f64" else 3
+        p = (7 if a.dtype == "f64" else 8) if a.symmetric else (4 if a.dtype == "f64" else 3)
     if p in (1, 2, 4, 6, 7):
         w = {6: 5, 7: 4}.get(p, p)
         return "spgemm_block_kernel (%d warp%s per row%s)" % (w, "s" if w > 1 else "", ", compact" if p == 7 else "")
@@ -381,7 +381,7 @@ def run_ours(a):
                  _t.empty(a.n, dtype=_t.int32).pin_memory()) for _ in range(2)]
         Xins = [S.Ellpack.empty(a.n, w1, DT) for _ in range(2)]
         Xouts = [X2, S.Ellpack.empty(a.n, w2, DT)]
-        streams = [stream, torch.cuda.Stream(device=dev)]
+        streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]  # not the legacy stream
 
         def upload(t):
             b = t % 2

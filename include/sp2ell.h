@@ -358,7 +358,8 @@ typedef struct sp2_options {
   int32_t n_fp64_tail;  /* MIXED: minimum FP64 iterations after the switch (default 2) */
   int32_t max_width;    /* cap on the working width (0 = n); SP2E_OVERFLOW beyond it */
   int32_t spgemm_path;  /* SpGEMM first pass: 0 automatic (column blocks; F64: 4 warps
-                           per row, F32: path 3); 1, 2, 4 = column-block accumulator
+                           per row, F32: path 3; their compact forms 7 and 8 for
+                           symmetric products); 1, 2, 4 = column-block accumulator
                            shared by that many warps per row (6: by 5; 7: 4, compact); 3 = column blocks, one
                            warp per row, two k steps per pass (8: compact); 5 = column blocks, one
                            warp per row, chunk stream prefetched 8 chunks ahead; 10..12 =

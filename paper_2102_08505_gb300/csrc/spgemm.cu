@@ -2098,9 +2098,14 @@ int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
     case 7: rc = launch_block_compact<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 8: rc = launch_super_compact<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     default:  // automatic: the variant measured fastest on the 3D tight-binding products
-              // (FP64: 4 warps per row; FP32: one warp per row, two k steps per pass)
-      rc = sizeof(T) == 8 ? launch_block_r<T, 4>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
-                          : launch_super_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s);
+              // (FP64: 4 warps per row; FP32: one warp per row, two k steps per pass), in
+              // its compact form for the upper triangle of a symmetric product
+      if (a.up.tp)
+        rc = sizeof(T) == 8 ? launch_block_compact<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
+                            : launch_super_compact<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s);
+      else
+        rc = sizeof(T) == 8 ? launch_block_r<T, 4>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
+                            : launch_super_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s);
       break;
   }
   // deferred rows: a dense window per CTA when the row's span fits it, then the 2^14-slot

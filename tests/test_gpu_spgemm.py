@@ -286,7 +286,8 @@ def test_first_pass_variants(gpu, first_pass, fp32):
     info = S.sp2_step(d1, out, n / 2, 1e-5, spgemm_path=first_pass)
     up = info.branch == 2
     compare_spgemm(out.to_numpy(), X1, X1, X1, -1.0 if up else 1.0, 2.0 if up else 0.0, 1e-5, fp32=fp32)
-    assert info.rows_deferred == 0
+    if first_pass not in (7, 8):  # the compact variants hold half a full row's blocks: long rows defer
+        assert info.rows_deferred == 0
     again = S.Ellpack.empty(n, out.width, dt)
     S.sp2_step(d1, again, n / 2, 1e-5, spgemm_path=first_pass)
     for a, b in zip(out.to_numpy(), again.to_numpy()):

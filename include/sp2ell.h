@@ -262,6 +262,14 @@ int nnzpred_train(nnzpred_t *p, const float *feat, const int32_t *count, int64_t
 /* Predicted row lengths pred[n] (device float) from feat[n*16].  Asynchronous. */
 int nnzpred_predict(const nnzpred_t *p, const float *feat, int64_t n, float *pred, void *stream);
 
+/* Output width for the product the SP2 step with `branch` and `tau` computes from X:
+ * the features of X, the predicted row lengths (into pred, device float[n], optional),
+ * and *width (host) = ceil(1.1 x the longest prediction) + 16 rounded up to 32 and capped
+ * at n -- the rule sp2_purify uses with sizing 2.  Synchronises `stream`.
+ * Errors: SP2E_ARG, SP2E_NOMEM, SP2E_CUDA. */
+int nnzpred_width(const nnzpred_t *p, const ellpack_t *X, double tau, int32_t branch, int32_t *width, float *pred,
+                  void *stream);
+
 /* Weights and statistics to / from a file. */
 int nnzpred_save(const nnzpred_t *p, const char *path, void *stream);
 int nnzpred_load(nnzpred_t *p, const char *path, void *stream);

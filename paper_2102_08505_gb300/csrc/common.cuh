@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <cstddef>
@@ -196,6 +197,8 @@ int predict_async(const nnzpred_t *p, const float *feat, long long n, float *pre
 constexpr int kPredErrDoubles = 2 + 2 * 256;
 int pred_error_async(const float *pred, const int *actual, long long n, double *out2, cudaStream_t s);
 int max_float_async(const float *v, long long n, float *out, cudaStream_t s);
+// Output width from the predictor's longest row: 10 % and 16 slots of margin.
+inline long long predicted_width(float max_pred) { return (long long)ceil(1.10 * (double)max_pred) + 16; }
 
 // Autotuner (tune.cu): mean stored row length of X (synchronises); the table entry for
 // the class of a multiply (false if absent); timing every first-pass variant on the

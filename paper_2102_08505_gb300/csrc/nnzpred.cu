@@ -700,6 +700,35 @@ extern "C" int nnzpred_predict(const nnzpred_t *p, const float *feat, int64_t n,
   return predict_async(p, feat, n, pred, as_stream(stream));
 }
 
+extern "C" int nnzpred_width(const nnzpred_t *p, const ellpack_t *X, double tau, int32_t branch, int32_t *width,
+                             float *pred, void *stream) {
+  SP2_TRY(check_pred(p, "nnzpred_width"));
+  SP2_TRY(check_matrix(X, "nnzpred_width: X"));
+  if (!width) return fail(SP2E_ARG, "nnzpred_width: width is NULL");
+  if (!(tau >= 0.0) || !isfinite(tau)) return fail(SP2E_ARG, "nnzpred_width: bad tau");
+  cudaStream_t s = as_stream(stream);
+  const size_t n = (size_t)X->n;
+  float *scr = nullptr;  // rmax[n], feat[16n], pred[n] (unless given), max
+  SP2_TRY(dev_alloc((void **)&scr, sizeof(float) * (18 * n + 1), s));
+  float *rmax = scr, *feat = scr + n, *pr = pred ? pred : scr + 17 * n, *fmax = scr + 18 * n;
+  int rc = features_async(X, tau, branch, rmax, feat, s);
+  if (rc == SP2_OK) rc = predict_async(p, feat, (long long)n, pr, s);
+  if (rc == SP2_OK) rc = max_float_async(pr, (long long)n, fmax, s);
+  float h = 0.f;
+  if (rc == SP2_OK) {
+    cudaError_t e = cudaMemcpyAsync(&h, fmax, sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "nnzpred_width", __FILE__, __LINE__);
+  }
+  dev_free(scr, s);
+  SP2_TRY(rc);
+  long long w = ((predicted_width(h) + 31) / 32) * 32;
+  if (w > X->n) w = X->n;
+  if (w < 1) w = 1;
+  *width = (int32_t)w;
+  return SP2_OK;
+}
+
 extern "C" int nnzpred_save(const nnzpred_t *p, const char *path, void *stream) {
   SP2_TRY(check_pred(p, "nnzpred_save"));
   if (!path) return fail(SP2E_ARG, "nnzpred_save: path is NULL");

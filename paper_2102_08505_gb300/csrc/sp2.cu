@@ -283,7 +283,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
       float fm = 0.f;
       SP2_CUDA(cudaMemcpyAsync(&fm, sz_fmax, sizeof(float), cudaMemcpyDeviceToHost, s));
       SP2_CUDA(cudaStreamSynchronize(s));
-      guess = (long long)ceil(1.10 * (double)fm) + 16;
+      guess = predicted_width(fm);
     }
     int width = round_up((int)(guess < max_w ? guess : max_w), 32);
     if (width > n) width = n;

@@ -119,6 +119,7 @@ def _load():
         "nnzpred_train": ([P(nnzpred_t), V, V, ctypes.c_int64, I, I, ctypes.c_float, P(ctypes.c_float), V],
                           ctypes.c_int),
         "nnzpred_predict": ([P(nnzpred_t), V, ctypes.c_int64, V, V], ctypes.c_int),
+        "nnzpred_width": ([P(nnzpred_t), E, D, I, P(I), V, V], ctypes.c_int),
         "nnzpred_save": ([P(nnzpred_t), ctypes.c_char_p, V], ctypes.c_int),
         "nnzpred_load": ([P(nnzpred_t), ctypes.c_char_p, V], ctypes.c_int),
         "sp2_profile_start": ([], ctypes.c_int),
@@ -480,6 +481,15 @@ class NnzPredictor:
         _check(lib.nnzpred_predict(ctypes.byref(self.desc), feat.data_ptr(), feat.shape[0], pred.data_ptr(),
                                    _stream(stream)))
         return pred
+
+    def width(self, X, tau, branch, stream=None):
+        """(output width for the SP2 product of X, predicted row lengths [n])."""
+        import torch
+        pred = torch.empty(X.n, dtype=torch.float32, device="cuda")
+        w = ctypes.c_int32()
+        _check(lib.nnzpred_width(ctypes.byref(self.desc), _d(X), float(tau), int(branch), ctypes.byref(w),
+                                 pred.data_ptr(), _stream(stream)))
+        return w.value, pred
 
     def params(self):
         """(weights float32[NNZPRED_NPARAMS], statistics float32[NNZPRED_NSTATS]) on the host,

@@ -185,3 +185,25 @@ def test_sizing_errors(gpu):
     with pytest.raises(S.Sp2Error) as e:
         S.sp2_purify(_dev(S, H), 32, 1e-10, S.sp2_options_default(sizing=3))
     assert e.value.code == S.SP2E_ARG
+
+
+def test_predicted_width_rule(gpu, trainset):
+    """nnzpred_width: the predictions from the features of X, and the width rule
+    ceil(1.1 x longest) + 16 rounded up to 32."""
+    S = gpu
+    feat, counts = trainset
+    p = S.NnzPredictor(seed=4)
+    p.set_stats(feat, counts)
+    p.train(feat, counts, 300, 1024, 2e-3)
+    X = _dev(S, _x0(4096, 23))
+    w, pred = p.width(X, 1e-5, 2)
+    ref = p.predict(S.nnzpred_features(X, 1e-5, 2))
+    assert torch_equal(pred, ref)
+    m = float(ref.max().item())
+    expect = min(4096, ((int(np.ceil(1.10 * m)) + 16 + 31) // 32) * 32)
+    assert w == expect
+
+
+def torch_equal(a, b):
+    import torch
+    return torch.equal(a, b)

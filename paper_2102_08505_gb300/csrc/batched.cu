@@ -567,6 +567,7 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
         if (tune_find(cur->dtype, ntot, mean, path)) return SP2_OK;
         MultiplyArgs a{cur, cur, nullptr, nxt, 1.0, 0.0, opt.tau, 0};
         a.sym = opt.symmetric != 0;
+        a.no_compact = true;  // captured once: no feedback on deferred rows, so the full-row variants
         a.sym_prealloc = d_sym;
         a.sym_prealloc_bytes = sym_bytes;
         SP2_TRY(tune_multiply(a, mean, d_rowstat, c, 2, path, nullptr, s));
@@ -590,6 +591,7 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
         a.bv = bv32;
         a.fb_prealloc = d_fb;
         a.sym = opt.symmetric != 0;
+        a.no_compact = true;  // captured once: no feedback on deferred rows, so the full-row variants
         a.sym_prealloc = d_sym;
         a.sym_prealloc_bytes = sym_bytes;
         SP2_TRY(multiply_async(a, d_rowstat, d_c32, s));
@@ -599,6 +601,7 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
         a.bv = bv64;
         a.fb_prealloc = d_fb;
         a.sym = opt.symmetric != 0;
+        a.no_compact = true;  // captured once: no feedback on deferred rows, so the full-row variants
         a.sym_prealloc = d_sym;
         a.sym_prealloc_bytes = sym_bytes;
         SP2_TRY(multiply_async(a, d_rowstat, d_c64, s));

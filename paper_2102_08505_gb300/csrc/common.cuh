@@ -144,6 +144,7 @@ struct MultiplyArgs {
   // X*X (+ X) with X symmetric (A == B, Add null or A): compute the upper triangle and
   // mirror it (bitwise the same result as full rows, about half the products)
   bool sym = false;
+  bool no_compact = false;  // path 0 of a symmetric product: keep the full-row variants
   void *sym_prealloc = nullptr;  // scratch of the symmetric product (null: allocated per call)
   size_t sym_prealloc_bytes = 0;
   Upper up{};  // set internally for the upper-triangle pass

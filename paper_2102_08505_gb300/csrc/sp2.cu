@@ -210,6 +210,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   } stats_on_exit{stats, &st, &it};
   int status = 0;  // set when the loop stops: 0 err < tol, 1 stall rule, 2 max_iter
   int last_count = res.max_nnz;
+  bool compact_ok = true;
   for (;;) {
     if (res.nonfinite) return fail(SP2E_NONFINITE, "sp2_purify: non-finite trace at iteration %d", it);
     const double trX = res.tr, trX2 = res.fro;
@@ -301,6 +302,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
       SP2_TRY(ensure(&b.Y, n, width, b.X.dtype, s));
       MultiplyArgs a{&b.X, &b.X, beta != 0.0 ? &b.X : nullptr, &b.Y, alpha, beta, opt.tau, lg};
       a.sym = opt.symmetric != 0;
+      a.no_compact = !compact_ok;
       SP2_TRY(multiply_async(a, b.rowstat, b.ctl, s));
       launch_reduce_rows(b.rowstat, b.Y.nnz, n, b.ctl, b.dres, s);
       SP2_CUDA(cudaGetLastError());
@@ -339,6 +341,9 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
       rows_seen += (double)n;
     }
     last_count = res.max_count;
+    // the compact first pass (automatic for symmetric products) holds half a row's blocks:
+    // once it defers more than 0.2 % of the rows, the full-row variants take over for the run
+    if (compact_ok && opt.symmetric && lg == 0 && res.n_fallback > n / 500) compact_ok = false;
     ellpack_t t = b.X; b.X = b.Y; b.Y = t;
     ++it;
   }

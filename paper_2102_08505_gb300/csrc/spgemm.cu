@@ -394,10 +394,10 @@ template <> struct BlockCfg<float, 0> {
   static constexpr int GSH = 5, NB = 128, LOG2G = 9;
 };
 template <> struct BlockCfg<double, 1> {
-  static constexpr int GSH = 4, NB = 160, LOG2G = 9;
+  static constexpr int GSH = 4, NB = 192, LOG2G = 9;
 };
 template <> struct BlockCfg<float, 1> {
-  static constexpr int GSH = 5, NB = 80, LOG2G = 8;
+  static constexpr int GSH = 5, NB = 112, LOG2G = 9;
 };
 template <typename T, int R, int SZ = 0>
 struct BlockGeo {
@@ -2100,7 +2100,7 @@ int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
     default:  // automatic: the variant measured fastest on the 3D tight-binding products
               // (FP64: 4 warps per row; FP32: one warp per row, two k steps per pass), in
               // its compact form for the upper triangle of a symmetric product
-      if (a.up.tp)
+      if (a.up.tp && !a.no_compact)
         rc = sizeof(T) == 8 ? launch_block_compact<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
                             : launch_super_compact<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s);
       else

@@ -49,8 +49,8 @@ def parse():
                         "model Hamiltonians at N=32000; schedule: stall-rule and precision-schedule variants")
     p.add_argument("--count", type=int, default=256)
     p.add_argument("--path", type=int, default=0,
-                   help="SpGEMM first pass: 0 automatic, 1/2/4/6 column blocks with 1/2/4/5 warps per row, 3 two-step, "
-                        "5 runs, 10-12 hash, -1 tuned")
+                   help="SpGEMM first pass: 0 automatic, 1/2/4 column blocks with 1/2/4 warps per row, 3 two-step, "
+                        "7/8 compact forms of 4/3, 10-12 hash, -1 tuned")
     p.add_argument("--full-rows", dest="symmetric", action="store_false",
                    help="SP2 steps compute full product rows instead of the upper triangle of the "
                         "symmetric product mirrored (the default)")
@@ -247,13 +247,11 @@ def spgemm_kernel_name(a):
     p = a.path
     if p == 0:
         p = (7 if a.dtype == "f64" else 8) if a.symmetric else (4 if a.dtype == "f64" else 3)
-    if p in (1, 2, 4, 6, 7):
-        w = {6: 5, 7: 4}.get(p, p)
+    if p in (1, 2, 4, 7):
+        w = 4 if p == 7 else p
         return "spgemm_block_kernel (%d warp%s per row%s)" % (w, "s" if w > 1 else "", ", compact" if p == 7 else "")
     if p == 8:
         return "spgemm_super_kernel (one warp per row, two k steps per pass, compact)"
-    if p == 5:
-        return "spgemm_run_kernel (one warp per row, a run of entries per lane)"
     if p == -1:
         return "tuned first pass"
     if p == 3:

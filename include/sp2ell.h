@@ -314,10 +314,10 @@ int ellpack_from_dense(const void *dense, int64_t ld, double tau, ellpack_t *A, 
 /* ---------------------------------------------------------------- autotuner */
 /*
  * The SpGEMM first pass has several variants that compute the same product (spgemm_path
- * 1, 2, 4, 6: column-block accumulator shared by 1, 2, 4, 5 warps per row (7: 4 warps, half
- * the blocks per row, for the upper triangles of symmetric products); 3: one warp per
- * row, two k steps per pass (8: compact, as 7); 5: one warp per row, the row's gather as one chunk stream
- * prefetched 8 chunks ahead; 10..12: per-warp hash table of 2^path slots).  The tuner
+ * 1, 2, 4: column-block accumulator shared by that many warps per row (7: 4 warps, about
+ * half the blocks per row, for the upper triangles of symmetric products); 3: one warp per
+ * row, two k steps per pass (8: compact, as 7); 10..12: per-warp hash table of 2^path
+ * slots).  The tuner
  * times them on a real product and keeps the fastest per class (SM count, dtype,
  * floor(log2 n), floor(log2 mean stored row length of A)) in a process-wide host table
  * (thread-safe).  sp2_purify, sp2_step and sp2_purify_batched use the table when
@@ -325,7 +325,7 @@ int ellpack_from_dense(const void *dense, int64_t ld, double tau, ellpack_t *A, 
  * counterpart.
  */
 #define SP2_PATH_TUNED (-1)
-#define SP2_TUNE_CANDIDATES 11  /* 1, 2, 4, 6, 7, 3, 8, 5, 10, 11, 12 in this order */
+#define SP2_TUNE_CANDIDATES 9  /* 1, 2, 4, 7, 3, 8, 10, 11, 12 in this order */
 
 /* Times every variant on Out <- drop_tau(alpha A*B + beta C) (C may be NULL): one untimed
  * and `reps` timed runs each (CUDA events on `stream`); records the fastest for A's class
@@ -368,10 +368,9 @@ typedef struct sp2_options {
   int32_t spgemm_path;  /* SpGEMM first pass: 0 automatic (column blocks; F64: 4 warps
                            per row, F32: path 3; their compact forms 7 and 8 for
                            symmetric products); 1, 2, 4 = column-block accumulator
-                           shared by that many warps per row (6: by 5; 7: 4, compact); 3 = column blocks, one
-                           warp per row, two k steps per pass (8: compact); 5 = column blocks, one
-                           warp per row, chunk stream prefetched 8 chunks ahead; 10..12 =
-                           per-warp hash table of 2^k slots; SP2_PATH_TUNED = the
+                           shared by that many warps per row (7: 4, compact); 3 = column
+                           blocks, one warp per row, two k steps per pass (8: compact);
+                           10..12 = per-warp hash table of 2^k slots; SP2_PATH_TUNED = the
                            autotuner's choice */
   double tau;           /* drop tolerance (default 1e-5) */
   double switch_tol;    /* MIXED: leave the FP32 loop once err_n < switch_tol (0 = automatic:

@@ -385,9 +385,9 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
     return fail(SP2E_ARG, "sp2_purify_batched: unknown precision %d", opt.precision);
   if (opt.max_iter < 0 || opt.max_iter + opt.n_fp64_tail >= SP2_STATS_CAP || opt.n_fp64_tail < 0)
     return fail(SP2E_ARG, "sp2_purify_batched: bad max_iter / n_fp64_tail");
-  if (!(opt.spgemm_path == SP2_PATH_TUNED || (opt.spgemm_path >= 0 && opt.spgemm_path <= 8) ||
-        (opt.spgemm_path >= 10 && opt.spgemm_path <= 12)))
-    return fail(SP2E_ARG, "sp2_purify_batched: spgemm_path must be -1, 0..8 or 10..12");
+  if (!(opt.spgemm_path == SP2_PATH_TUNED || (opt.spgemm_path >= 0 && opt.spgemm_path <= 4) || opt.spgemm_path == 7 ||
+        opt.spgemm_path == 8 || (opt.spgemm_path >= 10 && opt.spgemm_path <= 12)))
+    return fail(SP2E_ARG, "sp2_purify_batched: spgemm_path must be -1, 0..4, 7, 8 or 10..12");
   if (!(opt.stall_arm > 0.0) || !isfinite(opt.stall_arm))
     return fail(SP2E_ARG, "sp2_purify_batched: stall_arm must be > 0");
   long long ntot_ll = 0;
@@ -567,7 +567,7 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
         if (tune_find(cur->dtype, ntot, mean, path)) return SP2_OK;
         MultiplyArgs a{cur, cur, nullptr, nxt, 1.0, 0.0, opt.tau, 0};
         a.sym = opt.symmetric != 0;
-        a.no_compact = true;  // captured once: no feedback on deferred rows, so the full-row variants
+        a.compact_level = 1;  // captured once, without feedback on deferred rows: the loose compact variants
         a.sym_prealloc = d_sym;
         a.sym_prealloc_bytes = sym_bytes;
         SP2_TRY(tune_multiply(a, mean, d_rowstat, c, 2, path, nullptr, s));
@@ -591,7 +591,7 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
         a.bv = bv32;
         a.fb_prealloc = d_fb;
         a.sym = opt.symmetric != 0;
-        a.no_compact = true;  // captured once: no feedback on deferred rows, so the full-row variants
+        a.compact_level = 1;  // captured once, without feedback on deferred rows: the loose compact variants
         a.sym_prealloc = d_sym;
         a.sym_prealloc_bytes = sym_bytes;
         SP2_TRY(multiply_async(a, d_rowstat, d_c32, s));
@@ -601,7 +601,7 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
         a.bv = bv64;
         a.fb_prealloc = d_fb;
         a.sym = opt.symmetric != 0;
-        a.no_compact = true;  // captured once: no feedback on deferred rows, so the full-row variants
+        a.compact_level = 1;  // captured once, without feedback on deferred rows: the loose compact variants
         a.sym_prealloc = d_sym;
         a.sym_prealloc_bytes = sym_bytes;
         SP2_TRY(multiply_async(a, d_rowstat, d_c64, s));

@@ -144,7 +144,9 @@ struct MultiplyArgs {
   // X*X (+ X) with X symmetric (A == B, Add null or A): compute the upper triangle and
   // mirror it (bitwise the same result as full rows, about half the products)
   bool sym = false;
-  bool no_compact = false;  // path 0 of a symmetric product: keep the full-row variants
+  // path 0 of a symmetric product: 0 the tight compact variant, 1 the loose one, 2 the
+  // full-row variants
+  int compact_level = 0;
   void *sym_prealloc = nullptr;  // scratch of the symmetric product (null: allocated per call)
   size_t sym_prealloc_bytes = 0;
   Upper up{};  // set internally for the upper-triangle pass

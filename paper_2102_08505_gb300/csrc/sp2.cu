@@ -46,7 +46,7 @@ int read_result(Buffers &b, StepResult *h) {
 }
 
 // (Re)allocates m with at least `width` slots and the given dtype; contents undefined.
-bool valid_path(int p) { return p == SP2_PATH_TUNED || (p >= 0 && p <= 8) || (p >= 10 && p <= 12); }
+bool valid_path(int p) { return p == SP2_PATH_TUNED || (p >= 0 && p <= 4) || p == 7 || p == 8 || (p >= 10 && p <= 12); }
 
 int ensure(ellpack_t *m, int n, int width, int dtype, cudaStream_t s) {
   if (m->owner && m->width >= width && m->dtype == dtype) return SP2_OK;
@@ -99,7 +99,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   if (opt.max_iter < 0 || opt.max_iter + opt.n_fp64_tail >= SP2_STATS_CAP)
     return fail(SP2E_ARG, "sp2_purify: max_iter + n_fp64_tail must be < %d", SP2_STATS_CAP);
   if (opt.n_fp64_tail < 0) return fail(SP2E_ARG, "sp2_purify: n_fp64_tail < 0");
-  if (!valid_path(opt.spgemm_path)) return fail(SP2E_ARG, "sp2_purify: spgemm_path must be -1, 0..8 or 10..12");
+  if (!valid_path(opt.spgemm_path)) return fail(SP2E_ARG, "sp2_purify: spgemm_path must be -1, 0..4, 7, 8 or 10..12");
   const int max_w = (opt.max_width > 0 && opt.max_width < n) ? opt.max_width : n;
   if (!(opt.switch_tol >= 0.0) || !isfinite(opt.switch_tol)) return fail(SP2E_ARG, "sp2_purify: bad switch_tol");
   if (opt.sizing < 0 || opt.sizing > 2) return fail(SP2E_ARG, "sp2_purify: sizing must be 0, 1 or 2");
@@ -210,7 +210,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   } stats_on_exit{stats, &st, &it};
   int status = 0;  // set when the loop stops: 0 err < tol, 1 stall rule, 2 max_iter
   int last_count = res.max_nnz;
-  bool compact_ok = true;
+  int compact_level = 0;
   for (;;) {
     if (res.nonfinite) return fail(SP2E_NONFINITE, "sp2_purify: non-finite trace at iteration %d", it);
     const double trX = res.tr, trX2 = res.fro;
@@ -302,7 +302,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
       SP2_TRY(ensure(&b.Y, n, width, b.X.dtype, s));
       MultiplyArgs a{&b.X, &b.X, beta != 0.0 ? &b.X : nullptr, &b.Y, alpha, beta, opt.tau, lg};
       a.sym = opt.symmetric != 0;
-      a.no_compact = !compact_ok;
+      a.compact_level = compact_level;
       SP2_TRY(multiply_async(a, b.rowstat, b.ctl, s));
       launch_reduce_rows(b.rowstat, b.Y.nnz, n, b.ctl, b.dres, s);
       SP2_CUDA(cudaGetLastError());
@@ -341,9 +341,10 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
       rows_seen += (double)n;
     }
     last_count = res.max_count;
-    // the compact first pass (automatic for symmetric products) holds half a row's blocks:
-    // once it defers more than 0.2 % of the rows, the full-row variants take over for the run
-    if (compact_ok && opt.symmetric && lg == 0 && res.n_fallback > n / 500) compact_ok = false;
+    // the compact first passes (automatic for symmetric products) hold fewer blocks per row:
+    // once one defers more than 0.2 % of the rows, the next larger variant takes over for the
+    // rest of the run (tight -> loose -> full rows)
+    if (compact_level < 2 && opt.symmetric && lg == 0 && res.n_fallback > n / 500) ++compact_level;
     ellpack_t t = b.X; b.X = b.Y; b.Y = t;
     ++it;
   }
@@ -411,7 +412,7 @@ extern "C" int sp2_step(const ellpack_t *X, ellpack_t *Xn, double nocc, double t
   if (X->idx == Xn->idx || X->val == Xn->val || X->nnz == Xn->nnz) return fail(SP2E_ARG, "sp2_step: Xn aliases X");
   if (!(tau >= 0.0) || !isfinite(tau)) return fail(SP2E_ARG, "sp2_step: tau must be finite and >= 0");
   if (!isfinite(nocc)) return fail(SP2E_ARG, "sp2_step: nocc not finite");
-  if (!valid_path(info->spgemm_path)) return fail(SP2E_ARG, "sp2_step: spgemm_path must be -1, 0..8 or 10..12");
+  if (!valid_path(info->spgemm_path)) return fail(SP2E_ARG, "sp2_step: spgemm_path must be -1, 0..4, 7, 8 or 10..12");
   const int n = X->n;
   Buffers b;
   b.s = as_stream(stream);

@@ -12,14 +12,12 @@
 //
 // First pass (one of several variants that compute the same product; the tuner or the
 // caller picks one):
-//  - column blocks (paths 1, 2, 4, 6 = 5 warps, 7 = 4 warps compact): a row's output columns are grouped in runs of GW (16
+//  - column blocks (paths 1, 2, 4; 7 = 4 warps, compact): a row's output columns are grouped in runs of GW (16
 //    for FP64, 32 for FP32); a per-row group table in shared memory maps a group to a
 //    block of GW accumulator slots (claimed on first touch), so column j sits in bank
 //    j mod 32.  R warps share a row and split each source row's entries, with a named
 //    barrier between source rows.
 //  - two-step (path 3; 8 = compact): one warp per row, two source rows per pass.
-//  - runs (path 5): one warp per row, each lane takes a run of consecutive entries of a
-//    source row and looks its group up once per change of group.
 //  - hash (paths 10..12): a per-warp open-addressing table of 2^path slots.
 // Rows whose groups outgrow the table are deferred to a one-warp 2^14-slot hash table
 // (bin 1), and rows beyond that to a dense global-memory row per CTA (bin 2), so no row
@@ -394,9 +392,16 @@ template <> struct BlockCfg<float, 0> {
   static constexpr int GSH = 5, NB = 128, LOG2G = 9;
 };
 template <> struct BlockCfg<double, 1> {
-  static constexpr int GSH = 4, NB = 192, LOG2G = 9;
+  static constexpr int GSH = 4, NB = 160, LOG2G = 9;
 };
 template <> struct BlockCfg<float, 1> {
+  static constexpr int GSH = 5, NB = 80, LOG2G = 8;
+};
+// SZ = 2: between the two, for the denser products of converging SP2 iterations
+template <> struct BlockCfg<double, 2> {
+  static constexpr int GSH = 4, NB = 192, LOG2G = 9;
+};
+template <> struct BlockCfg<float, 2> {
   static constexpr int GSH = 5, NB = 112, LOG2G = 9;
 };
 template <typename T, int R, int SZ = 0>
@@ -427,21 +432,6 @@ template <> __device__ __forceinline__ float untouched<float>() { return __uint_
 
 template <int LOG2G>
 __device__ __forceinline__ int ghash(unsigned g) { return (int)((g * 0x9E3779B1u) >> (32 - LOG2G)); }
-
-// Block of group g, or -1 when g is not in the table (probes until a hit or an empty
-// entry; a probe longer than 16 also answers -1 and the slow path finds the group).
-template <int LOG2G>
-__device__ __forceinline__ int probe_block(const unsigned *gtab, unsigned g) {
-  int h = ghash<LOG2G>(g);
-#pragma unroll 1
-  for (int p = 0; p < 16; ++p) {
-    const unsigned e = ((const volatile unsigned *)gtab)[h];
-    if ((e >> 8) == g) return (int)(e & 0xFFu);
-    if (e == 0xFFFFFFFFu) return -1;
-    h = (h + 1) & ((1 << LOG2G) - 1);
-  }
-  return -1;
-}
 
 // Group -> block, taking a fresh (pre-cleared) block when the group is new.  Lanes of
 // different warps may race for the same group: the CAS keeps the first block, the other
@@ -1002,319 +992,6 @@ __global__ void __launch_bounds__(BlockGeo<T, 1, SZ>::WARPS * 32, 1)
       continue;
     }
     // epilogue: groups in order, lane -> column (as in the block kernel)
-    int ng = 0;
-    for (int c = 0; c < G; c += 32) {
-      const unsigned e = gtab[c + lane];
-      const bool used = e != 0xFFFFFFFFu;
-      const unsigned m = __ballot_sync(kFull, used);
-      __syncwarp();
-      if (used) gtab[ng + __popc(m & lt)] = e;
-      ng += __popc(m);
-    }
-    {
-      int P = 32;
-      while (P < ng) P <<= 1;
-      for (int s2 = ng + lane; s2 < P; s2 += 32) gtab[s2] = 0xFFFFFFFFu;
-      __syncwarp();
-      for (int k = 2; k <= P; k <<= 1)
-        for (int jj = k >> 1; jj > 0; jj >>= 1) {
-          for (int e = lane; e < (P >> 1); e += 32) {
-            const int i = ((e & ~(jj - 1)) << 1) | (e & (jj - 1));
-            const unsigned x = gtab[i], y = gtab[i + jj];
-            if ((x > y) == ((i & k) == 0)) { gtab[i] = y; gtab[i + jj] = x; }
-          }
-          __syncwarp();
-        }
-    }
-    const auto tb = mag_bits(tau);
-    int nk = 0;
-    double dsum = 0.0, fsum = 0.0;
-    int *oi = Out.idx + (size_t)r * Out.w;
-    T *ov = Out.val + (size_t)r * Out.w;
-    constexpr int GPP = 32 / GW;
-    for (int c = 0; c < ng; c += GPP) {
-      const int gi = c + lane / GW;
-      bool keep = false;
-      int j = 0;
-      T v = T(0);
-      if (gi < ng) {
-        const unsigned e = gtab[gi];
-        const int b = (int)(e & 0xFFu);
-        j = (int)((e >> 8) << GSH) + (lane & (GW - 1));
-        v = vals[b * GW + (lane & (GW - 1))];
-        keep = KEEPZ ? !is_untouched(v) : mag_bits(v) > tb;
-      }
-      const unsigned m = __ballot_sync(kFull, keep);
-      if (keep) {
-        const int pos = nk + __popc(m & lt);
-        if (pos < Out.w) { oi[pos] = j; ov[pos] = v; }
-        const double dv = (double)v;
-        if (j == r) dsum += dv;
-        fsum = fma(dv, dv, fsum);
-      }
-      nk += __popc(m);
-    }
-    dsum = warp_sum(dsum);
-    fsum = warp_sum(fsum);
-    wmax = max(wmax, nk);
-    if (lane == 0) {
-      if (nk > Out.w) {
-        ++wover;
-        rowstat[r] = make_double2(0.0, 0.0);
-      } else {
-        Out.nnz[r] = nk;
-        rowstat[r] = make_double2(dsum, fsum);
-      }
-    }
-    __syncwarp();
-  }
-  if (lane == 0) {
-    if (wmax) atomicMax(&ctl->max_count, wmax);
-    if (wover) atomicAdd(&ctl->overflow_rows, wover);
-  }
-}
-
-// ------------------------------------------------------------------ run first pass
-// One warp per output row.  Each source row of the gather (the addend row C_i, then row
-// k of B for every entry a_ik) is split into 32 runs of consecutive entries, one run per
-// lane (PER = ceil(nb / 32) entries; rows longer than 32 * kRunMax go in rounds of that
-// size).  A sorted row's consecutive entries mostly share a column group, so a lane looks
-// its group up once per change of group, and the warp-level work per source row
-// (shuffles, addresses, branches) is paid once per row instead of once per 32 entries.
-// Source rows are loaded two ahead into registers.  Within a source row the columns are
-// distinct, so lanes never update the same slot; a __syncwarp between source rows orders
-// them, and every output entry accumulates its terms in source order (deterministic).
-constexpr int kRunMax = 8;
-
-template <typename T>
-struct RunGeo {
-  static constexpr int GSH = BlockCfg<T>::GSH, GW = 1 << GSH, NB = BlockCfg<T>::NB;
-  static constexpr int LOG2G = BlockCfg<T>::LOG2G, G = 1 << LOG2G;
-  static constexpr int VAL_BYTES = NB * GW * (int)sizeof(T);
-  static constexpr int BYTES_PER_ROW = VAL_BYTES + G * 4 + 16;
-  static constexpr int ROWS_RAW = 232192 / BYTES_PER_ROW;
-  static constexpr int ROWS = ROWS_RAW > 16 ? 16 : (ROWS_RAW < 1 ? 1 : ROWS_RAW);
-  static constexpr int SMEM = ROWS * BYTES_PER_ROW;
-  static constexpr unsigned MAX_GROUP = (1u << 24) - 1u;
-  static_assert(G == BlockGeo<T, 1>::G && NB == BlockGeo<T, 1>::NB, "one group table layout");
-};
-
-// One source row's first round, held by the warp: lane's run of cnt entries, the run
-// length per of the round (uniform), the coefficient, and the row for later rounds.
-template <typename T>
-struct RunBuf {
-  int j[kRunMax];
-  T v[kRunMax];
-  int per, cnt, nb;
-  T a;
-  const int *ri;
-  const T *rv;
-};
-
-template <typename T, bool KEEPZ>
-__global__ void __launch_bounds__(RunGeo<T>::ROWS * 32, 1)
-    spgemm_run_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
-                      int use_add, BatchView bv, Upper up, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
-                      int *__restrict__ fb_list, int *__restrict__ fb_count) {
-  using Geo = RunGeo<T>;
-  constexpr int GW = Geo::GW, GSH = Geo::GSH, G = Geo::G;
-  constexpr int ROUND = 32 * kRunMax;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned char *base = smem + (size_t)wid * Geo::BYTES_PER_ROW;
-  T *vals = reinterpret_cast<T *>(base);
-  unsigned *gtab = reinterpret_cast<unsigned *>(base + Geo::VAL_BYTES);
-  int *nblk = reinterpret_cast<int *>(base + Geo::VAL_BYTES + G * 4);
-  const int ncol = Out.n;
-  const unsigned lt = lanemask_lt();
-  int wmax = 0, wover = 0;
-
-  for (int r = blockIdx.x * Geo::ROWS + wid; r < A.n; r += gridDim.x * Geo::ROWS) {
-    T alpha_r = alpha, beta_r = beta;
-    int add_r = use_add;
-    if (bv.row_mat) {
-      const int m = bv.row_mat[r];
-      if (!bv.active[m]) continue;
-      alpha_r = (T)bv.alpha[m];
-      beta_r = (T)bv.beta[m];
-      add_r = beta_r != T(0);
-    }
-    {  // clear the blocks and the table
-      const T c = KEEPZ ? untouched<T>() : T(0);
-      constexpr int PER16 = 16 / (int)sizeof(T);
-      for (int i = lane * PER16; i < Geo::NB * GW; i += 32 * PER16) {
-#pragma unroll
-        for (int t = 0; t < PER16; ++t) vals[i + t] = c;
-      }
-      for (int i = lane * 4; i < G; i += 32 * 4) *reinterpret_cast<uint4 *>(gtab + i) = make_uint4(~0u, ~0u, ~0u, ~0u);
-      if (lane == 0) *nblk = 0;
-    }
-    __syncwarp();
-
-    const int na = min(A.nnz[r], A.w);
-    const int ns = na + (add_r ? 1 : 0);  // sources: [addend row], then the rows of B
-    const int *arow_i = A.idx + (size_t)r * A.w;
-    const T *arow_v = A.val + (size_t)r * A.w;
-    int pk = 0, pnb = 0, pst = 0, pbase = -32;  // A entries pbase .. pbase+31 (k, count, start, alpha*a)
-    T pa = T(0);
-
-    // run of this lane in a round of n entries starting at entry off of row (ri, rv)
-    auto load_run = [&](const int *ri, const T *rv, int off, int n, int &per, int &cnt, int (&jr)[kRunMax],
-                        T (&vr)[kRunMax]) {
-      per = (n + 31) >> 5;
-      const int s0 = lane * per;
-      cnt = max(0, min(per, n - s0));
-#pragma unroll
-      for (int i = 0; i < kRunMax; ++i) {
-        jr[i] = i < cnt ? __ldg(ri + off + s0 + i) : -1;
-        vr[i] = i < cnt ? __ldg(rv + off + s0 + i) : T(0);
-      }
-    };
-    // source s -> buffer (first round loaded); s >= ns gives an empty buffer
-    auto load_src = [&](int s, RunBuf<T> &bf) {
-      bf.nb = 0; bf.a = T(0); bf.ri = B.idx; bf.rv = B.val;
-      if (s < ns) {
-        if (add_r && s == 0) {
-          const int nc = min(Add.nnz[r], Add.w);
-          const int d0 = up.tpd ? min(max(up.tpd[r], 0), nc) : 0;  // upper-triangle mode
-          bf.ri = Add.idx + (size_t)r * Add.w + d0;
-          bf.rv = Add.val + (size_t)r * Add.w + d0;
-          bf.nb = nc - d0;
-          bf.a = beta_r;
-        } else {
-          const int t = s - add_r;
-          if (t >= pbase + 32) {
-            pbase = t & ~31;
-            const int q = pbase + lane;
-            pk = 0; pnb = 0; pst = 0; pa = T(0);
-            if (q < na) {
-              const int k = __ldg(arow_i + q);
-              if ((unsigned)k < (unsigned)B.n) {
-                pk = k;
-                pa = alpha_r * __ldg(arow_v + q);
-                pnb = min(__ldg(B.nnz + k), B.w);
-                if (up.tp) pst = min(max(__ldg(up.tp + (size_t)r * A.w + q), 0), pnb);
-                pnb -= pst;
-              }
-            }
-          }
-          const int k = __shfl_sync(kFull, pk, t & 31);
-          const int st = __shfl_sync(kFull, pst, t & 31);
-          bf.nb = __shfl_sync(kFull, pnb, t & 31);
-          bf.a = __shfl_sync(kFull, pa, t & 31);
-          bf.ri = B.idx + (size_t)k * B.w + st;
-          bf.rv = B.val + (size_t)k * B.w + st;
-        }
-      }
-      load_run(bf.ri, bf.rv, 0, min(bf.nb, ROUND), bf.per, bf.cnt, bf.j, bf.v);
-    };
-
-    bool aborted = false;
-    // accumulate one round held in registers: lookups once per change of group, claims
-    // for new groups (one elected lane per group), then one load-FMA-store per entry
-    auto accumulate = [&](auto per_c, int cnt, const int (&jr)[kRunMax], const T (&vr)[kRunMax], T a) {
-      constexpr int PER = decltype(per_c)::value;
-      int bk[PER];
-      unsigned miss = 0;
-      unsigned gp = 0xFFFFFFFFu;
-      int bp = -1;
-#pragma unroll
-      for (int i = 0; i < PER; ++i) {
-        bk[i] = -2;
-        if (i < cnt && (unsigned)jr[i] < (unsigned)ncol) {
-          const unsigned g = (unsigned)jr[i] >> GSH;
-          if (g != gp) {
-            gp = g;
-            bp = probe_block<Geo::LOG2G>(gtab, g);
-          }
-          bk[i] = bp;
-          if (bp < 0) miss |= 1u << i;
-        }
-      }
-      while (__any_sync(kFull, miss != 0)) {
-        const int i0 = miss ? __ffs(miss) - 1 : -1;
-        unsigned g = 0;
-#pragma unroll
-        for (int i = 0; i < PER; ++i)
-          if (i == i0) g = (unsigned)jr[i] >> GSH;
-        const unsigned act = __ballot_sync(kFull, i0 >= 0);
-        if (i0 >= 0) {
-          const unsigned peers = __match_any_sync(act, g);
-          const int leader = __ffs(peers) - 1;
-          int b = -1;
-          if (lane == leader) b = g < Geo::MAX_GROUP ? group_block<T, 1>(gtab, nblk, g) : -1;
-          b = __shfl_sync(peers, b, leader);
-          if (b < 0) aborted = true;
-#pragma unroll
-          for (int i = 0; i < PER; ++i)
-            if ((miss >> i) & 1u && ((unsigned)jr[i] >> GSH) == g) {
-              bk[i] = b;
-              miss &= ~(1u << i);
-            }
-        }
-        __syncwarp();
-      }
-#pragma unroll
-      for (int i = 0; i < PER; ++i)
-        if ((unsigned)bk[i] < (unsigned)Geo::NB) {
-          const int slot = bk[i] * GW + (jr[i] & (GW - 1));
-          const T o0 = vals[slot];
-          const T o = (KEEPZ && is_untouched(o0)) ? T(0) : o0;
-          vals[slot] = fmadd(a, vr[i], o);
-        }
-    };
-    auto accumulate_any = [&](int per, int cnt, const int (&jr)[kRunMax], const T (&vr)[kRunMax], T a) {
-      switch (per) {
-        case 0: break;
-        case 1: accumulate(std::integral_constant<int, 1>{}, cnt, jr, vr, a); break;
-        case 2: accumulate(std::integral_constant<int, 2>{}, cnt, jr, vr, a); break;
-        case 3: accumulate(std::integral_constant<int, 3>{}, cnt, jr, vr, a); break;
-        case 4: accumulate(std::integral_constant<int, 4>{}, cnt, jr, vr, a); break;
-        case 5: accumulate(std::integral_constant<int, 5>{}, cnt, jr, vr, a); break;
-        case 6: accumulate(std::integral_constant<int, 6>{}, cnt, jr, vr, a); break;
-        case 7: accumulate(std::integral_constant<int, 7>{}, cnt, jr, vr, a); break;
-        default: accumulate(std::integral_constant<int, kRunMax>{}, cnt, jr, vr, a); break;
-      }
-    };
-    // (aborted is set by single lanes; it is made warp-uniform before every test of it,
-    // since the code it guards uses whole-warp shuffles and votes)
-    auto process = [&](const RunBuf<T> &bf) {
-      accumulate_any(bf.per, bf.cnt, bf.j, bf.v, bf.a);
-      __syncwarp();  // this source row's updates land before the next one reads
-      aborted = __any_sync(kFull, aborted);
-      for (int off = ROUND; off < bf.nb && !aborted; off += ROUND) {  // rows longer than one round
-        int per, cnt, jt[kRunMax];
-        T vt[kRunMax];
-        load_run(bf.ri, bf.rv, off, min(bf.nb - off, ROUND), per, cnt, jt, vt);
-        accumulate_any(per, cnt, jt, vt, bf.a);
-        __syncwarp();
-        aborted = __any_sync(kFull, aborted);
-      }
-    };
-
-    RunBuf<T> b0, b1, b2;
-    load_src(0, b0);
-    load_src(1, b1);
-    for (int s = 0; s < ns && !aborted; s += 3) {
-      load_src(s + 2, b2);
-      process(b0);
-      if (s + 1 >= ns || aborted) break;
-      load_src(s + 3, b0);
-      process(b1);
-      if (s + 2 >= ns || aborted) break;
-      load_src(s + 4, b1);
-      process(b2);
-    }
-    if (aborted) {
-      if (lane == 0) {
-        const int p = atomicAdd(fb_count, 1);
-        fb_list[p] = r;
-      }
-      __syncwarp();
-      continue;
-    }
-
-    // ---- epilogue: groups in column order, lane -> column
     int ng = 0;
     for (int c = 0; c < G; c += 32) {
       const unsigned e = gtab[c + lane];
@@ -1987,43 +1664,6 @@ int launch_super(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
   return SP2_OK;
 }
 
-template <typename T, bool KEEPZ>
-int launch_run(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
-  using Geo = RunGeo<T>;
-  auto kern = spgemm_run_kernel<T, KEEPZ>;
-  static bool attr_set[64] = {false};
-  static int occ_cache[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (!attr_set[dev]) {
-    SP2_TRY(set_smem(kern, Geo::SMEM));
-    int occ = 0;
-    SP2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Geo::ROWS * 32, Geo::SMEM));
-    occ_cache[dev] = occ < 1 ? 1 : occ;
-    attr_set[dev] = true;
-  }
-  const long long cap = (long long)num_sms() * occ_cache[dev];
-  const long long blocks = ((long long)a.A->n + Geo::ROWS - 1) / Geo::ROWS;
-  int grid = (int)(blocks < cap ? blocks : cap);
-  if (grid < 1) grid = 1;
-  const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
-  prof_begin(SP2_PROF_SPGEMM, s);
-  kern<<<grid, Geo::ROWS * 32, Geo::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
-                                              (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv, a.up,
-                                              rowstat, ctl, fb, fb_count);
-  note_launch();
-  prof_end(SP2_PROF_SPGEMM, s);
-  SP2_CUDA(cudaGetLastError());
-  return SP2_OK;
-}
-
-template <typename T>
-int launch_run_auto(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
-  return a.tau == 0.0 ? launch_run<T, true>(a, rowstat, ctl, fb, fb_count, s)
-                      : launch_run<T, false>(a, rowstat, ctl, fb, fb_count, s);
-}
-
 template <typename T>
 int launch_super_auto(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
   constexpr int QM = sizeof(T) == 8 ? 6 : 6;
@@ -2033,17 +1673,17 @@ int launch_super_auto(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, i
 
 // Compact variants for the upper-triangle rows of symmetric products: half the blocks
 // per row and register slots for the shorter source rows, more rows per SM.
-template <typename T>
+template <typename T, int SZ>
 int launch_block_compact(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count,
                          cudaStream_t s) {
-  return a.tau == 0.0 ? launch_block<T, 4, 1, true, 1>(a, rowstat, ctl, fb, fb_count, s)
-                      : launch_block<T, 4, 1, false, 1>(a, rowstat, ctl, fb, fb_count, s);
+  return a.tau == 0.0 ? launch_block<T, 4, 1, true, SZ>(a, rowstat, ctl, fb, fb_count, s)
+                      : launch_block<T, 4, 1, false, SZ>(a, rowstat, ctl, fb, fb_count, s);
 }
-template <typename T>
+template <typename T, int SZ>
 int launch_super_compact(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count,
                          cudaStream_t s) {
-  return a.tau == 0.0 ? launch_super<T, 3, 2, true, 1>(a, rowstat, ctl, fb, fb_count, s)
-                      : launch_super<T, 3, 2, false, 1>(a, rowstat, ctl, fb, fb_count, s);
+  return a.tau == 0.0 ? launch_super<T, 3, 2, true, SZ>(a, rowstat, ctl, fb, fb_count, s)
+                      : launch_super<T, 3, 2, false, SZ>(a, rowstat, ctl, fb, fb_count, s);
 }
 
 // Block first pass with R warps per row; the register slots per warp cover the width of B.
@@ -2088,21 +1728,22 @@ int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
   switch (path) {
     case 1: rc = launch_block_r<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 4: rc = launch_block_r<T, 4>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
-    case 6: rc = launch_block_r<T, 5>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 10: rc = launch_hash<T, 10, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s); break;
     case 11: rc = launch_hash<T, 11, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s); break;
     case 12: rc = launch_hash<T, 12, QM>(a, rowstat, ctl, nullptr, nullptr, fb1, &ctl->n_fallback, s); break;
     case 2: rc = launch_block_r<T, 2>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 3: rc = launch_super_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
-    case 5: rc = launch_run_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
-    case 7: rc = launch_block_compact<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
-    case 8: rc = launch_super_compact<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
+    case 7: rc = launch_block_compact<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
+    case 8: rc = launch_super_compact<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     default:  // automatic: the variant measured fastest on the 3D tight-binding products
               // (FP64: 4 warps per row; FP32: one warp per row, two k steps per pass), in
               // its compact form for the upper triangle of a symmetric product
-      if (a.up.tp && !a.no_compact)
-        rc = sizeof(T) == 8 ? launch_block_compact<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
-                            : launch_super_compact<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s);
+      if (a.up.tp && a.compact_level == 0)
+        rc = sizeof(T) == 8 ? launch_block_compact<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
+                            : launch_super_compact<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s);
+      else if (a.up.tp && a.compact_level == 1)
+        rc = sizeof(T) == 8 ? launch_block_compact<T, 2>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
+                            : launch_super_compact<T, 2>(a, rowstat, ctl, fb1, &ctl->n_fallback, s);
       else
         rc = sizeof(T) == 8 ? launch_block_r<T, 4>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
                             : launch_super_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s);

@@ -521,7 +521,7 @@ class NnzPredictor:
 
 
 # ---------------------------------------------------------------- autotuner
-TUNE_CANDIDATES = (1, 2, 4, 6, 7, 3, 8, 5, 10, 11, 12)
+TUNE_CANDIDATES = (1, 2, 4, 7, 3, 8, 10, 11, 12)
 
 
 def sp2_tune_spgemm(A, B, C, Out, alpha=1.0, beta=0.0, tau=0.0, reps=3, stream=None):

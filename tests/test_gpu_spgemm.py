@@ -264,7 +264,7 @@ def test_x0(gpu, tau):
         assert np.allclose(gv[i, :gn[i]], ref.row(i)[1], rtol=5e-16, atol=1e-300)
 
 
-@pytest.mark.parametrize("first_pass", [0, 1, 2, 3, 4, 5, 6, 7, 8, 11])
+@pytest.mark.parametrize("first_pass", [0, 1, 2, 3, 4, 7, 8, 11])
 @pytest.mark.parametrize("fp32", [False, True])
 def test_first_pass_variants(gpu, first_pass, fp32):
     """Every first-pass variant (column blocks with 1, 2, 4 warps per row, the two-step

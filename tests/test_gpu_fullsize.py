@@ -1,6 +1,7 @@
 """Full-size ELLPACK X^2 case (3D tight-binding N=262144, FP64, tau 1e-6) in the launch
-configuration the benchmark times (sp2_step, automatic table size): sampled output rows
-against the oracle computed row by row, plus properties that hold at any size (GPU)."""
+configuration the benchmark times (sp2_step, automatic first pass, symmetric product) and
+with full rows: sampled output rows against the oracle computed row by row, plus
+properties that hold at any size (GPU)."""
 import numpy as np
 import pytest
 
@@ -31,7 +32,9 @@ def x1():
     return X1, O.trace(X1), float((np.where(live, X1.val, 0.0) ** 2).sum())
 
 
-def test_fullsize_step_sampled_rows(gpu, x1):
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_fullsize_step_sampled_rows(gpu, x1, symmetric):
+    """symmetric: the upper-triangle product mirrored (the benchmark's configuration)."""
     S = gpu
     X1, tr, tr2 = x1
     nocc = N / 2
@@ -44,10 +47,10 @@ def test_fullsize_step_sampled_rows(gpu, x1):
     val[:, :X1.w] = X1.val
     dX = S.Ellpack.from_numpy(idx, val, X1.nnz)
     probe = S.Ellpack.empty(N, 32)
-    rc, info = S.sp2_step(dX, probe, nocc, TAU, traces=(tr, tr2), raise_on_overflow=False)
+    rc, info = S.sp2_step(dX, probe, nocc, TAU, traces=(tr, tr2), raise_on_overflow=False, symmetric=symmetric)
     assert rc == S.SP2E_OVERFLOW
     out = S.Ellpack.empty(N, ((info.required_width + 31) // 32) * 32)
-    info = S.sp2_step(dX, out, nocc, TAU, traces=(tr, tr2))
+    info = S.sp2_step(dX, out, nocc, TAU, traces=(tr, tr2), symmetric=symmetric)
     assert info.branch == (2 if up else 1)
     g = out.to_numpy()
     rng = np.random.default_rng(5)

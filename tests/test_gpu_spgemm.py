@@ -325,7 +325,7 @@ def hub_matrix(n, hubs, hub_nnz, other_nnz, seed):
     return O.Ell(*I.coo_to_ellpack(n, rows, cols, vals))
 
 
-@pytest.mark.parametrize("first_pass", [0, 5])
+@pytest.mark.parametrize("first_pass", [0, 3])
 def test_all_three_passes(gpu, first_pass):
     """Rows with more column groups than the block accumulator holds and a column span
     wider than the shared-memory window go to the 2^14-slot table; rows with more

@@ -182,11 +182,12 @@ int ellpack_gershgorin(const ellpack_t *H, double *emin, double *emax, void *str
 
 /* ---------------------------------------------------------------- profiling */
 /* Kernel classes timed by the profiler. */
-#define SP2_PROF_SPGEMM 0   /* the per-row hash SpGEMM kernel (dominant) */
-#define SP2_PROF_LARGE 1    /* the large-row (dense global row) SpGEMM kernel */
+#define SP2_PROF_SPGEMM 0   /* the first pass of the SpGEMM over every row (dominant) */
+#define SP2_PROF_LARGE 1    /* the bins of deferred rows (window, 2^14-slot table, dense row) */
 #define SP2_PROF_REDUCE 2   /* ordered trace/norm reductions */
 #define SP2_PROF_OTHER 3    /* everything else (X0, conversions, add, Gershgorin) */
-#define SP2_PROF_CLASSES 4
+#define SP2_PROF_SYMM 4     /* symmetric products: lower-bound starts and the mirror of U */
+#define SP2_PROF_CLASSES 5
 
 typedef struct sp2_profile {
   int64_t launches;                   /* kernels launched by the library while enabled */
@@ -314,9 +315,9 @@ int ellpack_from_dense(const void *dense, int64_t ld, double tau, ellpack_t *A, 
 /* ---------------------------------------------------------------- autotuner */
 /*
  * The SpGEMM first pass has several variants that compute the same product (spgemm_path
- * 1, 2, 4: column-block accumulator shared by that many warps per row (7: 4 warps, about
- * half the blocks per row, for the upper triangles of symmetric products); 3: one warp per
- * row, two k steps per pass (8: compact, as 7); 10..12: per-warp hash table of 2^path
+ * 1, 2, 4: column-block accumulator shared by that many warps per row (7: 2 warps, fewer
+ * accumulator slots per row, for the upper triangles of symmetric products); 3: one warp
+ * per row, two k steps per pass (8: compact, as 7); 10..12: per-warp hash table of 2^path
  * slots).  The tuner
  * times them on a real product and keeps the fastest per class (SM count, dtype,
  * floor(log2 n), floor(log2 mean stored row length of A)) in a process-wide host table
@@ -362,13 +363,14 @@ int sp2_tune_load(const char *path);
 typedef struct sp2_options {
   int32_t precision;    /* SP2_PREC_F64 or SP2_PREC_MIXED */
   int32_t max_iter;     /* cap on updates (default 100) */
-  int32_t stall_rule;   /* 1: stop once |trX - trX2| < stall_arm has been seen and err_n >= err_{n-2} */
+  int32_t stall_rule;   /* 1: stop once |trX - trX2| < stall_arm has been seen and
+                           err_n >= stall_ratio * err_{n-2} */
   int32_t n_fp64_tail;  /* MIXED: minimum FP64 iterations after the switch (default 2) */
   int32_t max_width;    /* cap on the working width (0 = n); SP2E_OVERFLOW beyond it */
   int32_t spgemm_path;  /* SpGEMM first pass: 0 automatic (column blocks; F64: 4 warps
                            per row, F32: path 3; their compact forms 7 and 8 for
                            symmetric products); 1, 2, 4 = column-block accumulator
-                           shared by that many warps per row (7: 4, compact); 3 = column
+                           shared by that many warps per row (7: 2, compact); 3 = column
                            blocks, one warp per row, two k steps per pass (8: compact);
                            10..12 = per-warp hash table of 2^k slots; SP2_PATH_TUNED = the
                            autotuner's choice */
@@ -387,6 +389,9 @@ typedef struct sp2_options {
                            otherwise); every product computes its upper triangle and mirrors
                            it (the same result bit for bit, about half the products).
                            0: full rows, no check */
+  double stall_ratio;   /* the armed stall rule fires once err_n >= stall_ratio * err_{n-2};
+                           in (0, 1], default 1 (two updates brought no reduction); below 1
+                           it also ends a slow monotone drift at the floor tau sets */
 } sp2_options;
 
 typedef struct sp2_stats {

@@ -59,7 +59,7 @@ def _declare(L):
     L.orc_gershgorin.argtypes = [P(_OrcEll), P(ctypes.c_double), P(ctypes.c_double)]
     L.orc_x0.argtypes = [P(_OrcEll), ctypes.c_double, ctypes.c_double, ctypes.c_double, P(_OrcEll)]
     L.orc_sp2.argtypes = [P(_OrcEll), ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                          ctypes.c_int, ctypes.c_double, P(_OrcEll), P(_OrcStats)]
+                          ctypes.c_int, ctypes.c_double, ctypes.c_double, P(_OrcEll), P(_OrcStats)]
     L.orc_free_ell.argtypes = [P(_OrcEll)]
     L.orc_set_threads.argtypes = [ctypes.c_int]
     L.orc_get_max_threads.restype = ctypes.c_int
@@ -247,10 +247,11 @@ def x0(H, emin, emax, tau=0.0):
     return out
 
 
-def sp2(H, nocc, tol, tau=0.0, max_iter=100, stall=True, stall_arm=0.1):
+def sp2(H, nocc, tol, tau=0.0, max_iter=100, stall=True, stall_arm=0.1, stall_ratio=1.0):
     """SP2 purification.  Returns (D, stats) where stats is a dict with the per-iteration
     trace, trace-of-square, error and branch sequences ("X2" / "2X-X2").  The stall rule
-    (stall=True) arms once |trX - trX2| < stall_arm and fires when err_n >= err_{n-2}."""
+    (stall=True) arms once |trX - trX2| < stall_arm and fires when
+    err_n >= stall_ratio * err_{n-2}."""
     L = lib()
     cap = max_iter + 1
     trX, trX2, err = np.zeros(cap), np.zeros(cap), np.zeros(cap)
@@ -269,7 +270,7 @@ def sp2(H, nocc, tol, tau=0.0, max_iter=100, stall=True, stall_arm=0.1):
     h = H._c()
     d = _OrcEll()
     rc = L.orc_sp2(ctypes.byref(h), float(nocc), float(tol), float(tau), int(max_iter),
-                   float(stall_arm) if stall else 0.0, ctypes.byref(d), ctypes.byref(st))
+                   float(stall_arm) if stall else 0.0, float(stall_ratio), ctypes.byref(d), ctypes.byref(st))
     if rc != 0:
         raise ValueError("oracle rejected its arguments")
     n, w = d.n, d.w

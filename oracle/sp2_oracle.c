@@ -336,11 +336,14 @@ static orc_ell add_fit(const orc_ell *A, const orc_ell *B, double alpha, double 
 /*
  * SP2 purification of H.  On return *D holds the density matrix (library-allocated
  * arrays, release with orc_free_ell).  Stall rule (if stall_arm > 0): armed once
- * |trX - trX2| < stall_arm (0.1 in the method's reading); fires when err_n >= err_{n-2}.
+ * |trX - trX2| < stall_arm (0.1 in the method's reading); fires when
+ * err_n >= stall_ratio * err_{n-2} (stall_ratio 1 in the method's reading: two updates
+ * brought no reduction; a ratio below 1 also ends a slow monotone drift).
  */
 int orc_sp2(const orc_ell *H, double nocc, double tol, double tau, int max_iter, double stall_arm,
-            orc_ell *D, orc_sp2_stats *st) {
+            double stall_ratio, orc_ell *D, orc_sp2_stats *st) {
   if (!H || !D || !st || max_iter < 0 || tau < 0.0) return -1;
+  if (!(stall_ratio > 0.0 && stall_ratio <= 1.0)) return -1;
   int n = H->n;
   double emin, emax;
   orc_gershgorin(H, &emin, &emax);
@@ -362,7 +365,7 @@ int orc_sp2(const orc_ell *H, double nocc, double tol, double tau, int max_iter,
     if (err < tol) { st->status = 0; ell_free(&P); break; }
     if (stall_arm > 0.0) {
       if (fabs(trX - trX2) < stall_arm) armed = 1;
-      if (armed && it >= 2 && err >= st->err[it - 2]) { st->status = 1; ell_free(&P); break; }
+      if (armed && it >= 2 && err >= stall_ratio * st->err[it - 2]) { st->status = 1; ell_free(&P); break; }
     }
     if (it >= max_iter) { st->status = 2; ell_free(&P); break; }
     orc_ell Xn;

@@ -53,6 +53,7 @@ struct Control {
   int halves;       // half-iterations run so far
   int max_halves;   // hard bound on the loop, whatever the per-matrix state says
   double stall_arm; // the stall rule arms once |trX - trX2| < stall_arm
+  double stall_ratio; // ... and fires once err_n >= stall_ratio * err_{n-2}
 };
 
 struct Stats {
@@ -265,7 +266,7 @@ __global__ void control_kernel(int count, int half, MatState *__restrict__ st, c
         s.final_dt = s.phase == 0 ? SP2_F32 : SP2_F64;
       }
       if (fabs(rr.tr - rr.fro) < ctl->stall_arm) s.armed = 1;
-      const bool stalled = s.armed && it >= 2 && it - 2 < kCap && err >= stats.err[(size_t)m * kCap + it - 2];
+      const bool stalled = s.armed && it >= 2 && it - 2 < kCap && err >= ctl->stall_ratio * stats.err[(size_t)m * kCap + it - 2];
       bool done = false;
       if (!isfinite(rr.tr) || !isfinite(rr.fro)) {
         done = true;
@@ -390,6 +391,8 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
     return fail(SP2E_ARG, "sp2_purify_batched: spgemm_path must be -1, 0..4, 7, 8 or 10..12");
   if (!(opt.stall_arm > 0.0) || !isfinite(opt.stall_arm))
     return fail(SP2E_ARG, "sp2_purify_batched: stall_arm must be > 0");
+  if (!(opt.stall_ratio > 0.0 && opt.stall_ratio <= 1.0))
+    return fail(SP2E_ARG, "sp2_purify_batched: stall_ratio must be in (0, 1]");
   long long ntot_ll = 0;
   int wh = 1, nmax = 0;
   std::vector<int> off(count + 1, 0);
@@ -497,7 +500,7 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
     SP2_CUDA(cudaMemsetAsync(d_act64, 0, sizeof(int) * count, s));
     SP2_CUDA(cudaMemsetAsync(sd.branch, 0, sizeof(int) * (size_t)count * kCap, s));
     Control ch{opt.max_iter, opt.stall_rule, mixed ? opt.n_fp64_tail : 0, mixed ? 1 : 0, tol, switch_tol, 0, 0, 0,
-               2 * (opt.max_iter + opt.n_fp64_tail + 8), opt.stall_arm};
+               2 * (opt.max_iter + opt.n_fp64_tail + 8), opt.stall_arm, opt.stall_ratio};
     SP2_CUDA(cudaMemcpyAsync(d_ctl, &ch, sizeof(ch), cudaMemcpyHostToDevice, s));
     SP2_CUDA(cudaMemsetAsync(d_c32, 0, sizeof(SpgemmCtl), s));
     SP2_CUDA(cudaMemsetAsync(d_c64, 0, sizeof(SpgemmCtl), s));

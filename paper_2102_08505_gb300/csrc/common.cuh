@@ -95,6 +95,7 @@ struct StepResult {
   int n_fallback;      // rows deferred from the per-warp tables to the 2^14-slot table
   int nonfinite;       // 1 if tr or fro is not finite
   int n_fallback2;     // rows deferred further to the dense global-row kernel
+  int n_heavy;         // of n_fallback: rows sent on for the length of their row of A alone
 };
 
 // Device control block of one multiply launch.
@@ -104,6 +105,7 @@ struct SpgemmCtl {
   int n_fallback;   // count of the first deferred-row list
   int n_fallback2;  // count of the second deferred-row list
   int n_fallbackw;  // count of the rows the window bin passes on
+  int n_heavy;      // rows of the first list deferred for the length of their row of A
 };
 
 // rowstat[r] = {diagonal value, sum of squares} of output row r (post-threshold).

@@ -15,7 +15,7 @@ struct Pair {
   cudaEvent_t a, b;
 };
 std::vector<Pair> g_pairs;
-thread_local cudaEvent_t t_open[SP2_PROF_CLASSES] = {nullptr, nullptr, nullptr, nullptr};
+thread_local cudaEvent_t t_open[SP2_PROF_CLASSES] = {};
 }  // namespace
 
 void note_launch() {

@@ -75,6 +75,7 @@ extern "C" void sp2_options_default(sp2_options *o) {
   o->sizing = 0;
   o->predictor = nullptr;
   o->stall_arm = 0.1;
+  o->stall_ratio = 1.0;
   o->symmetric = 1;
 }
 
@@ -104,6 +105,8 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   if (!(opt.switch_tol >= 0.0) || !isfinite(opt.switch_tol)) return fail(SP2E_ARG, "sp2_purify: bad switch_tol");
   if (opt.sizing < 0 || opt.sizing > 2) return fail(SP2E_ARG, "sp2_purify: sizing must be 0, 1 or 2");
   if (!(opt.stall_arm > 0.0) || !isfinite(opt.stall_arm)) return fail(SP2E_ARG, "sp2_purify: stall_arm must be > 0");
+  if (!(opt.stall_ratio > 0.0 && opt.stall_ratio <= 1.0))
+    return fail(SP2E_ARG, "sp2_purify: stall_ratio must be in (0, 1]");
   if (opt.sizing == 2 && (!opt.predictor || !opt.predictor->params))
     return fail(SP2E_ARG, "sp2_purify: sizing 2 needs a created predictor");
   const double switch_tol = opt.switch_tol > 0.0 ? opt.switch_tol : (tol > 1e-4 ? tol : 1e-4);
@@ -226,7 +229,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
     bool stop = false;
     const bool stalled = [&] {
       if (fabs(trX - trX2) < opt.stall_arm) armed = true;
-      return armed && it >= 2 && err >= st.err[it - 2];
+      return armed && it >= 2 && err >= opt.stall_ratio * st.err[it - 2];
     }();
     if (phase == MAIN) {
       bool main_done = false;
@@ -344,7 +347,8 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
     // the compact first passes (automatic for symmetric products) hold fewer blocks per row:
     // once one defers more than 0.2 % of the rows, the next larger variant takes over for the
     // rest of the run (tight -> loose -> full rows)
-    if (compact_level < 2 && opt.symmetric && lg == 0 && res.n_fallback > n / 500) ++compact_level;
+    // rows deferred for their length alone take the bins at every level: not counted here
+    if (compact_level < 2 && opt.symmetric && lg == 0 && res.n_fallback - res.n_heavy > n / 500) ++compact_level;
     ellpack_t t = b.X; b.X = b.Y; b.Y = t;
     ++it;
   }

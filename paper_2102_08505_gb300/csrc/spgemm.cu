@@ -12,8 +12,8 @@
 //
 // First pass (one of several variants that compute the same product; the tuner or the
 // caller picks one):
-//  - column blocks (paths 1, 2, 4; 7 = 4 warps, compact): a row's output columns are grouped in runs of GW (16
-//    for FP64, 32 for FP32); a per-row group table in shared memory maps a group to a
+//  - column blocks (paths 1, 2, 4; 7 = 2 warps, compact): a row's output columns are grouped in runs of GW (16
+//    for FP64, 8 in its compact form; 32 for FP32); a per-row group table in shared memory maps a group to a
 //    block of GW accumulator slots (claimed on first touch), so column j sits in bank
 //    j mod 32.  R warps share a row and split each source row's entries, with a named
 //    barrier between source rows.
@@ -33,6 +33,12 @@ namespace sp2 {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kEmpty = -1;
+// Rows of A with more entries than this skip the one-warp first pass (spgemm_super_kernel)
+// and go straight to the deferred-row bins, whose one CTA per row suits their work
+// (hundreds of source rows per output row, which one warp would carry alone when they fit
+// its blocks).  The passes with several warps per row keep them: there, rows that fit the
+// blocks finish faster than in the bins, several rows per SM at a time.
+constexpr int kHeavyRowA = 512;
 
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
@@ -391,15 +397,15 @@ template <> struct BlockCfg<double, 0> {
 template <> struct BlockCfg<float, 0> {
   static constexpr int GSH = 5, NB = 128, LOG2G = 9;
 };
-template <> struct BlockCfg<double, 1> {
-  static constexpr int GSH = 4, NB = 160, LOG2G = 9;
+template <> struct BlockCfg<double, 1> {  // 8-column blocks: less of each block left unused
+  static constexpr int GSH = 3, NB = 224, LOG2G = 9;
 };
 template <> struct BlockCfg<float, 1> {
   static constexpr int GSH = 5, NB = 80, LOG2G = 8;
 };
 // SZ = 2: between the two, for the denser products of converging SP2 iterations
 template <> struct BlockCfg<double, 2> {
-  static constexpr int GSH = 4, NB = 192, LOG2G = 9;
+  static constexpr int GSH = 3, NB = 256, LOG2G = 9;
 };
 template <> struct BlockCfg<float, 2> {
   static constexpr int GSH = 5, NB = 112, LOG2G = 9;
@@ -809,6 +815,13 @@ __global__ void __launch_bounds__(BlockGeo<T, 1, SZ>::WARPS * 32, 1)
       alpha_r = (T)bv.alpha[m];
       beta_r = (T)bv.beta[m];
       add_r = beta_r != T(0);
+    }
+    if (A.nnz[r] > kHeavyRowA) {  // straight to the deferred-row bins (see kHeavyRowA)
+      if (lane == 0) {
+        fb_list[atomicAdd(fb_count, 1)] = r;
+        atomicAdd(&ctl->n_heavy, 1);
+      }
+      continue;
     }
     {
       const T c = KEEPZ ? untouched<T>() : T(0);
@@ -1671,13 +1684,13 @@ int launch_super_auto(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, i
                       : launch_super<T, QM, 2, false>(a, rowstat, ctl, fb, fb_count, s);
 }
 
-// Compact variants for the upper-triangle rows of symmetric products: half the blocks
-// per row and register slots for the shorter source rows, more rows per SM.
+// Compact variants for the upper-triangle rows of symmetric products: fewer accumulator
+// slots per row and fewer warps per row (2 for the column blocks), more rows per SM.
 template <typename T, int SZ>
 int launch_block_compact(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count,
                          cudaStream_t s) {
-  return a.tau == 0.0 ? launch_block<T, 4, 1, true, SZ>(a, rowstat, ctl, fb, fb_count, s)
-                      : launch_block<T, 4, 1, false, SZ>(a, rowstat, ctl, fb, fb_count, s);
+  return a.tau == 0.0 ? launch_block<T, 2, 2, true, SZ>(a, rowstat, ctl, fb, fb_count, s)
+                      : launch_block<T, 2, 2, false, SZ>(a, rowstat, ctl, fb, fb_count, s);
 }
 template <typename T, int SZ>
 int launch_super_compact(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count,
@@ -1736,8 +1749,9 @@ int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
     case 7: rc = launch_block_compact<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 8: rc = launch_super_compact<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     default:  // automatic: the variant measured fastest on the 3D tight-binding products
-              // (FP64: 4 warps per row; FP32: one warp per row, two k steps per pass), in
-              // its compact form for the upper triangle of a symmetric product
+              // (FP64: column blocks, 4 warps per row, 2 in the compact form; FP32: one warp
+              // per row, two k steps per pass), in its compact form for the upper triangle
+              // of a symmetric product
       if (a.up.tp && a.compact_level == 0)
         rc = sizeof(T) == 8 ? launch_block_compact<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
                             : launch_super_compact<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s);

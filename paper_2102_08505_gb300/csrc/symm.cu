@@ -22,7 +22,8 @@ namespace {
 
 constexpr unsigned kFullM = 0xffffffffu;
 constexpr int kSymThreads = 256;
-constexpr int kSortWarpMax = 512;    // lower parts up to this length are sorted by one warp in shared memory
+constexpr int kSortWarpMax = 256;    // lower parts up to this length are sorted by one warp in registers
+constexpr int kSortMidMax = 512;     // ... up to this length by one warp in registers, in a kernel of their own
 constexpr int kSortCtaMax = 4096;    // ... up to this length by one CTA in shared memory
 
 int grid_rows_sym(long long rows) {
@@ -130,16 +131,96 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// Bitonic network over the 32*E keys a warp holds, E per lane in lane-major order
+// (element lane*E + t): exchanges at distances below E stay in a lane's registers, the
+// others pair lanes lane ^ (j / E) by shuffle.  Ascending on exit.
+template <int E>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&a)[E], int lane) {
+  static_assert(E == 1 || E == 2 || E == 4 || E == 8 || E == 16, "E: 1, 2, 4, 8 or 16 keys per lane");
+  constexpr int LOGP = 5 + (E >= 2) + (E >= 4) + (E >= 8) + (E >= 16);
+#pragma unroll
+  for (int lk = 1; lk <= LOGP; ++lk) {
+    const int k = 1 << lk;
+#pragma unroll
+    for (int lj = lk - 1; lj >= 0; --lj) {
+      const int j = 1 << lj;
+      if (j < E) {
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+          if (t & j) continue;
+          const int u = t | j;
+          const bool asc = ((lane * E + t) & k) == 0;
+          const unsigned long long x = a[t], y = a[u];
+          const bool sw = asc ? (x > y) : (x < y);
+          a[t] = sw ? y : x;
+          a[u] = sw ? x : y;
+        }
+      } else {
+        const int m = j / E;
+        const bool lower = (lane & m) == 0;
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+          const unsigned long long x = a[t];
+          const unsigned long long y = __shfl_xor_sync(kFullM, x, m);
+          const bool asc = ((lane * E + t) & k) == 0;
+          const bool lo = x < y;
+          a[t] = (asc == lower) ? (lo ? x : y) : (lo ? y : x);
+        }
+      }
+    }
+  }
+}
+
+// Sorts the L <= 32*E entries at ri/rv by column (distinct columns): keys (column, old
+// position) sorted in registers, then the values gathered from their old positions.
+template <typename T, int E>
+__device__ __forceinline__ void warp_sort_row(int *ri, T *rv, int L, int lane) {
+  unsigned long long a[E];
+#pragma unroll
+  for (int t = 0; t < E; ++t) {
+    const int s = lane * E + t;
+    a[t] = s < L ? ((unsigned long long)(unsigned)ri[s] << 32) | (unsigned)s : ~0ull;
+  }
+  warp_bitonic<E>(a, lane);
+  T v[E];
+#pragma unroll
+  for (int t = 0; t < E; ++t) v[t] = lane * E + t < L ? rv[(unsigned)a[t]] : T(0);
+  __syncwarp();  // every old value is read before any is overwritten
+#pragma unroll
+  for (int t = 0; t < E; ++t) {
+    const int s = lane * E + t;
+    if (s < L) {
+      ri[s] = (int)(a[t] >> 32);
+      rv[s] = v[t];
+    }
+  }
+  __syncwarp();
+}
+
+// rowstat[i] = (diagonal, sum of squares) of the full row i, one warp.
+template <typename T>
+__device__ __forceinline__ void row_stat_warp(const int *ri, const T *rv, int total, int i, int lane,
+                                              double2 *rowstat) {
+  double d = 0.0, f = 0.0;
+  for (int s = lane; s < total; s += 32) {
+    const double v = (double)rv[s];
+    if (ri[s] == i) d += v;
+    f = fma(v, v, f);
+  }
+  d = warp_sum_d(d);
+  f = warp_sum_d(f);
+  if (lane == 0) rowstat[i] = make_double2(d, f);
+  __syncwarp();
+}
+
 // Sorts row i's lower part (positions 0 .. L-1) by column and records rowstat[i].  One
-// warp per row (bitonic in shared memory for L <= kSortWarpMax); longer lower parts are
-// left for the CTA pass (row flagged in `longs`).
+// warp per row, in registers for L <= kSortWarpMax; longer lower parts are left for the
+// passes over the flagged rows (list `longs`).
 template <typename T>
 __global__ void __launch_bounds__(kSymThreads) mirror_sort_kernel(EllOut<T> Out, BatchView bv,
                                                                  const int *__restrict__ cnt,
                                                                  double2 *__restrict__ rowstat,
                                                                  int *__restrict__ longs, int *__restrict__ nlong) {
-  __shared__ int sk[kSymThreads / 32][kSortWarpMax];
-  __shared__ T sv[kSymThreads / 32][kSortWarpMax];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int warps = gridDim.x * (kSymThreads / 32);
   for (int i = blockIdx.x * (kSymThreads / 32) + wid; i < Out.n; i += warps) {
@@ -156,47 +237,40 @@ __global__ void __launch_bounds__(kSymThreads) mirror_sort_kernel(EllOut<T> Out,
       if (lane == 0) longs[atomicAdd(nlong, 1)] = i;
       continue;
     }
-    if (L > 1) {
-      int P = 2;
-      while (P < L) P <<= 1;
-      for (int s = lane; s < P; s += 32) {
-        sk[wid][s] = s < L ? ri[s] : INT_MAX;
-        sv[wid][s] = s < L ? rv[s] : T(0);
-      }
-      __syncwarp();
-      for (int k = 2; k <= P; k <<= 1)
-        for (int jj = k >> 1; jj > 0; jj >>= 1) {
-          for (int e = lane; e < (P >> 1); e += 32) {
-            const int a = ((e & ~(jj - 1)) << 1) | (e & (jj - 1));
-            const int b = a + jj;
-            const int x = sk[wid][a], y = sk[wid][b];
-            if ((x > y) == ((a & k) == 0)) {
-              sk[wid][a] = y; sk[wid][b] = x;
-              const T t = sv[wid][a]; sv[wid][a] = sv[wid][b]; sv[wid][b] = t;
-            }
-          }
-          __syncwarp();
-        }
-      for (int s = lane; s < L; s += 32) {
-        ri[s] = sk[wid][s];
-        rv[s] = sv[wid][s];
-      }
-      __syncwarp();
+    if (L > 128) {
+      warp_sort_row<T, 8>(ri, rv, L, lane);
+    } else if (L > 32) {
+      if (L > 64) warp_sort_row<T, 4>(ri, rv, L, lane);
+      else warp_sort_row<T, 2>(ri, rv, L, lane);
+    } else if (L > 1) {
+      warp_sort_row<T, 1>(ri, rv, L, lane);
     }
-    double d = 0.0, f = 0.0;
-    for (int s = lane; s < total; s += 32) {
-      const double v = (double)rv[s];
-      if (ri[s] == i) d += v;
-      f = fma(v, v, f);
-    }
-    d = warp_sum_d(d);
-    f = warp_sum_d(f);
-    if (lane == 0) rowstat[i] = make_double2(d, f);
-    __syncwarp();
+    row_stat_warp(ri, rv, total, i, lane, rowstat);
   }
 }
 
-// Long lower parts: one CTA per row.  Up to kSortCtaMax entries, bitonic in shared memory;
+// Flagged rows with kSortWarpMax < L <= kSortMidMax: one warp per row, 16 keys per lane
+// (a kernel of its own so that the registers this takes do not limit the common pass).
+template <typename T>
+__global__ void __launch_bounds__(kSymThreads) mirror_sort_mid_kernel(EllOut<T> Out, const int *__restrict__ cnt,
+                                                                     double2 *__restrict__ rowstat,
+                                                                     const int *__restrict__ longs,
+                                                                     const int *__restrict__ nlong) {
+  const int nl = *nlong;
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (kSymThreads / 32);
+  for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nl; q += warps) {
+    const int i = longs[q];
+    const int L = cnt[i];
+    if (L > kSortMidMax) continue;
+    int *ri = Out.idx + (size_t)i * Out.w;
+    T *rv = Out.val + (size_t)i * Out.w;
+    warp_sort_row<T, 16>(ri, rv, L, lane);
+    row_stat_warp(ri, rv, Out.nnz[i], i, lane, rowstat);
+  }
+}
+
+// Long lower parts (L > kSortMidMax): one CTA per row.  Up to kSortCtaMax entries, bitonic in shared memory;
 // beyond, each entry's rank (count of smaller columns) places it in the row's slots of U,
 // free once the U part has been placed, and the sorted part is copied back.
 template <typename T>
@@ -214,6 +288,7 @@ __global__ void __launch_bounds__(kSymThreads) mirror_sort_long_kernel(EllOut<T>
   for (int q = blockIdx.x; q < nl; q += gridDim.x) {
     const int i = longs[q];
     const int L = cnt[i];
+    if (L <= kSortMidMax) continue;  // the same for the whole CTA: sorted by the warp pass
     const int total = Out.nnz[i];
     int *ri = Out.idx + (size_t)i * Out.w;
     T *rv = Out.val + (size_t)i * Out.w;
@@ -284,9 +359,11 @@ __global__ void __launch_bounds__(kSymThreads) mirror_sort_long_kernel(EllOut<T>
 
 int upper_start_async(const ellpack_t *X, int *tp, int *tpd, cudaStream_t s) {
   const int g = grid_rows_sym(X->n);
+  prof_begin(SP2_PROF_SYMM, s);
   if (X->dtype == SP2_F64) upper_start_kernel<double><<<g, kSymThreads, 0, s>>>(view<double>(X), tp, tpd);
   else upper_start_kernel<float><<<g, kSymThreads, 0, s>>>(view<float>(X), tp, tpd);
   note_launch();
+  prof_end(SP2_PROF_SYMM, s);
   SP2_CUDA(cudaGetLastError());
   return SP2_OK;
 }
@@ -297,6 +374,7 @@ static int mirror_t(const ellpack_t *U, ellpack_t *Out, const BatchView &bv, int
   const int n = U->n;
   // work: cnt[n], cursor[n], nlong[1] (zeroed here), longs[n]
   int *cnt = work, *cursor = work + n, *nlong = work + 2 * n, *longs = work + 2 * n + 1;
+  prof_begin(SP2_PROF_SYMM, s);
   SP2_CUDA(cudaMemsetAsync(work, 0, sizeof(int) * (2 * (size_t)n + 1), s));
   const int g = grid_rows_sym(n);
   mirror_count_kernel<T><<<g, kSymThreads, 0, s>>>(view<T>(U), bv, cnt);
@@ -304,6 +382,8 @@ static int mirror_t(const ellpack_t *U, ellpack_t *Out, const BatchView &bv, int
   mirror_sort_kernel<T><<<g, kSymThreads, 0, s>>>(outview<T>(Out), bv, cnt, rowstat, longs, nlong);
   note_launch();
   note_launch();
+  note_launch();
+  mirror_sort_mid_kernel<T><<<num_sms() * 2, kSymThreads, 0, s>>>(outview<T>(Out), cnt, rowstat, longs, nlong);
   note_launch();
   constexpr int smem = kSortCtaMax * (int)(sizeof(int) + sizeof(T));
   static bool attr[64] = {false};
@@ -317,6 +397,7 @@ static int mirror_t(const ellpack_t *U, ellpack_t *Out, const BatchView &bv, int
   mirror_sort_long_kernel<T><<<num_sms(), kSymThreads, smem, s>>>(outview<T>(Out), outview<T>(U), cnt, rowstat, longs,
                                                                    nlong);
   note_launch();
+  prof_end(SP2_PROF_SYMM, s);
   SP2_CUDA(cudaGetLastError());
   return SP2_OK;
 }

@@ -49,7 +49,7 @@ class sp2_options(ctypes.Structure):
                 ("n_fp64_tail", ctypes.c_int32), ("max_width", ctypes.c_int32), ("spgemm_path", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("switch_tol", ctypes.c_double), ("graph", ctypes.c_int32),
                 ("sizing", ctypes.c_int32), ("predictor", ctypes.POINTER(nnzpred_t)), ("stall_arm", ctypes.c_double),
-                ("symmetric", ctypes.c_int32)]
+                ("symmetric", ctypes.c_int32), ("stall_ratio", ctypes.c_double)]
 
 
 class sp2_stats(ctypes.Structure):
@@ -73,8 +73,8 @@ class sp2_step_info(ctypes.Structure):
                 ("spgemm_path_used", ctypes.c_int32), ("symmetric", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
-SP2_PROF_CLASSES = 4
-PROF_NAMES = ("spgemm", "large_rows", "reduce", "other")
+SP2_PROF_CLASSES = 5
+PROF_NAMES = ("spgemm", "large_rows", "reduce", "other", "symmetry")
 
 
 class sp2_profile(ctypes.Structure):

@@ -58,3 +58,4 @@ def test_options_defaults(libpath):
     from paper_2102_08505_gb300 import sp2ell
     o = sp2ell.sp2_options_default()
     assert (o.precision, o.max_iter, o.stall_rule, o.n_fp64_tail, o.tau) == (0, 100, 1, 2, 1e-5)
+    assert (o.stall_arm, o.stall_ratio, o.symmetric) == (0.1, 1.0, 1)

@@ -86,6 +86,24 @@ def test_batched_regrows_when_width_is_too_small(gpu):
         assert np.linalg.norm(dense_D(D) - Do.to_dense()) / np.sqrt(H.n) < 1e-10
 
 
+@pytest.mark.parametrize("ratio", [1.0, 0.5])
+def test_batched_stall_rule_matches_oracle(gpu, ratio):
+    """Gapless banded chains at tau = 1e-5 stop by the stall rule (ratio 1 and 0.5): the
+    same iterations, status and branches as the oracle, matrix by matrix."""
+    S = gpu
+    tau, tol = 1e-5, 1e-14
+    mats = [O.Ell(*I.banded(256, band=8, seed=1, delta=0.0)), O.Ell(*I.banded(384, band=6, seed=2, delta=0.0))]
+    Hs = [S.Ellpack.from_numpy(m.idx, m.val, m.nnz) for m in mats]
+    noccs = [m.n // 2 for m in mats]
+    Ds, sts = S.sp2_purify_batched(Hs, noccs, tol, S.sp2_options_default(tau=tau, max_iter=60, stall_ratio=ratio),
+                                   allow_notconv=True)
+    for m, H, D, st in zip(range(len(mats)), mats, Ds, sts):
+        Do, so = O.sp2(H, noccs[m], tol, tau, max_iter=60, stall_ratio=ratio)
+        assert so["status"] == "stalled", m
+        assert (st["iterations"], st["status"], st["branch"]) == (so["iterations"], so["status"], so["branch"]), m
+        assert np.abs(dense_D(D) - Do.to_dense()).max() < 1e-8, m
+
+
 def test_batched_argument_errors(gpu):
     S = gpu
     m = batch()[0]
@@ -96,6 +114,9 @@ def test_batched_argument_errors(gpu):
     F = S.Ellpack.from_numpy(m.idx, m.val, m.nnz, S.SP2_F32)
     with pytest.raises(S.Sp2Error) as e:
         S.sp2_purify_batched([F], [10.0], 1e-10)
+    assert e.value.code == S.SP2E_ARG
+    with pytest.raises(S.Sp2Error) as e:
+        S.sp2_purify_batched([H], [10.0], 1e-10, S.sp2_options_default(stall_ratio=0.0))
     assert e.value.code == S.SP2E_ARG
 
 

@@ -128,21 +128,24 @@ def test_sp2_errors(gpu):
     assert e.value.code == S.SP2E_NOTCONV
 
 
-@pytest.mark.parametrize("arm", [1e-300, 0.1, 1e300])
-def test_sp2_stall_arm_matches_oracle(gpu, arm):
-    """Stall-rule arming threshold variants on the gapless banded Hamiltonian (never armed,
-    the reading's 0.1, armed from the start): same iterations, status and branches as the
-    oracle."""
+@pytest.mark.parametrize("arm,ratio", [(1e-300, 1.0), (0.1, 1.0), (1e300, 1.0), (0.1, 0.9), (0.1, 0.5)])
+def test_sp2_stall_arm_matches_oracle(gpu, arm, ratio):
+    """Stall-rule variants on the gapless banded Hamiltonian (arming threshold: never armed,
+    the reading's 0.1, armed from the start; ratio 1 and below): same iterations, status
+    and branches as the oracle."""
     S = gpu
     n = 512
     H = ell(I.banded(n, band=8, seed=1, delta=0.0))
-    Do, so = O.sp2(H, n // 2, 1e-14, 1e-5, max_iter=60, stall_arm=arm)
-    D, sg = S.sp2_purify(dev(S, H), n // 2, 1e-14, S.sp2_options_default(tau=1e-5, max_iter=60, stall_arm=arm),
+    Do, so = O.sp2(H, n // 2, 1e-14, 1e-5, max_iter=60, stall_arm=arm, stall_ratio=ratio)
+    D, sg = S.sp2_purify(dev(S, H), n // 2, 1e-14,
+                         S.sp2_options_default(tau=1e-5, max_iter=60, stall_arm=arm, stall_ratio=ratio),
                          allow_notconv=True)
     assert sg["iterations"] == so["iterations"] and sg["status"] == so["status"] and sg["branch"] == so["branch"]
     assert np.abs(dense_D(D) - Do.to_dense()).max() < 1e-8
     with pytest.raises(S.Sp2Error):
         S.sp2_purify(dev(S, H), n // 2, 1e-10, S.sp2_options_default(stall_arm=0.0))
+    with pytest.raises(S.Sp2Error):
+        S.sp2_purify(dev(S, H), n // 2, 1e-10, S.sp2_options_default(stall_ratio=1.5))
 
 
 def test_sp2_symmetric_mode_is_bitwise_the_full_product(gpu):

@@ -267,8 +267,8 @@ def test_x0(gpu, tau):
 @pytest.mark.parametrize("first_pass", [0, 1, 2, 3, 4, 7, 8, 11])
 @pytest.mark.parametrize("fp32", [False, True])
 def test_first_pass_variants(gpu, first_pass, fp32):
-    """Every first-pass variant (column blocks with 1, 2, 4 warps per row, the two-step
-    and the chunk-stream one-warp variants, a per-warp hash table) on one SP2 step of a
+    """Every first-pass variant (column blocks with 1, 2, 4 warps per row and the compact
+    2-warp form, the two-step one-warp variant and its compact form, a per-warp hash table) on one SP2 step of a
     gapped tight-binding X; a second run is bitwise identical."""
     S = gpu
     n = 5000

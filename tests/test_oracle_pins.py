@@ -330,3 +330,33 @@ def test_stall_arm_threshold_variants():
     e = sa["err"]
     first = next(k for k in range(2, len(e)) if e[k] >= e[k - 2])
     assert sa["iterations"] == first
+
+
+def test_stall_ratio_variants():
+    """The stall rule's ratio on the gapless banded Hamiltonian at tau = 1e-5 (its error
+    settles at a floor): ratio 1 is the default run; with a smaller ratio the rule fires at
+    the first armed n with err_n >= ratio * err_{n-2} of the unstopped run's error sequence,
+    never later than with a larger ratio; the iterates before the stop are the unstopped
+    run's."""
+    H = ell(I.banded(256, band=8, seed=1, delta=0.0))
+    D0, s0 = O.sp2(H, 128, 1e-14, 1e-5, max_iter=60, stall=False)
+    Dd, sd = O.sp2(H, 128, 1e-14, 1e-5, max_iter=60)
+    D1, s1 = O.sp2(H, 128, 1e-14, 1e-5, max_iter=60, stall_ratio=1.0)
+    assert s1["iterations"] == sd["iterations"] and np.array_equal(D1.to_dense(), Dd.to_dense())
+    e = s0["err"]
+    armed_from = next(k for k in range(len(e)) if 256 * e[k] < 0.1)
+    last = 10 ** 9
+    for ratio in (1.0, 0.99, 0.9, 0.5):
+        Dr, sr = O.sp2(H, 128, 1e-14, 1e-5, max_iter=60, stall_ratio=ratio)
+        want = next((k for k in range(max(2, armed_from), len(e)) if e[k] >= ratio * e[k - 2]), None)
+        if want is None:
+            assert sr["status"] == "max_iter"
+            continue
+        assert sr["status"] == "stalled" and sr["iterations"] == want
+        assert np.array_equal(sr["err"], e[:want + 1]) and sr["branch"] == s0["branch"][:want]
+        assert want <= last
+        last = want
+    with pytest.raises(ValueError):
+        O.sp2(H, 128, 1e-14, 1e-5, max_iter=5, stall_ratio=0.0)
+    with pytest.raises(ValueError):
+        O.sp2(H, 128, 1e-14, 1e-5, max_iter=5, stall_ratio=1.5)

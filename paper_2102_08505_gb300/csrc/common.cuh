@@ -108,6 +108,46 @@ struct SpgemmCtl {
   int n_heavy;      // rows of the first list deferred for the length of their row of A
 };
 
+// Bitonic network over the 32*E keys a warp holds, E per lane in lane-major order
+// (element lane*E + t): exchanges at distances below E stay in a lane's registers, the
+// others pair lanes lane ^ (j / E) by shuffle.  Ascending on exit.
+template <typename K, int E>
+__device__ __forceinline__ void warp_bitonic(K (&a)[E], int lane) {
+  static_assert(E == 1 || E == 2 || E == 4 || E == 8 || E == 16, "E: 1, 2, 4, 8 or 16 keys per lane");
+  constexpr int LOGP = 5 + (E >= 2) + (E >= 4) + (E >= 8) + (E >= 16);
+#pragma unroll
+  for (int lk = 1; lk <= LOGP; ++lk) {
+    const int k = 1 << lk;
+#pragma unroll
+    for (int lj = lk - 1; lj >= 0; --lj) {
+      const int j = 1 << lj;
+      if (j < E) {
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+          if (t & j) continue;
+          const int u = t | j;
+          const bool asc = ((lane * E + t) & k) == 0;
+          const K x = a[t], y = a[u];
+          const bool sw = asc ? (x > y) : (x < y);
+          a[t] = sw ? y : x;
+          a[u] = sw ? x : y;
+        }
+      } else {
+        const int m = j / E;
+        const bool lower = (lane & m) == 0;
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+          const K x = a[t];
+          const K y = __shfl_xor_sync(0xffffffffu, x, m);
+          const bool asc = ((lane * E + t) & k) == 0;
+          const bool lo = x < y;
+          a[t] = (asc == lower) ? (lo ? x : y) : (lo ? y : x);
+        }
+      }
+    }
+  }
+}
+
 // rowstat[r] = {diagonal value, sum of squares} of output row r (post-threshold).
 // Reduces rowstat and out.nnz over n rows, copies ctl counters, into *res (device).
 void launch_reduce_rows(const double2 *rowstat, const int *nnz, int n, const SpgemmCtl *ctl,

@@ -462,6 +462,48 @@ __device__ __forceinline__ int group_block(unsigned *gtab, int *nblk, unsigned g
   return -1;
 }
 
+// Sorts the ng used entries at the front of a group table ascending (by group: the group
+// sits in the high bits, distinct per entry).  One warp: in registers for ng <= 256 (REGS),
+// else a bitonic network in the table itself, padded to a power of two (ng <= the table size).
+template <int E>
+__device__ __forceinline__ void sort_table_regs(unsigned *tab, int ng, int lane) {
+  unsigned a[E];
+#pragma unroll
+  for (int t = 0; t < E; ++t) a[t] = lane * E + t < ng ? tab[lane * E + t] : 0xFFFFFFFFu;
+  warp_bitonic<unsigned, E>(a, lane);
+  __syncwarp();  // every entry is read before any is overwritten
+#pragma unroll
+  for (int t = 0; t < E; ++t)
+    if (lane * E + t < ng) tab[lane * E + t] = a[t];
+  __syncwarp();
+}
+// REGS = false: always the in-table network (smaller code: the multi-warp block kernel
+// measured faster without the unrolled register networks; the one-warp kernel with them).
+template <bool REGS>
+__device__ __forceinline__ void sort_group_table(unsigned *tab, int ng, int lane) {
+  __syncwarp();  // the entries were just written by other lanes
+  if (ng <= 1) return;
+  if (REGS) {
+    if (ng <= 32) { sort_table_regs<1>(tab, ng, lane); return; }
+    if (ng <= 64) { sort_table_regs<2>(tab, ng, lane); return; }
+    if (ng <= 128) { sort_table_regs<4>(tab, ng, lane); return; }
+    if (ng <= 256) { sort_table_regs<8>(tab, ng, lane); return; }
+  }
+  int P = 32;
+  while (P < ng) P <<= 1;
+  for (int s2 = ng + lane; s2 < P; s2 += 32) tab[s2] = 0xFFFFFFFFu;
+  __syncwarp();
+  for (int k = 2; k <= P; k <<= 1)
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int e = lane; e < (P >> 1); e += 32) {
+        const int i = ((e & ~(jj - 1)) << 1) | (e & (jj - 1));
+        const unsigned x = tab[i], y = tab[i + jj];
+        if ((x > y) == ((i & k) == 0)) { tab[i] = y; tab[i + jj] = x; }
+      }
+      __syncwarp();
+    }
+}
+
 // Barrier of the R warps of a row group (named barrier grp + 1; the warp itself when
 // R == 1).  group_sync_or also returns the OR of `pred` over the group's threads, taken
 // by the barrier instruction itself, so every warp sees the same value.
@@ -592,7 +634,7 @@ __global__ void __launch_bounds__(BlockGeo<T, R, SZ>::WARPS * 32, 1)
     };
     // accumulate one step from registers, body instantiated per number NU of occupied
     // register slots of this warp (warp-uniform switch: empty slots cost nothing)
-    auto step_nu = [&](auto nu_c, const int (&jr)[QW], const T (&vr)[QW], T a) {
+    auto step_nu = [&](auto nu_c, const int (&jr)[QW], const T (&vr)[QW], T a, const unsigned (&hint)[QW]) {
       constexpr int NU = decltype(nu_c)::value;
       int sl[NU];
       unsigned miss = 0;
@@ -601,7 +643,10 @@ __global__ void __launch_bounds__(BlockGeo<T, R, SZ>::WARPS * 32, 1)
         sl[u] = -1;
         const unsigned g = (unsigned)jr[u] >> GSH;
         if ((unsigned)jr[u] < (unsigned)ncol) {
-          const unsigned e = ((volatile unsigned *)gtab)[ghash<Geo::LOG2G>(g)];
+          // the entry read before the last barrier, if it already holds g (entries are
+          // never changed once set), else a fresh read
+          unsigned e = hint[u];
+          if ((e >> 8) != g) e = ((volatile unsigned *)gtab)[ghash<Geo::LOG2G>(g)];
           if ((e >> 8) == g) sl[u] = (int)(e & 0xFFu) * GW + (jr[u] & (GW - 1));
           else miss |= 1u << u;
         }
@@ -638,30 +683,44 @@ __global__ void __launch_bounds__(BlockGeo<T, R, SZ>::WARPS * 32, 1)
           vals[sl[u]] = fmadd(a, vr[u], o);
         }
     };
-    auto step = [&](const int (&jr)[QW], const T (&vr)[QW], int nb, T a, const int *ri, const T *rv) {
+    // hints: the table entries at the first probe of the next step's register slots, read
+    // before this step's barrier so that their latency overlaps it
+    unsigned hint[QW];
+#pragma unroll
+    for (int u = 0; u < QW; ++u) hint[u] = 0xFFFFFFFFu;
+    auto step = [&](const int (&jr)[QW], const T (&vr)[QW], int nb, T a, const int *ri, const T *rv,
+                    const int (&jn)[QW]) {
       const int mine = nb > 32 * wr ? (nb - 32 * wr + SPAN - 1) / SPAN : 0;  // slots of this warp
       const int nu = min(mine, QW);
       switch (nu) {
         case 0: break;
-        case 1: step_nu(std::integral_constant<int, 1>{}, jr, vr, a); break;
-        case 2: step_nu(std::integral_constant<int, (QW >= 2 ? 2 : QW)>{}, jr, vr, a); break;
-        case 3: step_nu(std::integral_constant<int, (QW >= 3 ? 3 : QW)>{}, jr, vr, a); break;
-        case 4: step_nu(std::integral_constant<int, (QW >= 4 ? 4 : QW)>{}, jr, vr, a); break;
-        case 5: step_nu(std::integral_constant<int, (QW >= 5 ? 5 : QW)>{}, jr, vr, a); break;
-        case 6: step_nu(std::integral_constant<int, (QW >= 6 ? 6 : QW)>{}, jr, vr, a); break;
-        case 7: step_nu(std::integral_constant<int, (QW >= 7 ? 7 : QW)>{}, jr, vr, a); break;
-        default: step_nu(std::integral_constant<int, QW>{}, jr, vr, a); break;
+        case 1: step_nu(std::integral_constant<int, 1>{}, jr, vr, a, hint); break;
+        case 2: step_nu(std::integral_constant<int, (QW >= 2 ? 2 : QW)>{}, jr, vr, a, hint); break;
+        case 3: step_nu(std::integral_constant<int, (QW >= 3 ? 3 : QW)>{}, jr, vr, a, hint); break;
+        case 4: step_nu(std::integral_constant<int, (QW >= 4 ? 4 : QW)>{}, jr, vr, a, hint); break;
+        case 5: step_nu(std::integral_constant<int, (QW >= 5 ? 5 : QW)>{}, jr, vr, a, hint); break;
+        case 6: step_nu(std::integral_constant<int, (QW >= 6 ? 6 : QW)>{}, jr, vr, a, hint); break;
+        case 7: step_nu(std::integral_constant<int, (QW >= 7 ? 7 : QW)>{}, jr, vr, a, hint); break;
+        default: step_nu(std::integral_constant<int, QW>{}, jr, vr, a, hint); break;
       }
       if (nb > SPAN * QW) {  // rows longer than the registers: same phases, from memory
+        unsigned none[QW];
+#pragma unroll
+        for (int u = 0; u < QW; ++u) none[u] = 0xFFFFFFFFu;
         for (int q0 = SPAN * QW; q0 < nb; q0 += SPAN) {
           const int q = q0 + gt;
           int jt[QW];
           T vt[QW];
           jt[0] = q < nb ? __ldg(ri + q) : -1;
           vt[0] = q < nb ? __ldg(rv + q) : T(0);
-          step_nu(std::integral_constant<int, 1>{}, jt, vt, a);
+          step_nu(std::integral_constant<int, 1>{}, jt, vt, a, none);
         }
       }
+#pragma unroll
+      for (int u = 0; u < QW; ++u)
+        hint[u] = (unsigned)jn[u] < (unsigned)ncol
+                      ? ((volatile unsigned *)gtab)[ghash<Geo::LOG2G>((unsigned)jn[u] >> GSH)]
+                      : 0xFFFFFFFFu;
       aborted = group_sync_or<R>(grp, aborted);  // orders this step's updates before the next step's
     };
 
@@ -679,7 +738,7 @@ __global__ void __launch_bounds__(BlockGeo<T, R, SZ>::WARPS * 32, 1)
       fetch(ci, cv, nc, j2, v2);
       if (na > 0) fetch_step(0, j0, v0, nb0, a0, k0);
       if (na > 1) fetch_step(1, j1, v1, nb1, a1, k1);
-      step(j2, v2, nc, beta_r, ci, cv);
+      step(j2, v2, nc, beta_r, ci, cv, j0);
     } else {
       if (na > 0) fetch_step(0, j0, v0, nb0, a0, k0);
       if (na > 1) fetch_step(1, j1, v1, nb1, a1, k1);
@@ -691,13 +750,13 @@ __global__ void __launch_bounds__(BlockGeo<T, R, SZ>::WARPS * 32, 1)
         load_chunk(cbase + 32, nk_, nnb, na_, nst);
       }
       if (t + 2 < na) fetch_step(t + 2, j2, v2, nb2, a2, k2);
-      step(j0, v0, nb0, a0, B.idx + k0, B.val + k0);
+      step(j0, v0, nb0, a0, B.idx + k0, B.val + k0, j1);
       if (t + 1 >= na || aborted) break;
       if (t + 3 < na) fetch_step(t + 3, j0, v0, nb0, a0, k0);
-      step(j1, v1, nb1, a1, B.idx + k1, B.val + k1);
+      step(j1, v1, nb1, a1, B.idx + k1, B.val + k1, j2);
       if (t + 2 >= na || aborted) break;
       if (t + 4 < na) fetch_step(t + 4, j1, v1, nb1, a1, k1);
-      step(j2, v2, nb2, a2, B.idx + k2, B.val + k2);
+      step(j2, v2, nb2, a2, B.idx + k2, B.val + k2, j0);
     }
     if (aborted) {
       if (gt == 0) {
@@ -718,21 +777,7 @@ __global__ void __launch_bounds__(BlockGeo<T, R, SZ>::WARPS * 32, 1)
         if (used) gtab[ng + __popc(m & lt)] = e;
         ng += __popc(m);
       }
-      {
-        int P = 32;
-        while (P < ng) P <<= 1;
-        for (int s2 = ng + lane; s2 < P; s2 += 32) gtab[s2] = 0xFFFFFFFFu;
-        __syncwarp();
-        for (int k = 2; k <= P; k <<= 1)
-          for (int jj = k >> 1; jj > 0; jj >>= 1) {
-            for (int e = lane; e < (P >> 1); e += 32) {
-              const int i = ((e & ~(jj - 1)) << 1) | (e & (jj - 1));
-              const unsigned x = gtab[i], y = gtab[i + jj];
-              if ((x > y) == ((i & k) == 0)) { gtab[i] = y; gtab[i + jj] = x; }
-            }
-            __syncwarp();
-          }
-      }
+      sort_group_table<false>(gtab, ng, lane);
       // walk the groups in column order: 32 / GW groups per pass, lane -> column
       const auto tb = mag_bits(tau);
       int nk = 0;
@@ -1014,21 +1059,7 @@ __global__ void __launch_bounds__(BlockGeo<T, 1, SZ>::WARPS * 32, 1)
       if (used) gtab[ng + __popc(m & lt)] = e;
       ng += __popc(m);
     }
-    {
-      int P = 32;
-      while (P < ng) P <<= 1;
-      for (int s2 = ng + lane; s2 < P; s2 += 32) gtab[s2] = 0xFFFFFFFFu;
-      __syncwarp();
-      for (int k = 2; k <= P; k <<= 1)
-        for (int jj = k >> 1; jj > 0; jj >>= 1) {
-          for (int e = lane; e < (P >> 1); e += 32) {
-            const int i = ((e & ~(jj - 1)) << 1) | (e & (jj - 1));
-            const unsigned x = gtab[i], y = gtab[i + jj];
-            if ((x > y) == ((i & k) == 0)) { gtab[i] = y; gtab[i + jj] = x; }
-          }
-          __syncwarp();
-        }
-    }
+    sort_group_table<true>(gtab, ng, lane);
     const auto tb = mag_bits(tau);
     int nk = 0;
     double dsum = 0.0, fsum = 0.0;

@@ -131,46 +131,6 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// Bitonic network over the 32*E keys a warp holds, E per lane in lane-major order
-// (element lane*E + t): exchanges at distances below E stay in a lane's registers, the
-// others pair lanes lane ^ (j / E) by shuffle.  Ascending on exit.
-template <int E>
-__device__ __forceinline__ void warp_bitonic(unsigned long long (&a)[E], int lane) {
-  static_assert(E == 1 || E == 2 || E == 4 || E == 8 || E == 16, "E: 1, 2, 4, 8 or 16 keys per lane");
-  constexpr int LOGP = 5 + (E >= 2) + (E >= 4) + (E >= 8) + (E >= 16);
-#pragma unroll
-  for (int lk = 1; lk <= LOGP; ++lk) {
-    const int k = 1 << lk;
-#pragma unroll
-    for (int lj = lk - 1; lj >= 0; --lj) {
-      const int j = 1 << lj;
-      if (j < E) {
-#pragma unroll
-        for (int t = 0; t < E; ++t) {
-          if (t & j) continue;
-          const int u = t | j;
-          const bool asc = ((lane * E + t) & k) == 0;
-          const unsigned long long x = a[t], y = a[u];
-          const bool sw = asc ? (x > y) : (x < y);
-          a[t] = sw ? y : x;
-          a[u] = sw ? x : y;
-        }
-      } else {
-        const int m = j / E;
-        const bool lower = (lane & m) == 0;
-#pragma unroll
-        for (int t = 0; t < E; ++t) {
-          const unsigned long long x = a[t];
-          const unsigned long long y = __shfl_xor_sync(kFullM, x, m);
-          const bool asc = ((lane * E + t) & k) == 0;
-          const bool lo = x < y;
-          a[t] = (asc == lower) ? (lo ? x : y) : (lo ? y : x);
-        }
-      }
-    }
-  }
-}
-
 // Sorts the L <= 32*E entries at ri/rv by column (distinct columns): keys (column, old
 // position) sorted in registers, then the values gathered from their old positions.
 template <typename T, int E>
@@ -181,7 +141,7 @@ __device__ __forceinline__ void warp_sort_row(int *ri, T *rv, int L, int lane) {
     const int s = lane * E + t;
     a[t] = s < L ? ((unsigned long long)(unsigned)ri[s] << 32) | (unsigned)s : ~0ull;
   }
-  warp_bitonic<E>(a, lane);
+  warp_bitonic<unsigned long long, E>(a, lane);
   T v[E];
 #pragma unroll
   for (int t = 0; t < E; ++t) v[t] = lane * E + t < L ? rv[(unsigned)a[t]] : T(0);

@@ -59,3 +59,31 @@ def test_options_defaults(libpath):
     o = sp2ell.sp2_options_default()
     assert (o.precision, o.max_iter, o.stall_rule, o.n_fp64_tail, o.tau) == (0, 100, 1, 2, 1e-5)
     assert (o.stall_arm, o.stall_ratio, o.symmetric) == (0.1, 1.0, 1)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets of its C
+    declaration in include/sp2ell.h (a C program built against the header prints them)."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_2102_08505_gb300 import sp2ell
+    structs = [sp2ell.ellpack_t, sp2ell.nnzpred_t, sp2ell.sp2_options, sp2ell.sp2_stats, sp2ell.sp2_step_info,
+               sp2ell.sp2_profile]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "sp2ell.h"', 'int main(void) {']
+    for st in structs:
+        c = st.__name__
+        lines.append('  printf("%s %%zu\\n", sizeof(%s));' % (c, c))
+        for f in st._fields_:
+            lines.append('  printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (c, f[0], c, f[0]))
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_layout = dict(l.split() for l in out if l.strip())
+    for st in structs:
+        c = st.__name__
+        assert int(c_layout[c]) == ctypes.sizeof(st), c
+        for f in st._fields_:
+            assert int(c_layout["%s.%s" % (c, f[0])]) == getattr(st, f[0]).offset, (c, f[0])

@@ -437,7 +437,10 @@ typedef struct sp2_step_info {
   int32_t max_row_nnz;     /* out: longest row of X' */
   int32_t required_width;  /* out: longest post-threshold row (valid on overflow too) */
   int32_t spgemm_path;     /* in: SpGEMM first pass, as sp2_options.spgemm_path */
-  int32_t rows_deferred;   /* out: rows the first pass handed to the 2^14-slot table */
+  int32_t rows_deferred;   /* out: rows the first pass handed to the deferred-row bins (the
+                              shared-memory window, then the 2^14-slot table): rows that
+                              outgrew its accumulator, and with the one-warp pass rows of X
+                              longer than 512 entries */
   int32_t rows_dense;      /* out: rows handed further to the dense global-row pass */
   int32_t spgemm_path_used; /* out: the first-pass variant that ran (the tuner's choice
                                for SP2_PATH_TUNED) */

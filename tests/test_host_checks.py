@@ -106,3 +106,41 @@ def test_batched_rejects_bad_counts_and_occupations(S):
     assert rc == S.SP2E_ARG and b"count" in S.lib.sp2_last_error_string()
     rc = S.lib.sp2_purify_batched(Hs, (ctypes.c_double * 2)(4.0, 16.0), 2, 1e-10, None, Ds, None, None)
     assert rc == S.SP2E_ARG and b"nocc[1]" in S.lib.sp2_last_error_string()
+
+
+def test_multiply_add_and_step_reject_bad_arguments(S):
+    """ellpack_multiply, ellpack_add and sp2_step: size, dtype, aliasing, tolerance, scalar and
+    path errors come back as SP2E_ARG before any device call."""
+    keep = []
+    A, B, C = fake_matrix(S, keep=keep), fake_matrix(S, keep=keep), fake_matrix(S, keep=keep)
+    big = fake_matrix(S, n=16, keep=keep)
+    f32 = fake_matrix(S, keep=keep)
+    f32.dtype = S.SP2_F32
+    w = ctypes.c_int32()
+    mul = lambda a, b, c, al=1.0, be=0.0, tau=0.0: S.lib.sp2_last_error_string() if S.lib.ellpack_multiply(
+        ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), al, be, tau, None, ctypes.byref(w)) == S.SP2E_ARG else None
+    assert b"sizes differ" in mul(A, B, big)
+    assert b"dtypes differ" in mul(A, B, f32)
+    assert b"aliases" in mul(A, B, A)
+    assert b"aliases" in mul(A, B, B)
+    assert b"tau" in mul(A, B, C, tau=-1.0)
+    assert b"not finite" in mul(A, B, C, al=float("inf"))
+    add = lambda a, b, al=1.0, be=1.0, tau=0.0: S.lib.sp2_last_error_string() if S.lib.ellpack_add(
+        ctypes.byref(a), ctypes.byref(b), al, be, tau, None, ctypes.byref(w)) == S.SP2E_ARG else None
+    assert b"sizes differ" in add(A, big)
+    assert b"dtypes differ" in add(A, f32)
+    assert b"alias" in add(A, A)
+    assert b"not finite" in add(A, B, be=float("nan"))
+    info = S.sp2_step_info()
+
+    def step(x, xn, nocc=4.0, tau=1e-5, path=0, inf=True):
+        info.spgemm_path = path
+        rc = S.lib.sp2_step(ctypes.byref(x), ctypes.byref(xn), nocc, tau, ctypes.byref(info) if inf else None, None)
+        return S.lib.sp2_last_error_string() if rc == S.SP2E_ARG else None
+    assert b"info" in step(A, B, inf=False)
+    assert b"differ" in step(A, big)
+    assert b"differ" in step(A, f32)
+    assert b"aliases" in step(A, A)
+    assert b"tau" in step(A, B, tau=float("nan"))
+    assert b"nocc" in step(A, B, nocc=float("inf"))
+    assert b"spgemm_path" in step(A, B, path=6)

@@ -325,8 +325,12 @@ static orc_ell spgemm_fit(const orc_ell *A, const orc_ell *B, const orc_ell *C, 
   }
 }
 
+/* Sized by the longest union of two rows (at most nnz_A(i) + nnz_B(i)), not by the stored
+ * widths, so that the widths of an iteration's matrices do not compound. */
 static orc_ell add_fit(const orc_ell *A, const orc_ell *B, double alpha, double beta, double tau) {
-  int w = A->w + B->w;
+  int w = 1;
+  for (int i = 0; i < A->n; ++i)
+    if (A->nnz[i] + B->nnz[i] > w) w = A->nnz[i] + B->nnz[i];
   if (w > A->n) w = A->n;
   orc_ell out = ell_alloc(A->n, w);
   orc_add(A, B, alpha, beta, tau, &out, NULL);
@@ -355,7 +359,10 @@ int orc_sp2(const orc_ell *H, double nocc, double tol, double tau, int max_iter,
   int it = 0;
   for (;; ++it) {
     double trX = orc_trace(&X);
-    orc_ell P = spgemm_fit(&X, &X, NULL, 1.0, 0.0, 0.0, 2 * X.w, NULL);
+    long long xt; int xmax;
+    row_stats(&X, &xt, &xmax);
+    /* first width tried: 8x the longest row of X (spgemm_fit grows it to the exact count) */
+    orc_ell P = spgemm_fit(&X, &X, NULL, 1.0, 0.0, 0.0, 8 * xmax, NULL);
     double trX2 = orc_trace(&P);
     double err = fabs(trX - trX2) / (double)n;
     if (it <= st->max_iter) {

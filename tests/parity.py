@@ -114,3 +114,16 @@ def dense_of(idx, val, nnz, n):
         k = int(nnz[i])
         M[i, idx[i, :k]] = val[i, :k]
     return M
+
+
+def sparse_of(idx, val, nnz, n):
+    """scipy CSR copy of an ELLPACK matrix, for comparisons at sizes a dense copy cannot hold."""
+    import scipy.sparse as sp
+    live = np.arange(idx.shape[1])[None, :] < np.asarray(nnz)[:, None]
+    rows = np.repeat(np.arange(n), np.asarray(nnz, dtype=np.int64))
+    return sp.csr_matrix((np.asarray(val, dtype=np.float64)[live], (rows, idx[live].astype(np.int64))), shape=(n, n))
+
+
+def sparse_fro(M):
+    """Frobenius norm of a scipy sparse matrix."""
+    return float(np.sqrt((M.multiply(M)).sum()))

@@ -1,0 +1,47 @@
+"""Full-size SP2 case: 3D tight-binding with A/B splitting, N=131072, tau 1e-5, tol 1e-10,
+nocc = N/2, in the configuration the benchmark's SP2 workload runs (sp2_purify defaults:
+symmetric products, automatic first pass).  FP64 on the GPU against the oracle: the same
+iterations, branches, status and traces, and the same density matrix to 1e-10 (Frobenius /
+sqrt(N)); mixed precision within 1e-5 of the oracle's density matrix (GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2102_08505_gb300 import inputs as I
+from parity import sparse_fro, sparse_of
+
+pytestmark = pytest.mark.gpu
+
+N, TAU, TOL = 131072, 1e-5, 1e-10
+
+
+def test_fullsize_sp2_f64_and_mixed_against_oracle(gpu):
+    S = gpu
+    H = O.Ell(*I.tight_binding(N, seed=0, delta=10.0))
+    O.set_threads(O.max_threads())
+    try:
+        Do, so = O.sp2(H, N // 2, TOL, TAU)
+    finally:
+        O.set_threads(1)
+    assert so["status"] == "converged"
+    ref = sparse_of(Do.idx, Do.val, Do.nnz, N)
+
+    dH = S.Ellpack.from_numpy(H.idx, H.val, H.nnz)
+    D64, s64 = S.sp2_purify(dH, N // 2, TOL, S.sp2_options_default(tau=TAU))
+    assert (s64["iterations"], s64["status"], s64["branch"]) == (so["iterations"], so["status"], so["branch"])
+    assert np.allclose(s64["trX"], so["trX"], rtol=1e-11, atol=0)
+    d64 = sparse_fro(sparse_of(*D64.to_numpy(), N) - ref) / math.sqrt(N)
+    assert d64 < 1e-10, d64
+
+    Dm, sm = S.sp2_purify(dH, N // 2, TOL, S.sp2_options_default(tau=TAU, precision=S.SP2_PREC_MIXED),
+                          allow_notconv=True)
+    Mm = sparse_of(*Dm.to_numpy(), N)
+    dm = sparse_fro(Mm - ref) / math.sqrt(N)
+    print("full size: %d iterations (fp32 %d), |D_mixed - D_oracle|_F/sqrt(N) = %.3e, FP64 %.3e" % (
+        sm["iterations"], sm["fp32_iterations"], dm, d64))
+    assert sm["status"] in ("converged", "stalled")
+    assert dm <= 1e-5, dm
+    assert sm["fp32_iterations"] >= 1 and sm["iterations"] - sm["fp32_iterations"] >= 2
+    assert abs(Mm.diagonal().sum() - N / 2) < 1e-3

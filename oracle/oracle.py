@@ -164,14 +164,24 @@ def from_dense(M, width=None, keep_zeros=False):
     return E
 
 
+ORC_NOMEM = -3
+
+
+def _check(rc):
+    """Raises for a negative oracle status: -3 is out of host memory, others bad arguments."""
+    if rc == ORC_NOMEM:
+        raise MemoryError("oracle ran out of host memory")
+    if rc < 0:
+        raise ValueError("oracle rejected its arguments")
+
+
 def _fit(call, n_rows, w0, n_cols_cap):
     w = max(1, min(int(w0), n_cols_cap))
     cnt = np.zeros(n_rows, np.int32)
     while True:
         out = Ell.empty(n_rows, w)
         rc = call(out, cnt)
-        if rc < 0:
-            raise ValueError("oracle rejected its arguments")
+        _check(rc)
         if rc == 0:
             return out, cnt
         w = int(cnt.max())
@@ -242,8 +252,7 @@ def gershgorin(H):
 def x0(H, emin, emax, tau=0.0):
     out = Ell.empty(H.n, H.w + 1)
     a, o = H._c(), out._c()
-    if lib().orc_x0(ctypes.byref(a), float(emin), float(emax), float(tau), ctypes.byref(o)) != 0:
-        raise ValueError("oracle rejected its arguments")
+    _check(lib().orc_x0(ctypes.byref(a), float(emin), float(emax), float(tau), ctypes.byref(o)))
     return out
 
 
@@ -271,8 +280,7 @@ def sp2(H, nocc, tol, tau=0.0, max_iter=100, stall=True, stall_arm=0.1, stall_ra
     d = _OrcEll()
     rc = L.orc_sp2(ctypes.byref(h), float(nocc), float(tol), float(tau), int(max_iter),
                    float(stall_arm) if stall else 0.0, float(stall_ratio), ctypes.byref(d), ctypes.byref(st))
-    if rc != 0:
-        raise ValueError("oracle rejected its arguments")
+    _check(rc)
     n, w = d.n, d.w
     idx = np.ctypeslib.as_array(d.idx, shape=(n * w,)).reshape(n, w).copy()
     val = np.ctypeslib.as_array(d.val, shape=(n * w,)).reshape(n, w).copy()

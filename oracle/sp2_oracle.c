@@ -28,8 +28,24 @@
  *       repeat: trX = tr X; P = X*X; trX2 = tr P; err = |trX - trX2| / N
  *               stop if err < tol (or the stall rule fires, or max_iter is reached)
  *               X <- drop(2X - P) if |2 trX - trX2 - nocc| < |trX2 - nocc|, else drop(P)
- *     The branch rule, error definition and stall rule are readings of an SP2 the paper
- *     only names; they are listed as readings in the design notes.
+ *     The paper names SP2 but prints none of its rules, so the following are readings:
+ *       - branch: 2X - X^2 is taken iff |2 trX - trX2 - nocc| < |trX2 - nocc| (strict);
+ *         a tie takes X^2, which keeps the choice deterministic;
+ *       - error: err_n = |trX_n - trX2_n| / N, the trace defect per orbital, because with
+ *         tau > 0 the unnormalised defect cannot reach a tolerance such as 1e-10;
+ *       - stall rule: armed once |trX - trX2| < stall_arm (0.1), it fires when
+ *         err_n >= stall_ratio * err_{n-2} (ratio 1: two updates brought no reduction),
+ *         so that a run whose error has reached the floor set by tau ends there; it is
+ *         not armed earlier because a gapless H shows that pattern long before the end;
+ *       - tr X^2 is the diagonal of the unthresholded product P, taken before the drop;
+ *       - keep rule: an entry survives the drop iff |v| > tau (a drop tolerance removes
+ *         the small entries; an entry equal to tau is removed); at tau == 0 every
+ *         structural entry is kept, exact zeros included, so that the pattern does not
+ *         depend on cancellation.
+ *
+ * Storage readings (the paper fixes only the array sizes): rows are stored row-major
+ * (index[i*M + s], consistent with the N*M allocations), each row in ascending column
+ * order; padding slots are never read.
  *
  * Compiled with -ffp-contract=off so that every a*b + c is a separately rounded
  * multiply and add, i.e. the arithmetic is exactly what the C source says.
@@ -90,18 +106,22 @@ int orc_spgemm(const orc_ell *A, const orc_ell *B, const orc_ell *C, double alph
   if (B->n != n) return -1;
   if (beta != 0.0 && (!C || C->n != n)) return -1;
   if (rows == NULL) nrows = n;
-  int overflow = 0;
-#pragma omp parallel num_threads(g_threads) reduction(| : overflow)
+  int overflow = 0, nomem = 0;
+#pragma omp parallel num_threads(g_threads) reduction(| : overflow, nomem)
   {
-    double *acc = (double *)malloc(sizeof(double) * (size_t)n);
-    double *cv = (double *)malloc(sizeof(double) * (size_t)n);
-    int *mark = (int *)malloc(sizeof(int) * (size_t)n);
-    int *list = (int *)malloc(sizeof(int) * (size_t)n);
+    double *acc = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *cv = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    int *mark = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    int *list = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
     kv *arow = (kv *)malloc(sizeof(kv) * (size_t)(A->w > 0 ? A->w : 1));
+    const int ok = acc && cv && mark && list && arow;
+    if (!ok) nomem = 1;
     /* mark[j] == r  <=>  column j is already in the pattern of output row r */
-    for (int j = 0; j < n; ++j) mark[j] = -1;
+    if (ok)
+      for (int j = 0; j < n; ++j) mark[j] = -1;
 #pragma omp for schedule(dynamic, 64)
     for (int r = 0; r < nrows; ++r) {
+      if (!ok) continue;
       int i = rows ? rows[r] : r;
       int cnt = 0;
       /* row i of A in ascending column order */
@@ -152,6 +172,7 @@ int orc_spgemm(const orc_ell *A, const orc_ell *B, const orc_ell *C, double alph
     }
     free(acc); free(cv); free(mark); free(list); free(arow);
   }
+  if (nomem) return -3;
   return overflow ? 1 : 0;
 }
 
@@ -161,10 +182,11 @@ int orc_add(const orc_ell *A, const orc_ell *B, double alpha, double beta, doubl
   if (!A || !B || !out || A->n != B->n || tau < 0.0) return -1;
   int n = A->n;
   int overflow = 0;
-  double *av = (double *)calloc((size_t)n, sizeof(double));
-  double *bv = (double *)calloc((size_t)n, sizeof(double));
-  int *mark = (int *)malloc(sizeof(int) * (size_t)n);
-  int *list = (int *)malloc(sizeof(int) * (size_t)n);
+  double *av = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double *bv = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  int *mark = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  int *list = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  if (!av || !bv || !mark || !list) { free(av); free(bv); free(mark); free(list); return -3; }
   for (int j = 0; j < n; ++j) mark[j] = -1;
   for (int i = 0; i < n; ++i) {
     int cnt = 0;
@@ -252,6 +274,7 @@ int orc_x0(const orc_ell *H, double emin, double emax, double tau, orc_ell *out)
   double *v = (double *)malloc(sizeof(double) * (size_t)(H->w + 1));
   int *c = (int *)malloc(sizeof(int) * (size_t)(H->w + 1));
   kv *row = (kv *)malloc(sizeof(kv) * (size_t)(H->w + 1));
+  if (!v || !c || !row) { free(v); free(c); free(row); return -3; }
   for (int i = 0; i < n; ++i) {
     int cnt = 0, has_diag = 0;
     for (int s = 0; s < H->nnz[i]; ++s) {
@@ -281,7 +304,8 @@ int orc_x0(const orc_ell *H, double emin, double emax, double tau, orc_ell *out)
 
 typedef struct {
   int iterations;     /* number of updates applied */
-  int status;         /* 0 converged (err < tol), 1 stopped by stall rule, 2 max_iter reached, <0 error */
+  int status;         /* 0 converged (err < tol), 1 stopped by stall rule, 2 max_iter reached,
+                         -1 bad arguments, -3 out of host memory */
   int max_iter;       /* capacity of the per-iteration arrays below */
   double emin, emax;  /* Gershgorin bounds */
   double *trX;        /* per visited X_n: tr X_n                         [max_iter+1] */
@@ -292,15 +316,18 @@ typedef struct {
   int *max_row_nnz;   /* per visited X_n                                  [max_iter+1] */
 } orc_sp2_stats;
 
-static orc_ell ell_alloc(int n, int w) {
-  orc_ell m;
-  m.n = n; m.w = w;
-  m.idx = (int *)malloc(sizeof(int) * (size_t)n * (size_t)w);
-  m.val = (double *)malloc(sizeof(double) * (size_t)n * (size_t)w);
-  m.nnz = (int *)calloc((size_t)n, sizeof(int));
-  return m;
-}
 static void ell_free(orc_ell *m) { free(m->idx); free(m->val); free(m->nnz); m->idx = 0; m->val = 0; m->nnz = 0; }
+
+/* Allocates an n x w matrix; returns 0, or ORC_NOMEM (nothing left allocated). */
+#define ORC_NOMEM (-3)
+static int ell_alloc(int n, int w, orc_ell *m) {
+  m->n = n; m->w = w;
+  m->idx = (int *)malloc(sizeof(int) * (size_t)n * (size_t)w);
+  m->val = (double *)malloc(sizeof(double) * (size_t)n * (size_t)w);
+  m->nnz = (int *)calloc((size_t)n, sizeof(int));
+  if (!m->idx || !m->val || !m->nnz) { ell_free(m); return ORC_NOMEM; }
+  return 0;
+}
 
 static void row_stats(const orc_ell *m, long long *tot, int *mx) {
   long long t = 0; int x = 0;
@@ -308,33 +335,38 @@ static void row_stats(const orc_ell *m, long long *tot, int *mx) {
   *tot = t; *mx = x;
 }
 
-/* Runs an ELLPACK product into a freshly sized matrix (width grown until it fits). */
-static orc_ell spgemm_fit(const orc_ell *A, const orc_ell *B, const orc_ell *C, double alpha,
-                          double beta, double tau, int w_guess, double *diag) {
+/* Runs an ELLPACK product into a freshly sized matrix *out (width grown until it fits).
+ * Returns 0, ORC_NOMEM, or -1 if the product rejects its arguments. */
+static int spgemm_fit(const orc_ell *A, const orc_ell *B, const orc_ell *C, double alpha,
+                      double beta, double tau, int w_guess, double *diag, orc_ell *out) {
   int n = A->n;
-  int *cnt = (int *)malloc(sizeof(int) * (size_t)n);
+  int *cnt = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  if (!cnt) return ORC_NOMEM;
   int w = w_guess < 1 ? 1 : (w_guess > n ? n : w_guess);
   for (;;) {
-    orc_ell out = ell_alloc(n, w);
-    int rc = orc_spgemm(A, B, C, alpha, beta, tau, NULL, n, &out, cnt, diag);
-    if (rc == 0) { free(cnt); return out; }
+    if (ell_alloc(n, w, out) != 0) { free(cnt); return ORC_NOMEM; }
+    int rc = orc_spgemm(A, B, C, alpha, beta, tau, NULL, n, out, cnt, diag);
+    if (rc == 0) { free(cnt); return 0; }
+    ell_free(out);
+    if (rc < 0) { free(cnt); return rc; }
     int need = 0;
     for (int i = 0; i < n; ++i) if (cnt[i] > need) need = cnt[i];
-    ell_free(&out);
     w = need;
   }
 }
 
 /* Sized by the longest union of two rows (at most nnz_A(i) + nnz_B(i)), not by the stored
  * widths, so that the widths of an iteration's matrices do not compound. */
-static orc_ell add_fit(const orc_ell *A, const orc_ell *B, double alpha, double beta, double tau) {
+static int add_fit(const orc_ell *A, const orc_ell *B, double alpha, double beta, double tau,
+                   orc_ell *out) {
   int w = 1;
   for (int i = 0; i < A->n; ++i)
     if (A->nnz[i] + B->nnz[i] > w) w = A->nnz[i] + B->nnz[i];
   if (w > A->n) w = A->n;
-  orc_ell out = ell_alloc(A->n, w);
-  orc_add(A, B, alpha, beta, tau, &out, NULL);
-  return out;
+  if (ell_alloc(A->n, w, out) != 0) return ORC_NOMEM;
+  int rc = orc_add(A, B, alpha, beta, tau, out, NULL);
+  if (rc < 0) ell_free(out);
+  return rc < 0 ? rc : 0;
 }
 
 /*
@@ -352,8 +384,10 @@ int orc_sp2(const orc_ell *H, double nocc, double tol, double tau, int max_iter,
   double emin, emax;
   orc_gershgorin(H, &emin, &emax);
   st->emin = emin; st->emax = emax;
-  orc_ell X = ell_alloc(n, H->w + 1);
-  if (orc_x0(H, emin, emax, tau, &X) != 0) { ell_free(&X); st->status = -1; return -1; }
+  orc_ell X;
+  if (ell_alloc(n, H->w + 1, &X) != 0) { st->status = ORC_NOMEM; return ORC_NOMEM; }
+  int rc = orc_x0(H, emin, emax, tau, &X);
+  if (rc != 0) { ell_free(&X); st->status = rc; return rc; }
   int armed = 0;
   st->status = 2;
   int it = 0;
@@ -362,7 +396,9 @@ int orc_sp2(const orc_ell *H, double nocc, double tol, double tau, int max_iter,
     long long xt; int xmax;
     row_stats(&X, &xt, &xmax);
     /* first width tried: 8x the longest row of X (spgemm_fit grows it to the exact count) */
-    orc_ell P = spgemm_fit(&X, &X, NULL, 1.0, 0.0, 0.0, 8 * xmax, NULL);
+    orc_ell P;
+    rc = spgemm_fit(&X, &X, NULL, 1.0, 0.0, 0.0, 8 * xmax, NULL, &P);
+    if (rc != 0) { ell_free(&X); st->status = rc; return rc; }
     double trX2 = orc_trace(&P);
     double err = fabs(trX - trX2) / (double)n;
     if (it <= st->max_iter) {
@@ -378,14 +414,15 @@ int orc_sp2(const orc_ell *H, double nocc, double tol, double tau, int max_iter,
     orc_ell Xn;
     if (fabs(2.0 * trX - trX2 - nocc) < fabs(trX2 - nocc)) {
       st->branch[it] = 2;
-      Xn = add_fit(&P, &X, -1.0, 2.0, tau);    /* 2X - X^2 */
+      rc = add_fit(&P, &X, -1.0, 2.0, tau, &Xn);    /* 2X - X^2 */
     } else {
       st->branch[it] = 1;
-      Xn = ell_alloc(n, P.w);                   /* X^2, thresholded */
-      orc_drop(&P, tau, &Xn);
+      rc = ell_alloc(n, P.w, &Xn);                   /* X^2, thresholded */
+      if (rc == 0) orc_drop(&P, tau, &Xn);
     }
     ell_free(&P);
     ell_free(&X);
+    if (rc != 0) { st->status = rc; return rc; }
     X = Xn;
   }
   st->iterations = it;

@@ -10,6 +10,7 @@
 #include <stdint.h>
 
 #include <cstddef>
+#include <mutex>
 
 #include "sp2ell.h"
 
@@ -35,6 +36,28 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
 inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 int num_sms();
+// Ordinal of the current device, clamped to the 64 per-device cache entries.
+int current_device();
+
+// One-time per-device set-up of a launcher (kernel attributes, occupancy), safe against
+// first calls made at the same time from several host threads: the set-up runs under a
+// lock, and a failed set-up is retried on the next call.  value[dev] holds what the
+// set-up stored (read after device_once returned SP2_OK).
+struct DeviceOnce {
+  std::mutex mu;
+  bool done[64] = {false};
+  int value[64] = {0};
+};
+template <typename F>
+int device_once(DeviceOnce &o, int dev, F &&setup) {
+  std::lock_guard<std::mutex> lk(o.mu);
+  if (!o.done[dev]) {
+    const int rc = setup(o.value[dev]);
+    if (rc != 0) return rc;
+    o.done[dev] = true;
+  }
+  return 0;
+}
 inline int round_up(int x, int m) { return ((x + m - 1) / m) * m; }
 inline size_t round_up_sz(size_t x, size_t m) { return ((x + m - 1) / m) * m; }
 

@@ -37,17 +37,24 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
   return e == cudaErrorMemoryAllocation ? SP2E_NOMEM : SP2E_CUDA;
 }
 
-int num_sms() {
-  static int cache[64] = {0};
+int current_device() {
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (cache[dev] == 0) {
-    int v = 0;
+  return (dev < 0 || dev >= 64) ? 0 : dev;
+}
+
+int num_sms() {
+  static DeviceOnce once;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int slot = (dev < 0 || dev >= 64) ? 0 : dev;
+  device_once(once, slot, [&](int &v) {
+    v = 0;
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    cache[dev] = v > 0 ? v : 1;
-  }
-  return cache[dev];
+    if (v < 1) v = 1;
+    return 0;
+  });
+  return once.value[slot];
 }
 
 int check_matrix(const ellpack_t *m, const char *name) {

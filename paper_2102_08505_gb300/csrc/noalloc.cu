@@ -65,6 +65,10 @@ extern "C" int ellpack_trace_noalloc(const ellpack_t *A, double *trace, double *
   SP2_CUDA(cudaStreamSynchronize(s));
   *trace = h.tr;
   if (frobenius2) *frobenius2 = h.fro;
-  if (!isfinite(h.tr) || !isfinite(h.fro)) return fail(SP2E_NONFINITE, "ellpack_trace_noalloc: non-finite result");
+  // each requested output follows the rule of its allocating counterpart (ellpack_trace,
+  // ellpack_frobenius2): a squared norm that overflows fails only if it was asked for
+  if (!isfinite(h.tr)) return fail(SP2E_NONFINITE, "ellpack_trace_noalloc: non-finite trace");
+  if (frobenius2 && !isfinite(h.fro))
+    return fail(SP2E_NONFINITE, "ellpack_trace_noalloc: non-finite squared Frobenius norm");
   return SP2_OK;
 }

@@ -420,8 +420,11 @@ struct BlockGeo {
   static constexpr int GROUPS_RAW = 232192 / BYTES_PER_GROUP;
   // at most 32 warps per CTA (1024 threads)
   static constexpr int GROUPS_MAX0 = (SZ ? (sizeof(T) == 4 ? 20 : 32) : (sizeof(T) == 4 ? 12 : 16)) / (R > 2 ? 2 : 1);
-  static constexpr int GROUPS_MAX = GROUPS_MAX0 < 32 / R ? GROUPS_MAX0 : 32 / R;
+  // R > 1: group g synchronises on named barrier g + 1, and PTX names barriers 0..15 only
+  static constexpr int GROUPS_CAP = R == 1 ? 32 : (32 / R < 15 ? 32 / R : 15);
+  static constexpr int GROUPS_MAX = GROUPS_MAX0 < GROUPS_CAP ? GROUPS_MAX0 : GROUPS_CAP;
   static constexpr int GROUPS = GROUPS_RAW > GROUPS_MAX ? GROUPS_MAX : (GROUPS_RAW < 1 ? 1 : GROUPS_RAW);
+  static_assert(R == 1 || GROUPS <= 15, "named barriers 1..15 only");
   static constexpr int WARPS = GROUPS * R;
   static constexpr int SMEM = GROUPS * BYTES_PER_GROUP;
   // g < 2^24 - 1 fits the packed entry and never matches the empty entry 0xFFFFFFFF
@@ -1618,19 +1621,16 @@ int launch_hash(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, const i
                 int *fb, int *fb_count, cudaStream_t s) {
   using Cfg = HashCfg<T, LOG2T>;
   auto kern = spgemm_hash_kernel<T, LOG2T, QM>;
-  static bool attr_set[64] = {false};
-  static int occ_cache[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (!attr_set[dev]) {
+  static DeviceOnce once;
+  const int dev = current_device();
+  SP2_TRY(device_once(once, dev, [&](int &occ) {
     SP2_TRY(set_smem(kern, Cfg::SMEM));
-    int occ = 0;
+    occ = 0;
     SP2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Cfg::WARPS * 32, Cfg::SMEM));
-    occ_cache[dev] = occ < 1 ? 1 : occ;
-    attr_set[dev] = true;
-  }
-  const long long cap = (long long)num_sms() * occ_cache[dev];
+    if (occ < 1) occ = 1;
+    return SP2_OK;
+  }));
+  const long long cap = (long long)num_sms() * once.value[dev];
   long long blocks = row_list ? cap : ((long long)a.A->n + Cfg::WARPS - 1) / Cfg::WARPS;
   int grid = (int)(blocks < cap ? blocks : cap);
   if (grid < 1) grid = 1;
@@ -1650,19 +1650,16 @@ template <typename T, int R, int QW, bool KEEPZ, int SZ = 0>
 int launch_block(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
   using Geo = BlockGeo<T, R, SZ>;
   auto kern = spgemm_block_kernel<T, R, QW, KEEPZ, SZ>;
-  static bool attr_set[64] = {false};
-  static int occ_cache[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (!attr_set[dev]) {
+  static DeviceOnce once;
+  const int dev = current_device();
+  SP2_TRY(device_once(once, dev, [&](int &occ) {
     SP2_TRY(set_smem(kern, Geo::SMEM));
-    int occ = 0;
+    occ = 0;
     SP2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Geo::WARPS * 32, Geo::SMEM));
-    occ_cache[dev] = occ < 1 ? 1 : occ;
-    attr_set[dev] = true;
-  }
-  const long long cap = (long long)num_sms() * occ_cache[dev];
+    if (occ < 1) occ = 1;
+    return SP2_OK;
+  }));
+  const long long cap = (long long)num_sms() * once.value[dev];
   const long long blocks = ((long long)a.A->n + Geo::GROUPS - 1) / Geo::GROUPS;
   int grid = (int)(blocks < cap ? blocks : cap);
   if (grid < 1) grid = 1;
@@ -1681,19 +1678,16 @@ template <typename T, int QM, int S, bool KEEPZ, int SZ = 0>
 int launch_super(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
   using Geo = BlockGeo<T, 1, SZ>;
   auto kern = spgemm_super_kernel<T, QM, S, KEEPZ, SZ>;
-  static bool attr_set[64] = {false};
-  static int occ_cache[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (!attr_set[dev]) {
+  static DeviceOnce once;
+  const int dev = current_device();
+  SP2_TRY(device_once(once, dev, [&](int &occ) {
     SP2_TRY(set_smem(kern, Geo::SMEM));
-    int occ = 0;
+    occ = 0;
     SP2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Geo::WARPS * 32, Geo::SMEM));
-    occ_cache[dev] = occ < 1 ? 1 : occ;
-    attr_set[dev] = true;
-  }
-  const long long cap = (long long)num_sms() * occ_cache[dev];
+    if (occ < 1) occ = 1;
+    return SP2_OK;
+  }));
+  const long long cap = (long long)num_sms() * once.value[dev];
   const long long blocks = ((long long)a.A->n + Geo::GROUPS - 1) / Geo::GROUPS;
   int grid = (int)(blocks < cap ? blocks : cap);
   if (grid < 1) grid = 1;
@@ -1746,14 +1740,8 @@ template <typename T>
 int launch_window(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, const int *in, const int *in_count, int *out,
                   int *out_count, cudaStream_t s) {
   using Cfg = WinCfg<T>;
-  static bool attr_set[64] = {false};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (!attr_set[dev]) {
-    SP2_TRY(set_smem(spgemm_window_kernel<T>, Cfg::SMEM));
-    attr_set[dev] = true;
-  }
+  static DeviceOnce once;
+  SP2_TRY(device_once(once, current_device(), [&](int &) { return set_smem(spgemm_window_kernel<T>, Cfg::SMEM); }));
   const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
   prof_begin(SP2_PROF_LARGE, s);
   spgemm_window_kernel<T><<<num_sms(), kWinThreads, Cfg::SMEM, s>>>(

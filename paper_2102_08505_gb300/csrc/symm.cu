@@ -346,14 +346,11 @@ static int mirror_t(const ellpack_t *U, ellpack_t *Out, const BatchView &bv, int
   mirror_sort_mid_kernel<T><<<num_sms() * 2, kSymThreads, 0, s>>>(outview<T>(Out), cnt, rowstat, longs, nlong);
   note_launch();
   constexpr int smem = kSortCtaMax * (int)(sizeof(int) + sizeof(T));
-  static bool attr[64] = {false};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (!attr[dev]) {
+  static DeviceOnce once;
+  SP2_TRY(device_once(once, current_device(), [&](int &) {
     SP2_CUDA(cudaFuncSetAttribute(mirror_sort_long_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    attr[dev] = true;
-  }
+    return SP2_OK;
+  }));
   mirror_sort_long_kernel<T><<<num_sms(), kSymThreads, smem, s>>>(outview<T>(Out), outview<T>(U), cnt, rowstat, longs,
                                                                    nlong);
   note_launch();

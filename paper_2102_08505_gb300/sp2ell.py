@@ -314,12 +314,14 @@ def ellpack_frobenius2(A, stream=None):
 SP2_NOALLOC_MAX_N = 65536
 
 
-def ellpack_trace_noalloc(A, stream=None):
+def ellpack_trace_noalloc(A, stream=None, frobenius=True):
     """(tr A, ||A||_F^2) through the entry point that allocates no device memory (its
-    scratch is a fixed array inside the library; n <= SP2_NOALLOC_MAX_N)."""
+    scratch is a fixed array inside the library; n <= SP2_NOALLOC_MAX_N).  With
+    frobenius=False the squared norm is not requested (NULL) and None is returned for it."""
     tr, fro = ctypes.c_double(), ctypes.c_double()
-    _check(lib.ellpack_trace_noalloc(_d(A), ctypes.byref(tr), ctypes.byref(fro), _stream(stream)))
-    return tr.value, fro.value
+    _check(lib.ellpack_trace_noalloc(_d(A), ctypes.byref(tr), ctypes.byref(fro) if frobenius else None,
+                                     _stream(stream)))
+    return tr.value, (fro.value if frobenius else None)
 
 
 def ellpack_gershgorin(H, stream=None):

@@ -250,6 +250,132 @@ def test_sp2_thresholded_invariants():
     assert st["status"] in ("converged", "stalled")
 
 
+def tie_matrix(n, seed, tau, with_zeros=True):
+    """Sparse matrix whose stored values include exact ties at +-tau, exact zeros (stored
+    structurally) and values one ulp on either side of tau, beside random values."""
+    rng = np.random.default_rng(seed)
+    idx, val, nnz = I.random_sparse(n, seed=seed, min_nnz=0, max_nnz=9)
+    special = [tau, -tau, np.nextafter(tau, 1.0), -np.nextafter(tau, 1.0), np.nextafter(tau, 0.0),
+               -np.nextafter(tau, 0.0)] + ([0.0, -0.0] if with_zeros else [])
+    for i in range(n):
+        for s_ in range(nnz[i]):
+            if rng.random() < 0.4:
+                val[i, s_] = special[int(rng.integers(len(special)))]
+    return O.Ell(idx, val, nnz)
+
+
+@pytest.mark.parametrize("tau", [0.0, 0.05, 0.25])
+def test_drop_matches_dense(tau):
+    """The drop of the X^2 branch: keep (j, v) iff |v| > tau (an entry equal to tau is
+    removed, one ulp above it stays); tau = 0 keeps every stored entry, zeros included.
+    Reference: numpy thresholding of the dense matrix."""
+    n = 48
+    A = tie_matrix(n, 61, tau if tau > 0 else 0.125)
+    out = O.drop(A, tau)
+    Ad = A.to_dense()
+    if tau == 0.0:
+        assert np.array_equal(structural(out), structural(A))
+        assert np.array_equal(out.to_dense(), Ad)
+        return
+    keep = (structural(A) > 0) & (np.abs(Ad) > tau)
+    assert np.array_equal(structural(out) > 0, keep)
+    assert np.array_equal(out.to_dense(), np.where(keep, Ad, 0.0))
+    for i in range(n):  # stored order stays ascending
+        assert np.all(np.diff(out.row(i)[0]) > 0)
+
+
+@pytest.mark.parametrize("ab", ALPHA_BETA)
+@pytest.mark.parametrize("tau", [0.05, 0.25])
+def test_add_thresholded_matches_dense(ab, tau):
+    """drop_tau(alpha A + beta B) at tau > 0 against the dense numpy formula: the pattern
+    is the union of the two patterns where |alpha a + beta b| > tau, values exact (both
+    sides round alpha*a and beta*b separately and then add them)."""
+    alpha, beta = ab
+    n = 48
+    A = tie_matrix(n, 71, tau)
+    B = tie_matrix(n, 72, tau)
+    out = O.add(A, B, alpha, beta, tau)
+    v = alpha * A.to_dense() + beta * B.to_dense()
+    union = (structural(A) + structural(B)) > 0
+    keep = union & (np.abs(v) > tau)
+    assert np.array_equal(structural(out) > 0, keep)
+    assert np.array_equal(out.to_dense(), np.where(keep, v, 0.0))
+
+
+def test_add_exact_tie_is_dropped():
+    """alpha*a + beta*b landing exactly on tau is dropped; one ulp above is kept."""
+    tau = 0.25
+    up = np.nextafter(0.125, 1.0)  # 0.125 + 2^-55; twice that is 0.25 + 2^-54, one ulp above tau
+    A = O.from_dense(np.array([[0.125, up, 0.5], [0.0, 0.25, 0.0], [0.0, 0.0, 0.125]]))
+    B = O.from_dense(np.array([[0.125, up, -0.25], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0625]]))
+    out = O.add(A, B, 1.0, 1.0, tau)
+    # row 0: 0.25 (tie, dropped), 0.25 + ulp (kept), 0.25 (tie, dropped); row 1: 0.25 (tie);
+    # row 2: 0.1875 (below)
+    assert out.nnz.tolist() == [1, 0, 0]
+    assert out.row(0)[0].tolist() == [1]
+    out2 = O.add(A, B, 2.0, 0.0, tau)  # 2 * 0.125 = tau: dropped; 2 * up, 2 * 0.5, 2 * 0.25 kept
+    assert out2.nnz.tolist() == [2, 1, 0]
+    assert out2.row(0)[0].tolist() == [1, 2]
+
+
+def dense_sp2(Hd, nocc, tol, tau, max_iter=100, stall_arm=0.1, stall_ratio=1.0):
+    """SP2 restated on dense numpy arrays with the same readings (Gershgorin X0, branch on
+    the trace rule, drop |v| > tau after each update, error |trX - trX2| / N, stall rule).
+    Dense matrix products and thresholding; no code shared with the oracle."""
+    n = Hd.shape[0]
+    d = np.diag(Hd)
+    rad = np.abs(Hd).sum(axis=1) - np.abs(d)
+    lo, hi = float(np.min(d - rad)), float(np.max(d + rad))
+    X = (hi * np.eye(n) - Hd) / (hi - lo)
+    X = np.where(np.abs(X) > tau, X, 0.0)
+    errs, branch = [], []
+    armed = False
+    it = 0
+    while True:
+        P = X @ X
+        trX, trX2 = float(np.trace(X)), float(np.trace(P))
+        err = abs(trX - trX2) / n
+        errs.append(err)
+        if err < tol:
+            status = "converged"
+            break
+        if stall_arm > 0:
+            if abs(trX - trX2) < stall_arm:
+                armed = True
+            if armed and it >= 2 and err >= stall_ratio * errs[it - 2]:
+                status = "stalled"
+                break
+        if it >= max_iter:
+            status = "max_iter"
+            break
+        if abs(2 * trX - trX2 - nocc) < abs(trX2 - nocc):
+            branch.append("2X-X2")
+            X = 2.0 * X - P
+        else:
+            branch.append("X2")
+            X = P
+        X = np.where(np.abs(X) > tau, X, 0.0)
+        it += 1
+    return X, {"iterations": it, "branch": branch, "err": np.array(errs), "status": status}
+
+
+@pytest.mark.parametrize("tau", [1e-4, 1e-3])
+def test_sp2_thresholded_matches_dense_restatement(tau):
+    """tau > 0: the oracle's SP2 (sparse products, its own drop and add) against the dense
+    restatement above: the same iterations, branches and stop, D's pattern exactly the
+    dense nonzeros, values within 1e-12."""
+    n = 96
+    H = ell(I.banded(n, band=6, seed=4, delta=10.0))
+    D, st = O.sp2(H, n // 2, 1e-10, tau)
+    Dd, sd = dense_sp2(H.to_dense(), n // 2, 1e-10, tau)
+    assert st["iterations"] == sd["iterations"]
+    assert st["branch"] == sd["branch"]
+    assert st["status"] == sd["status"]
+    assert "X2" in st["branch"] and "2X-X2" in st["branch"]
+    assert np.array_equal(structural(D) > 0, Dd != 0.0)
+    assert np.max(np.abs(D.to_dense() - Dd)) < 1e-12
+
+
 # ---------------------------------------------------------------- planted mistakes
 MUTANTS = {
     "dropped_beta_term": [("double v = alpha * acc[j] + beta * cv[j];", "double v = alpha * acc[j];")],
@@ -262,6 +388,10 @@ MUTANTS = {
     "branch_flipped": [("if (fabs(2.0 * trX - trX2 - nocc) < fabs(trX2 - nocc)) {",
                         "if (fabs(2.0 * trX - trX2 - nocc) > fabs(trX2 - nocc)) {")],
     "gershgorin_radius": [("if (j == i) d = v; else r = r + fabs(v);", "if (j == i) d = v; else r = r + v;")],
+    "drop_ignores_tau": [("      if (tau == 0.0 || fabs(v) > tau) {\n        out->idx[(size_t)i * out->w + kept]",
+                          "      if (1) {\n        out->idx[(size_t)i * out->w + kept]")],
+    "add_keep_ge": [("if (tau == 0.0 || fabs(v) > tau) { list[kept++] = j; av[j] = v; }",
+                     "if (tau == 0.0 || fabs(v) >= tau) { list[kept++] = j; av[j] = v; }")],
 }
 
 
@@ -298,7 +428,22 @@ def _pins_pass():
         Hg = ell(I.banded(64, band=4, seed=5, delta=10.0))
         D, st = O.sp2(Hg, 32, 1e-12, 0.0, max_iter=60)
         c = O.checks(Hg.to_dense(), D.to_dense(), 32)
-        return c["proj_err"] < 1e-9
+        if not c["proj_err"] < 1e-9:
+            return False
+        # drop and add at tau > 0 with exact ties, against dense thresholding
+        T = tie_matrix(24, 81, 0.25)
+        Td = T.to_dense()
+        if not np.array_equal(O.drop(T, 0.25).to_dense(), np.where(np.abs(Td) > 0.25, Td, 0.0)):
+            return False
+        T2 = tie_matrix(24, 82, 0.25)
+        v = T.to_dense() + T2.to_dense()
+        if not np.array_equal(O.add(T, T2, 1.0, 1.0, 0.25).to_dense(), np.where(np.abs(v) > 0.25, v, 0.0)):
+            return False
+        Ht = ell(I.banded(64, band=5, seed=4, delta=10.0))
+        Dt, stt = O.sp2(Ht, 32, 1e-10, 1e-3)
+        Dtd, sdt = dense_sp2(Ht.to_dense(), 32, 1e-10, 1e-3)
+        return (stt["branch"] == sdt["branch"] and np.array_equal(structural(Dt) > 0, Dtd != 0.0)
+                and np.max(np.abs(Dt.to_dense() - Dtd)) < 1e-12)
     except Exception:
         return False
 

@@ -38,3 +38,25 @@ def test_noalloc_rejects_sizes_beyond_scratch(gpu):
     with pytest.raises(S.Sp2Error) as e:
         S.ellpack_trace_noalloc(A)
     assert e.value.code == S.SP2E_ARG and "exceeds" in str(e.value)
+
+
+def test_noalloc_outputs_follow_their_allocating_counterparts(gpu):
+    """Entries near 1e200: the trace is finite but the squares overflow.  ellpack_trace
+    succeeds and ellpack_frobenius2 fails; the allocation-free call does the same for each
+    output it is asked for (a trace-only call succeeds)."""
+    S = gpu
+    idx, val, nnz = I.banded(300, band=3, seed=5)
+    val = np.where(np.isnan(val), val, val * 1e200)
+    A = S.Ellpack.from_numpy(idx, val, nnz)
+    want_tr = S.ellpack_trace(A)
+    assert np.isfinite(want_tr)
+    with pytest.raises(S.Sp2Error) as e:
+        S.ellpack_frobenius2(A)
+    assert e.value.code == S.SP2E_NONFINITE
+    for _ in range(2):
+        tr, fro = S.ellpack_trace_noalloc(A, frobenius=False)
+        assert fro is None
+        assert tr == pytest.approx(want_tr, rel=1e-13)
+        with pytest.raises(S.Sp2Error) as e:
+            S.ellpack_trace_noalloc(A)
+        assert e.value.code == S.SP2E_NONFINITE

@@ -204,6 +204,14 @@ int sp2_profile_start(void);
  * Errors: SP2E_CUDA. */
 int sp2_profile_stop(sp2_profile *out);
 
+/* Measured multiply-add rate of the current device in `dtype` (SP2_F64: DFMA, SP2_F32:
+ * FFMA): a grid of 8 CTAs per SM runs independent fused multiply-add chains; one untimed
+ * launch, then `reps` (1..1000) launches timed with CUDA events on `stream`.  *tflops
+ * (host) receives the best rate in TFLOP/s (2 flop per FMA).  It is the ALU roofline that
+ * the FP64 product is measured against (the paper has no counterpart: it measures on
+ * CPUs).  Errors: SP2E_ARG, SP2E_NOMEM, SP2E_CUDA.  Synchronises `stream`. */
+int sp2_fma_peak(int dtype, int reps, double *tflops, void *stream);
+
 /* ---------------------------------------------------------------- learned sizing */
 /*
  * Exact structural row counts of A*B (+ C when C is not NULL): counts[i] =

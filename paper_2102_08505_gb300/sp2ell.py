@@ -105,6 +105,7 @@ def _load():
         "ellpack_trace": ([E, P(D), V], ctypes.c_int),
         "ellpack_frobenius2": ([E, P(D), V], ctypes.c_int),
         "ellpack_gershgorin": ([E, P(D), P(D), V], ctypes.c_int),
+        "sp2_fma_peak": ([I, I, P(D), V], ctypes.c_int),
         "ellpack_trace_noalloc": ([E, P(D), P(D), V], ctypes.c_int),
         "sp2_options_default": ([P(sp2_options)], None),
         "sp2_purify": ([E, D, D, P(sp2_options), E, P(sp2_stats), V], ctypes.c_int),
@@ -614,3 +615,10 @@ def ellpack_from_dense(D, A, tau=0.0, stream=None, raise_on_overflow=True):
         return rc, w.value
     _check(rc)
     return w.value
+
+
+def sp2_fma_peak(dtype=SP2_F64, reps=5, stream=None):
+    """Measured FMA rate of the current device in TFLOP/s (DFMA for SP2_F64, FFMA for SP2_F32)."""
+    out = ctypes.c_double()
+    _check(lib.sp2_fma_peak(int(dtype), int(reps), ctypes.byref(out), _stream(stream)))
+    return out.value

@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--no-tts", action="store_true",
+                   help="skip the time-to-solution block (whole SP2 runs of the C1, C3, C4 and C5 workloads)")
     return p.parse_args()
 
 
@@ -147,14 +149,16 @@ class Clocks:
 
 def kernel_traffic(dtype):
     """Per-launch DRAM bytes of the SpGEMM kernel from the committed ncu summary, or None
-    if the kernel source changed since the counters were taken."""
+    if the kernel's source file changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "spgemm_traffic.json")
-    src = os.path.join(ROOT, "paper_2102_08505_gb300", "csrc", "spgemm.cu")
     try:
         rec = json.load(open(path))
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
         ent = rec.get(dtype)
-        if ent and ent.get("spgemm_cu_sha256") == sha:
+        if not ent:
+            return None
+        src = os.path.join(ROOT, "paper_2102_08505_gb300", "csrc", ent.get("source", "spgemm.cu"))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if ent.get("source_sha256", ent.get("spgemm_cu_sha256")) == sha:
             return ent.get("dram_bytes_per_launch_full_size")
     except Exception:
         pass
@@ -253,6 +257,8 @@ def spgemm_kernel_name(a):
         return "spgemm_block_kernel (%d warp%s per row%s)" % (w, "s" if w > 1 else "", ", compact" if p == 7 else "")
     if p == 8:
         return "spgemm_super_kernel (one warp per row, two k steps per pass, compact)"
+    if p == 9:
+        return "spgemm_tile_kernel (8-row tiles sharing one column index, one warp per row)"
     if p == -1:
         return "tuned first pass"
     if p == 3:
@@ -345,13 +351,15 @@ def run_ours(a):
     gbs = alg_bytes / (k_ms * 1e-3) / 1e9
     pk = peaks()
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
-    alu_peak = FP64_PEAK_TFLOPS if a.dtype == "f64" else FP32_PEAK_TFLOPS
+    derived_peak = FP64_PEAK_TFLOPS if a.dtype == "f64" else FP32_PEAK_TFLOPS
+    # the FMA rate of this GPU measured now (dependent-free FMA chains, 8 CTAs per SM)
+    alu_peak = S.sp2_fma_peak(DT, 5)
     traffic = kernel_traffic(a.dtype)
     # the bound is the roof the kernel's arithmetic intensity meets first: FP64 products hit
     # the FP64 FMA rate long before HBM; FP32 products would reach HBM first
     alu_view = {"achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": tflops / alu_peak,
-                "peak_source": "derived: 152 SMs x %s FMA/clk x 2 flop x 2.07 GHz" % (
-                    "2 FP64" if a.dtype == "f64" else "128 FP32"),
+                "peak_source": "of measured: sp2_fma_peak, %s FMA chains timed in this run (derived %.4g)" % (
+                    "DFMA" if a.dtype == "f64" else "FFMA", derived_peak),
                 "flops_per_launch": 2.0 * fmas_exec,
                 "flops": "2 x the products executed" + (" (upper triangle of the symmetric product)" if a.symmetric else "")}
     hbm_view = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
@@ -423,6 +431,9 @@ def run_ours(a):
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(a)
+    tts = None
+    if rank == 0 and world == 1 and not a.no_tts and a.dtype == "f64":
+        tts = time_to_solution(a, local)
 
     if rank == 0:
         line = {
@@ -445,6 +456,8 @@ def run_ours(a):
             "kernels_timed": {k: prof[k] for k in ("spgemm", "large_rows", "reduce", "other", "symmetry")},
             "clocks": clk,
         }
+        if tts is not None:
+            line["time_to_solution"] = tts
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -458,6 +471,166 @@ def diff_fro(S, D1, D2):
     S.ellpack_copy(A, Aw)
     S.ellpack_add(Aw, D2.to_torch(), 1.0, -1.0, 0.0)
     return float(np.sqrt(S.ellpack_frobenius2(Aw)))
+
+
+# ------------------------------------------------------------------ time to solution
+def _median_runs(fn, reps, warm=1):
+    """Runs fn() warm times untimed, then reps times; returns (median seconds, last result)."""
+    import torch
+    out = None
+    for _ in range(warm):
+        out = fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    return float(np.median(times)), out, times
+
+
+def time_to_solution(a, dev_id, reps=3):
+    """Whole SP2 purifications on one GPU, each entry the median of `reps` runs after a
+    warm-up, with the SM clocks sampled around it and the distance of every result to the
+    FP64 GPU run of the same input (||D - D_FP64||_F / sqrt(N), same tau):
+      C1: banded N = 1024, band 16 (the gapped variant: A/B onsite splitting 10), FP64,
+          iterations per second host-stepped (sp2_purify) and as one captured graph
+          (sp2_purify_batched of one matrix); the literal gapless configuration beside it;
+      C3: gapped 3D tight-binding N = 131072, FP64 against mixed precision;
+      C4: 256 gapped open clusters, N log-uniform in [512, 8192]: one graph launch in mixed
+          precision and in FP64, against FP64 purified one by one;
+      C5: gapped 3D tight-binding N = 1048576, input width 128: mixed precision with the
+          row-length MLP (trained here on about 50k rows of SP2 products of 4096 .. 16384
+          site Hamiltonians), mixed precision with the heuristic widths, and plain FP64."""
+    import torch
+    from paper_2102_08505_gb300 import inputs as I
+    from paper_2102_08505_gb300 import learned
+    from paper_2102_08505_gb300 import sp2ell as S
+    out = {}
+    tol = 1e-10
+
+    def clocked(fn):
+        c = Clocks(dev_id, enabled=not a.no_clocks)
+        r = fn()
+        r["clocks"] = c.stop()
+        return r
+
+    def dD(Dx, Dy, n):
+        return diff_fro(S, Dx, Dy) / np.sqrt(n)
+
+    # C1 ---------------------------------------------------------------------------
+    def c1():
+        r = {}
+        n, tau = 1024, 1e-5
+        Hg = S.Ellpack.from_numpy(*I.banded(n, band=16, seed=1, delta=10.0, width=64))
+        opt = S.sp2_options_default(tau=tau)
+        t_host, (D, st), _ = _median_runs(lambda: S.sp2_purify(Hg, n / 2, tol, opt), reps * 3)
+        optg = S.sp2_options_default(tau=tau, graph=1)
+        t_graph, (Dg, sg), _ = _median_runs(lambda: S.sp2_purify_batched([Hg], [n // 2], tol, optg), reps * 3)
+        r["gapped_delta10"] = {
+            "iterations": st["iterations"], "status": st["status"], "final_err": float(st["err"][-1]),
+            "host_stepped": {"time_s": t_host, "iters_per_s": st["iterations"] / t_host},
+            "graph": {"time_s": t_graph, "iters_per_s": sg[0]["iterations"] / t_graph,
+                      "iterations": sg[0]["iterations"], "dD_vs_host_stepped": dD(Dg[0], D, n)},
+            "max_row_nnz": int(max(st["max_row_nnz"]))}
+        H = S.Ellpack.from_numpy(*I.banded(n, band=16, seed=1, width=64))
+        t_lit, (Dl, sl), _ = _median_runs(lambda: S.sp2_purify(H, n / 2, tol, opt, allow_notconv=True), reps)
+        r["literal_gapless"] = {"time_s": t_lit, "iterations": sl["iterations"], "status": sl["status"],
+                                "final_err": float(sl["err"][-1]), "max_row_nnz": int(max(sl["max_row_nnz"])),
+                                "iters_per_s": sl["iterations"] / t_lit}
+        r["workload"] = "banded N=1024 band 16, nocc 512, tau 1e-5, tol 1e-10, input width 64"
+        return r
+    out["C1"] = clocked(c1)
+
+    # C3 ---------------------------------------------------------------------------
+    def c3():
+        n, tau = 131072, 1e-5
+        H = S.Ellpack.from_numpy(*I.tight_binding(n, seed=0, delta=10.0))
+        r, Ds = {}, {}
+        for name, prec in (("f64", S.SP2_PREC_F64), ("mixed", S.SP2_PREC_MIXED)):
+            opt = S.sp2_options_default(tau=tau, precision=prec)
+            t, (D, st), times = _median_runs(lambda: S.sp2_purify(H, n / 2, tol, opt), reps)
+            Ds[name] = D
+            r[name] = {"time_s": t, "times_s": times, "iterations": st["iterations"],
+                       "fp32_iterations": st["fp32_iterations"], "status": st["status"],
+                       "iters_per_s": st["iterations"] / t, "final_err": float(st["err"][-1])}
+        r["mixed"]["dD_vs_f64"] = dD(Ds["mixed"], Ds["f64"], n)
+        r["speedup_mixed_vs_f64"] = r["f64"]["time_s"] / r["mixed"]["time_s"]
+        r["workload"] = "3D tight-binding gapped (delta 10) N=131072, nocc N/2, tau 1e-5, tol 1e-10"
+        return r
+    out["C3"] = clocked(c3)
+
+    # C4 ---------------------------------------------------------------------------
+    def c4():
+        tau = 1e-5
+        sizes = I.cluster_sizes(256, 512, 8192, seed=0)
+        Hs = [S.Ellpack.from_numpy(*I.tight_binding(int(m), seed=k, delta=10.0, periodic=False))
+              for k, m in enumerate(sizes)]
+        noccs = [h.n // 2 for h in Hs]
+        r, Dsets = {}, {}
+        for name, prec in (("batched_mixed_graph", S.SP2_PREC_MIXED), ("batched_f64_graph", S.SP2_PREC_F64)):
+            opt = S.sp2_options_default(tau=tau, precision=prec, graph=1)
+            t, (Ds, sts), times = _median_runs(lambda: S.sp2_purify_batched(Hs, noccs, tol, opt), reps)
+            Dsets[name] = Ds
+            r[name] = {"time_s": t, "times_s": times, "iterations_total": int(sum(x["iterations"] for x in sts)),
+                       "max_iterations": int(max(x["iterations"] for x in sts))}
+        opt = S.sp2_options_default(tau=tau, precision=S.SP2_PREC_F64)
+
+        def one_by_one():
+            return [S.sp2_purify(H, m, tol, opt) for H, m in zip(Hs, noccs)]
+        t, res1, times = _median_runs(one_by_one, reps)
+        r["one_by_one_f64"] = {"time_s": t, "times_s": times, "iterations_total": int(sum(x[1]["iterations"] for x in res1))}
+        ref = [x[0] for x in res1]
+        for name in Dsets:
+            d = [dD(Dx, Dy, h.n) for Dx, Dy, h in zip(Dsets[name], ref, Hs)]
+            r[name]["dD_vs_one_by_one_f64_max"] = float(max(d))
+        r["speedup_batched_mixed_vs_one_by_one_f64"] = t / r["batched_mixed_graph"]["time_s"]
+        r["speedup_batched_mixed_vs_batched_f64"] = r["batched_f64_graph"]["time_s"] / r["batched_mixed_graph"]["time_s"]
+        r["workload"] = "256 gapped open 3D clusters, N log-uniform [512, 8192], sum N = %d, tau 1e-5" % int(sizes.sum())
+        return r
+    out["C4"] = clocked(c4)
+
+    # C5 ---------------------------------------------------------------------------
+    def c5():
+        n, tau = 1048576, 1e-5
+        t0 = time.perf_counter()
+        feat, counts = learned.default_training_set(seed=100, rows=50000, tau=tau, dtype=S.SP2_F32)
+        pred, loss = learned.train(feat, counts, seed=0, steps=1500, batch=2048, lr=2e-3)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        idx, val, nnz = I.tight_binding(n, seed=0, delta=10.0, width=128)
+        H = S.Ellpack.from_numpy(idx, val, nnz)
+        r, Ds = {"training": {"rows": int(counts.shape[0]), "collect_and_train_s": t_train, "final_batch_loss": loss}}, {}
+        for name, prec, sizing in (("plain_f64", S.SP2_PREC_F64, 0), ("mixed_heuristic", S.SP2_PREC_MIXED, 0),
+                                   ("mixed_mlp", S.SP2_PREC_MIXED, 2)):
+            kw = dict(tau=tau, precision=prec, sizing=sizing)
+            if sizing == 2:
+                kw["predictor"] = pred
+            opt = S.sp2_options_default(**kw)
+            t, (D, st), times = _median_runs(lambda: S.sp2_purify(H, n / 2, tol, opt), reps)
+            Ds[name] = D
+            r[name] = {"time_s": t, "times_s": times, "iterations": st["iterations"],
+                       "fp32_iterations": st["fp32_iterations"], "status": st["status"],
+                       "width_max": st["width_max"], "regrows": st["regrows"],
+                       "peak_product_bytes": int(st["width_max"]) * n * (12 if prec == S.SP2_PREC_F64 else 8)}
+            if sizing == 2:
+                r[name].update({"pred_log_mae": st["pred_log_mae"], "pred_under_frac": st["pred_under_frac"]})
+            del D
+        for name in ("mixed_heuristic", "mixed_mlp"):
+            r[name]["dD_vs_f64"] = dD(Ds[name], Ds["plain_f64"], n)
+        r["dD_mlp_vs_heuristic"] = dD(Ds["mixed_mlp"], Ds["mixed_heuristic"], n)
+        r["speedup_mixed_mlp_vs_plain_f64"] = r["plain_f64"]["time_s"] / r["mixed_mlp"]["time_s"]
+        r["speedup_mixed_mlp_vs_mixed_heuristic"] = r["mixed_heuristic"]["time_s"] / r["mixed_mlp"]["time_s"]
+        r["workload"] = "3D tight-binding gapped (delta 10) N=1048576, input width 128, tau 1e-5, tol 1e-10"
+        return r
+    out["C5"] = clocked(c5)
+    tgt = out["C5"]
+    out["target_met"] = bool(tgt["mixed_mlp"]["dD_vs_f64"] <= 1e-5 and tgt["speedup_mixed_mlp_vs_plain_f64"] > 1.0 and
+                             out["C3"]["mixed"]["dD_vs_f64"] <= 1e-5 and out["C3"]["speedup_mixed_vs_f64"] > 1.0 and
+                             out["C4"]["batched_mixed_graph"]["dD_vs_one_by_one_f64_max"] <= 1e-5 and
+                             out["C4"]["speedup_batched_mixed_vs_one_by_one_f64"] > 1.0)
+    return out
 
 
 def run_sp2(a):

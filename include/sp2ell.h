@@ -139,6 +139,47 @@ int ellpack_multiply(const ellpack_t *A, const ellpack_t *B, ellpack_t *C, doubl
                      double tau, void *stream, int32_t *required_width);
 
 /*
+ * One row block of a thresholded product, for a product whose rows are spread over
+ * several GPUs (the row-block split of the multiply; the paper's NUMA-aware placement of
+ * row blocks, Section "Micro-Kernel Performance Evaluation - NUMA Aware Data", carried to
+ * one block per GPU):
+ *
+ *     Out_r <- drop_tau(alpha * A_r * B + beta * C_r),   r = row0 .. row0 + A->n - 1
+ *
+ *   A, C and Out hold the block's rows (local row i is global row row0 + i) with global
+ *   column indices; B has the global row count (B->n = the product's column count) and
+ *   must hold every row k that A's entries name (local rows and the halo rows received
+ *   from other GPUs); its other rows are never read and may be empty.  C may be NULL when
+ *   beta == 0.  Keep rule, sorted rows and summation order as ellpack_multiply, so the
+ *   blocks of a product are bitwise the rows of the whole product.
+ *   trace, frobenius2 (optional, host): the block's share of tr(Out) (entries
+ *   (i, row0 + i)) and of ||Out||_F^2, to be summed over the blocks.
+ *   required_width (optional, host) and SP2E_OVERFLOW as for ellpack_multiply.
+ *   Synchronises `stream`.  Errors: SP2E_ARG, SP2E_OVERFLOW, SP2E_NOMEM, SP2E_CUDA.
+ */
+int ellpack_multiply_block(const ellpack_t *A, int32_t row0, const ellpack_t *B, const ellpack_t *C, ellpack_t *Out,
+                           double alpha, double beta, double tau, int32_t *required_width, double *trace,
+                           double *frobenius2, void *stream);
+
+/* The rest of the row-block split: the block's share of the set-up and of the traces.
+ * Each takes the block's rows (local row i is global row row0 + i, global columns).
+ *   ellpack_gershgorin_block: the Gershgorin bounds of the block's discs (the diagonal of
+ *     local row i is column row0 + i); the global bounds are the minimum and maximum over
+ *     the blocks.  Errors: SP2E_ARG, SP2E_NONFINITE, SP2E_CUDA.
+ *   sp2_x0_block: X0's rows of the block from the global bounds, as sp2_x0 (the block's
+ *     rows of drop_tau((emax I - H) / (emax - emin)), diagonal at column row0 + i).
+ *     Errors: SP2E_ARG, SP2E_NOMEM, SP2E_CUDA.
+ *   ellpack_stats_block: the block's share of tr X and of ||X||_F^2 (= tr X^2 for a
+ *     symmetric X), the "SP2 Loop Norm" quantities (Section "Performance Evaluation using
+ *     an ExaSP2 Application") to be summed over the blocks.  Errors: SP2E_ARG,
+ *     SP2E_NONFINITE, SP2E_NOMEM, SP2E_CUDA.
+ * All three synchronise `stream`. */
+int ellpack_gershgorin_block(const ellpack_t *H, int32_t row0, double *emin, double *emax, void *stream);
+int sp2_x0_block(const ellpack_t *H, int32_t row0, double emin, double emax, double tau, ellpack_t *X0,
+                 void *stream);
+int ellpack_stats_block(const ellpack_t *X, int32_t row0, double *trace, double *frobenius2, void *stream);
+
+/*
  * A <- drop_tau(alpha * A + beta * B) (the "SP2 Loop Misc" update, Section "Performance
  * Evaluation using an ExaSP2 Application"): pattern is the union of the two rows, keep
  * rule as in ellpack_multiply, rows sorted.  A and B share n and dtype and must not be
@@ -334,7 +375,7 @@ int ellpack_from_dense(const void *dense, int64_t ld, double tau, ellpack_t *A, 
  * counterpart.
  */
 #define SP2_PATH_TUNED (-1)
-#define SP2_TUNE_CANDIDATES 9  /* 1, 2, 4, 7, 3, 8, 10, 11, 12 in this order */
+#define SP2_TUNE_CANDIDATES 10  /* 1, 2, 4, 7, 3, 8, 9, 10, 11, 12 in this order */
 
 /* Times every variant on Out <- drop_tau(alpha A*B + beta C) (C may be NULL): one untimed
  * and `reps` timed runs each (CUDA events on `stream`); records the fastest for A's class

@@ -95,7 +95,8 @@ static int cmp_kv(const void *a, const void *b) {
  * out must have out->n >= nrows and a width out->w.  row_count[r] receives the
  * post-threshold number of entries of output row r even when it exceeds out->w; such
  * rows are left unwritten (nnz set to 0) and the function returns 1.  Returns 0 when
- * every row fitted, -1 on bad arguments.
+ * every row fitted, -1 on bad arguments (a row or column index outside 0 .. n-1
+ * included), -3 when host memory runs out.
  * diag (optional, length nrows): the unthresholded, unscaled sum_k a_ik b_ki of each row.
  */
 int orc_spgemm(const orc_ell *A, const orc_ell *B, const orc_ell *C, double alpha,
@@ -106,8 +107,8 @@ int orc_spgemm(const orc_ell *A, const orc_ell *B, const orc_ell *C, double alph
   if (B->n != n) return -1;
   if (beta != 0.0 && (!C || C->n != n)) return -1;
   if (rows == NULL) nrows = n;
-  int overflow = 0, nomem = 0;
-#pragma omp parallel num_threads(g_threads) reduction(| : overflow, nomem)
+  int overflow = 0, nomem = 0, badidx = 0;
+#pragma omp parallel num_threads(g_threads) reduction(| : overflow, nomem, badidx)
   {
     double *acc = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double *cv = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -134,10 +135,12 @@ int orc_spgemm(const orc_ell *A, const orc_ell *B, const orc_ell *C, double alph
       for (int t = 0; t < na; ++t) {
         int k = arow[t].k;
         double a = arow[t].a;
+        if (k < 0 || k >= n) { badidx = 1; continue; }
         int nb = B->nnz[k];
         for (int s = 0; s < nb; ++s) {
           int j = B->idx[(size_t)k * B->w + s];
           double b = B->val[(size_t)k * B->w + s];
+          if (j < 0 || j >= n) { badidx = 1; continue; }
           if (mark[j] != r) { mark[j] = r; acc[j] = 0.0; cv[j] = 0.0; list[cnt++] = j; }
           acc[j] = acc[j] + a * b;
         }
@@ -147,6 +150,7 @@ int orc_spgemm(const orc_ell *A, const orc_ell *B, const orc_ell *C, double alph
         int nc = C->nnz[i];
         for (int s = 0; s < nc; ++s) {
           int j = C->idx[(size_t)i * C->w + s];
+          if (j < 0 || j >= n) { badidx = 1; continue; }
           if (mark[j] != r) { mark[j] = r; acc[j] = 0.0; cv[j] = 0.0; list[cnt++] = j; }
           cv[j] = C->val[(size_t)i * C->w + s];
         }
@@ -173,6 +177,7 @@ int orc_spgemm(const orc_ell *A, const orc_ell *B, const orc_ell *C, double alph
     free(acc); free(cv); free(mark); free(list); free(arow);
   }
   if (nomem) return -3;
+  if (badidx) return -1;  /* a column index outside 0 .. n-1: not an n x n matrix */
   return overflow ? 1 : 0;
 }
 
@@ -192,11 +197,13 @@ int orc_add(const orc_ell *A, const orc_ell *B, double alpha, double beta, doubl
     int cnt = 0;
     for (int s = 0; s < A->nnz[i]; ++s) {
       int j = A->idx[(size_t)i * A->w + s];
+      if (j < 0 || j >= n) { free(av); free(bv); free(mark); free(list); return -1; }
       if (mark[j] != i) { mark[j] = i; av[j] = 0.0; bv[j] = 0.0; list[cnt++] = j; }
       av[j] = A->val[(size_t)i * A->w + s];
     }
     for (int s = 0; s < B->nnz[i]; ++s) {
       int j = B->idx[(size_t)i * B->w + s];
+      if (j < 0 || j >= n) { free(av); free(bv); free(mark); free(list); return -1; }
       if (mark[j] != i) { mark[j] = i; av[j] = 0.0; bv[j] = 0.0; list[cnt++] = j; }
       bv[j] = B->val[(size_t)i * B->w + s];
     }

@@ -386,9 +386,9 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
     return fail(SP2E_ARG, "sp2_purify_batched: unknown precision %d", opt.precision);
   if (opt.max_iter < 0 || opt.max_iter + opt.n_fp64_tail >= SP2_STATS_CAP || opt.n_fp64_tail < 0)
     return fail(SP2E_ARG, "sp2_purify_batched: bad max_iter / n_fp64_tail");
-  if (!(opt.spgemm_path == SP2_PATH_TUNED || (opt.spgemm_path >= 0 && opt.spgemm_path <= 4) || opt.spgemm_path == 7 ||
-        opt.spgemm_path == 8 || (opt.spgemm_path >= 10 && opt.spgemm_path <= 12)))
-    return fail(SP2E_ARG, "sp2_purify_batched: spgemm_path must be -1, 0..4, 7, 8 or 10..12");
+  if (!(opt.spgemm_path == SP2_PATH_TUNED || (opt.spgemm_path >= 0 && opt.spgemm_path <= 4) ||
+        (opt.spgemm_path >= 7 && opt.spgemm_path <= 12)))
+    return fail(SP2E_ARG, "sp2_purify_batched: spgemm_path must be -1, 0..4 or 7..12");
   if (!(opt.stall_arm > 0.0) || !isfinite(opt.stall_arm))
     return fail(SP2E_ARG, "sp2_purify_batched: stall_arm must be > 0");
   if (!(opt.stall_ratio > 0.0 && opt.stall_ratio <= 1.0))

@@ -236,15 +236,17 @@ int multiply_async(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cuda
 int add_async(ellpack_t *A, const ellpack_t *B, double alpha, double beta, double tau, double2 *rowstat,
               SpgemmCtl *ctl, cudaStream_t s);
 
-// rowstat of an existing matrix (diag, sum of squares).
-int rowstat_async(const ellpack_t *A, double2 *rowstat, cudaStream_t s);
+// rowstat of an existing matrix (diag, sum of squares); the diagonal of local row r is
+// column r + row0 (row0 > 0: A holds rows row0 .. of a larger matrix).
+int rowstat_async(const ellpack_t *A, double2 *rowstat, cudaStream_t s, int row0 = 0);
 
-// Gershgorin bounds into dev_bounds[0..1] = {emin, emax}.
-int gershgorin_async(const ellpack_t *H, double *dev_bounds, cudaStream_t s);
+// Gershgorin bounds into dev_bounds[0..1] = {emin, emax} (row0 as for rowstat_async: the
+// bounds of the discs of rows row0 .. of a larger matrix).
+int gershgorin_async(const ellpack_t *H, double *dev_bounds, cudaStream_t s, int row0 = 0);
 
 // X0 = drop_tau((emax I - H)/(emax - emin)), bounds read from dev_bounds on the device.
 // X->width >= H->width + 1, X->dtype == SP2_F64, H F64.
-int x0_async(const ellpack_t *H, const double *dev_bounds, double tau, ellpack_t *X, cudaStream_t s);
+int x0_async(const ellpack_t *H, const double *dev_bounds, double tau, ellpack_t *X, cudaStream_t s, int row0 = 0);
 
 // Element-type conversion (same n).  Rows longer than dst->width are left unwritten and
 // counted in *overflow (device int, may be null).

@@ -217,7 +217,7 @@ void launch_reduce_rows(const double2 *rowstat, const int *nnz, int n, const Spg
 
 // rowstat of a stored matrix: warp per row.
 template <typename T>
-__global__ void rowstat_kernel(EllView<T> A, double2 *__restrict__ rowstat) {
+__global__ void rowstat_kernel(EllView<T> A, int row0, double2 *__restrict__ rowstat) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < A.n; r += warps) {
@@ -226,7 +226,7 @@ __global__ void rowstat_kernel(EllView<T> A, double2 *__restrict__ rowstat) {
     for (int s = lane; s < k; s += 32) {
       const int j = A.idx[(size_t)r * A.w + s];
       const double v = (double)A.val[(size_t)r * A.w + s];
-      if (j == r) d += v;
+      if (j == r + row0) d += v;
       f += v * v;
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -243,19 +243,19 @@ static int grid_for_rows(int n, int warps_per_block) {
   return (int)(blocks < cap ? (blocks < 1 ? 1 : blocks) : cap);
 }
 
-int rowstat_async(const ellpack_t *A, double2 *rowstat, cudaStream_t s) {
+int rowstat_async(const ellpack_t *A, double2 *rowstat, cudaStream_t s, int row0) {
   int grid = grid_for_rows(A->n, 8);
   if (A->dtype == SP2_F64)
-    { rowstat_kernel<double><<<grid, 256, 0, s>>>(view<double>(A), rowstat); note_launch(); }
+    { rowstat_kernel<double><<<grid, 256, 0, s>>>(view<double>(A), row0, rowstat); note_launch(); }
   else
-    { rowstat_kernel<float><<<grid, 256, 0, s>>>(view<float>(A), rowstat); note_launch(); }
+    { rowstat_kernel<float><<<grid, 256, 0, s>>>(view<float>(A), row0, rowstat); note_launch(); }
   SP2_CUDA(cudaGetLastError());
   return SP2_OK;
 }
 
 // Gershgorin: per-block min/max partials, then one CTA reduces them in order.
 template <typename T>
-__global__ void gershgorin_rows_kernel(EllView<T> H, double2 *__restrict__ part) {
+__global__ void gershgorin_rows_kernel(EllView<T> H, int row0, double2 *__restrict__ part) {
   __shared__ double s_lo[8], s_hi[8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double lo = INFINITY, hi = -INFINITY;
@@ -266,7 +266,7 @@ __global__ void gershgorin_rows_kernel(EllView<T> H, double2 *__restrict__ part)
     for (int s = lane; s < k; s += 32) {
       const int j = H.idx[(size_t)r * H.w + s];
       const double v = (double)H.val[(size_t)r * H.w + s];
-      if (j == r) d += v; else rad += fabs(v);
+      if (j == r + row0) d += v; else rad += fabs(v);
     }
     for (int o = 16; o > 0; o >>= 1) {
       d += __shfl_xor_sync(0xffffffffu, d, o);
@@ -311,14 +311,14 @@ __global__ void minmax_reduce_kernel(const double2 *__restrict__ part, int m, do
   if (threadIdx.x == 0) { out[0] = s_lo[0]; out[1] = isnan(s_lo[0]) ? NAN : s_hi[0]; }
 }
 
-int gershgorin_async(const ellpack_t *H, double *dev_bounds, cudaStream_t s) {
+int gershgorin_async(const ellpack_t *H, double *dev_bounds, cudaStream_t s, int row0) {
   int grid = grid_for_rows(H->n, 8);
   double2 *part = nullptr;
   SP2_TRY(dev_alloc((void **)&part, sizeof(double2) * grid, s));
   if (H->dtype == SP2_F64)
-    { gershgorin_rows_kernel<double><<<grid, 256, 0, s>>>(view<double>(H), part); note_launch(); }
+    { gershgorin_rows_kernel<double><<<grid, 256, 0, s>>>(view<double>(H), row0, part); note_launch(); }
   else
-    { gershgorin_rows_kernel<float><<<grid, 256, 0, s>>>(view<float>(H), part); note_launch(); }
+    { gershgorin_rows_kernel<float><<<grid, 256, 0, s>>>(view<float>(H), row0, part); note_launch(); }
   { minmax_reduce_kernel<<<1, 256, 0, s>>>(part, grid, dev_bounds); note_launch(); }
   cudaError_t e = cudaGetLastError();
   dev_free(part, s);
@@ -330,7 +330,7 @@ int gershgorin_async(const ellpack_t *H, double *dev_bounds, cudaStream_t s) {
 // entries with column < i (in H's order), the diagonal, then the kept entries with
 // column > i -- sorted whenever H's row is sorted.  The diagonal is always stored
 // unless it falls below tau.
-__global__ void x0_kernel(EllView<double> H, const double *__restrict__ bounds, double tau,
+__global__ void x0_kernel(EllView<double> H, const double *__restrict__ bounds, double tau, int row0,
                           EllOut<double> X) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -339,6 +339,7 @@ __global__ void x0_kernel(EllView<double> H, const double *__restrict__ bounds, 
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < H.n; r += warps) {
     const int k = min(H.nnz[r], H.w);
+    const int dc = r + row0;  // column of the diagonal entry of local row r
     // pass 1: counts of kept entries below / above the diagonal, diagonal presence
     int n_lo = 0, has_diag = 0;
     double dval = emax * inv;  // value if H has no diagonal entry
@@ -349,19 +350,19 @@ __global__ void x0_kernel(EllView<double> H, const double *__restrict__ bounds, 
       if (s < k) {
         j = H.idx[(size_t)r * H.w + s];
         const double h = H.val[(size_t)r * H.w + s];
-        x = (j == r) ? (emax - h) * inv : -h * inv;
-        if (j == r) dval = x;
+        x = (j == dc) ? (emax - h) * inv : -h * inv;
+        if (j == dc) dval = x;
       }
-      const bool keep = (s < k) && j != r && (tau == 0.0 || fabs(x) > tau);
-      n_lo += __popc(__ballot_sync(0xffffffffu, keep && j < r));
-      has_diag |= __any_sync(0xffffffffu, j == r);
+      const bool keep = (s < k) && j != dc && (tau == 0.0 || fabs(x) > tau);
+      n_lo += __popc(__ballot_sync(0xffffffffu, keep && j < dc));
+      has_diag |= __any_sync(0xffffffffu, j == dc);
     }
     // the diagonal value lives in one lane; broadcast it
     {
       unsigned m = 0;
       for (int b = 0; b < k; b += 32) {
         const int s = b + lane;
-        const bool isd = s < k && H.idx[(size_t)r * H.w + s] == r;
+        const bool isd = s < k && H.idx[(size_t)r * H.w + s] == dc;
         m = __ballot_sync(0xffffffffu, isd);
         if (m) { dval = __shfl_sync(0xffffffffu, dval, __ffs(m) - 1); break; }
       }
@@ -378,11 +379,11 @@ __global__ void x0_kernel(EllView<double> H, const double *__restrict__ bounds, 
         const double h = H.val[(size_t)r * H.w + s];
         x = -h * inv;
       }
-      const bool keep = (s < k) && j != r && (tau == 0.0 || fabs(x) > tau);
-      const unsigned mlo = __ballot_sync(0xffffffffu, keep && j < r);
-      const unsigned mhi = __ballot_sync(0xffffffffu, keep && j > r);
+      const bool keep = (s < k) && j != dc && (tau == 0.0 || fabs(x) > tau);
+      const unsigned mlo = __ballot_sync(0xffffffffu, keep && j < dc);
+      const unsigned mhi = __ballot_sync(0xffffffffu, keep && j > dc);
       if (keep) {
-        const int pos = (j < r) ? lo_pos + __popc(mlo & lt) : hi_pos + __popc(mhi & lt);
+        const int pos = (j < dc) ? lo_pos + __popc(mlo & lt) : hi_pos + __popc(mhi & lt);
         X.idx[(size_t)r * X.w + pos] = j;
         X.val[(size_t)r * X.w + pos] = x;
       }
@@ -391,7 +392,7 @@ __global__ void x0_kernel(EllView<double> H, const double *__restrict__ bounds, 
     }
     if (lane == 0) {
       if (keep_diag) {
-        X.idx[(size_t)r * X.w + n_lo] = r;
+        X.idx[(size_t)r * X.w + n_lo] = dc;
         X.val[(size_t)r * X.w + n_lo] = dval;
       }
       X.nnz[r] = hi_pos;
@@ -400,11 +401,11 @@ __global__ void x0_kernel(EllView<double> H, const double *__restrict__ bounds, 
   }
 }
 
-int x0_async(const ellpack_t *H, const double *dev_bounds, double tau, ellpack_t *X, cudaStream_t s) {
+int x0_async(const ellpack_t *H, const double *dev_bounds, double tau, ellpack_t *X, cudaStream_t s, int row0) {
   if (H->dtype != SP2_F64 || X->dtype != SP2_F64) return fail(SP2E_ARG, "x0: F64 matrices expected");
   if (X->width < H->width + 1) return fail(SP2E_ARG, "x0: output width too small");
   int grid = grid_for_rows(H->n, 8);
-  { x0_kernel<<<grid, 256, 0, s>>>(view<double>(H), dev_bounds, tau, outview<double>(X)); note_launch(); }
+  { x0_kernel<<<grid, 256, 0, s>>>(view<double>(H), dev_bounds, tau, row0, outview<double>(X)); note_launch(); }
   SP2_CUDA(cudaGetLastError());
   return SP2_OK;
 }
@@ -604,6 +605,55 @@ extern "C" int ellpack_gershgorin(const ellpack_t *H, double *emin, double *emax
   *emin = hb[0];
   *emax = hb[1];
   if (!isfinite(hb[0]) || !isfinite(hb[1])) return fail(SP2E_NONFINITE, "ellpack_gershgorin: non-finite bound");
+  return SP2_OK;
+}
+
+extern "C" int ellpack_gershgorin_block(const ellpack_t *H, int32_t row0, double *emin, double *emax, void *stream) {
+  SP2_TRY(check_matrix(H, "ellpack_gershgorin_block"));
+  if (!emin || !emax) return fail(SP2E_ARG, "ellpack_gershgorin_block: null output");
+  if (row0 < 0) return fail(SP2E_ARG, "ellpack_gershgorin_block: row0 = %d must be >= 0", row0);
+  cudaStream_t s = as_stream(stream);
+  double *db = nullptr;
+  SP2_TRY(dev_alloc((void **)&db, 2 * sizeof(double), s));
+  int rc = gershgorin_async(H, db, s, row0);
+  double hb[2] = {0, 0};
+  if (rc == SP2_OK) {
+    cudaError_t e = cudaMemcpyAsync(hb, db, sizeof(hb), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "gershgorin copy", __FILE__, __LINE__);
+  }
+  dev_free(db, s);
+  SP2_TRY(rc);
+  *emin = hb[0];
+  *emax = hb[1];
+  if (!isfinite(hb[0]) || !isfinite(hb[1])) return fail(SP2E_NONFINITE, "ellpack_gershgorin_block: non-finite bound");
+  return SP2_OK;
+}
+
+extern "C" int ellpack_stats_block(const ellpack_t *X, int32_t row0, double *trace, double *frobenius2,
+                                   void *stream) {
+  SP2_TRY(check_matrix(X, "ellpack_stats_block"));
+  if (!trace || !frobenius2) return fail(SP2E_ARG, "ellpack_stats_block: null output");
+  if (row0 < 0) return fail(SP2E_ARG, "ellpack_stats_block: row0 = %d must be >= 0", row0);
+  cudaStream_t s = as_stream(stream);
+  double2 *rowstat = nullptr;
+  StepResult *dres = nullptr;
+  SP2_TRY(dev_alloc((void **)&rowstat, sizeof(double2) * (size_t)X->n, s));
+  int rc = dev_alloc((void **)&dres, sizeof(StepResult), s);
+  StepResult h{};
+  if (rc == SP2_OK) rc = rowstat_async(X, rowstat, s, row0);
+  if (rc == SP2_OK) {
+    launch_reduce_rows(rowstat, X->nnz, X->n, nullptr, dres, s);
+    cudaError_t e = cudaMemcpyAsync(&h, dres, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "ellpack_stats_block", __FILE__, __LINE__);
+  }
+  dev_free(rowstat, s);
+  dev_free(dres, s);
+  SP2_TRY(rc);
+  *trace = h.tr;
+  *frobenius2 = h.fro;
+  if (!isfinite(h.tr) || !isfinite(h.fro)) return fail(SP2E_NONFINITE, "ellpack_stats_block: non-finite result");
   return SP2_OK;
 }
 

@@ -46,7 +46,7 @@ int read_result(Buffers &b, StepResult *h) {
 }
 
 // (Re)allocates m with at least `width` slots and the given dtype; contents undefined.
-bool valid_path(int p) { return p == SP2_PATH_TUNED || (p >= 0 && p <= 4) || p == 7 || p == 8 || (p >= 10 && p <= 12); }
+bool valid_path(int p) { return p == SP2_PATH_TUNED || (p >= 0 && p <= 4) || (p >= 7 && p <= 12); }
 
 int ensure(ellpack_t *m, int n, int width, int dtype, cudaStream_t s) {
   if (m->owner && m->width >= width && m->dtype == dtype) return SP2_OK;
@@ -100,7 +100,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   if (opt.max_iter < 0 || opt.max_iter + opt.n_fp64_tail >= SP2_STATS_CAP)
     return fail(SP2E_ARG, "sp2_purify: max_iter + n_fp64_tail must be < %d", SP2_STATS_CAP);
   if (opt.n_fp64_tail < 0) return fail(SP2E_ARG, "sp2_purify: n_fp64_tail < 0");
-  if (!valid_path(opt.spgemm_path)) return fail(SP2E_ARG, "sp2_purify: spgemm_path must be -1, 0..4, 7, 8 or 10..12");
+  if (!valid_path(opt.spgemm_path)) return fail(SP2E_ARG, "sp2_purify: spgemm_path must be -1, 0..4 or 7..12");
   const int max_w = (opt.max_width > 0 && opt.max_width < n) ? opt.max_width : n;
   if (!(opt.switch_tol >= 0.0) || !isfinite(opt.switch_tol)) return fail(SP2E_ARG, "sp2_purify: bad switch_tol");
   if (opt.sizing < 0 || opt.sizing > 2) return fail(SP2E_ARG, "sp2_purify: sizing must be 0, 1 or 2");
@@ -375,6 +375,34 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   return SP2_OK;
 }
 
+extern "C" int sp2_x0_block(const ellpack_t *H, int32_t row0, double emin, double emax, double tau, ellpack_t *X0,
+                            void *stream) {
+  SP2_TRY(check_matrix(H, "sp2_x0_block: H"));
+  SP2_TRY(check_matrix(X0, "sp2_x0_block: X0"));
+  if (H->n != X0->n) return fail(SP2E_ARG, "sp2_x0_block: H and X0 hold different row counts");
+  if (H->dtype != SP2_F64 || X0->dtype != SP2_F64) return fail(SP2E_ARG, "sp2_x0_block: F64 matrices expected");
+  if (X0->width < H->width + 1) return fail(SP2E_ARG, "sp2_x0_block: X0 width %d < H width + 1", X0->width);
+  if (X0->idx == H->idx || X0->val == H->val || X0->nnz == H->nnz) return fail(SP2E_ARG, "sp2_x0_block: X0 aliases H");
+  if (row0 < 0) return fail(SP2E_ARG, "sp2_x0_block: row0 = %d must be >= 0", row0);
+  if (!(tau >= 0.0) || !isfinite(tau)) return fail(SP2E_ARG, "sp2_x0_block: tau must be finite and >= 0");
+  if (!isfinite(emin) || !isfinite(emax) || !(emax > emin))
+    return fail(SP2E_ARG, "sp2_x0_block: bounds must be finite with emax > emin");
+  cudaStream_t s = as_stream(stream);
+  double *db = nullptr;
+  SP2_TRY(dev_alloc((void **)&db, 2 * sizeof(double), s));
+  const double hb[2] = {emin, emax};
+  int rc = SP2_OK;
+  cudaError_t e = cudaMemcpyAsync(db, hb, sizeof(hb), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) rc = cuda_fail(e, "sp2_x0_block bounds", __FILE__, __LINE__);
+  if (rc == SP2_OK) rc = x0_async(H, db, tau, X0, s, row0);
+  if (rc == SP2_OK) {
+    e = cudaStreamSynchronize(s);  // the bounds live in a stack array until the copy is done
+    if (e != cudaSuccess) rc = cuda_fail(e, "sp2_x0_block", __FILE__, __LINE__);
+  }
+  dev_free(db, s);
+  return rc;
+}
+
 extern "C" int sp2_x0(const ellpack_t *H, double tau, ellpack_t *X0, double *emin, double *emax, void *stream) {
   SP2_TRY(check_matrix(H, "sp2_x0: H"));
   SP2_TRY(check_matrix(X0, "sp2_x0: X0"));
@@ -416,7 +444,7 @@ extern "C" int sp2_step(const ellpack_t *X, ellpack_t *Xn, double nocc, double t
   if (X->idx == Xn->idx || X->val == Xn->val || X->nnz == Xn->nnz) return fail(SP2E_ARG, "sp2_step: Xn aliases X");
   if (!(tau >= 0.0) || !isfinite(tau)) return fail(SP2E_ARG, "sp2_step: tau must be finite and >= 0");
   if (!isfinite(nocc)) return fail(SP2E_ARG, "sp2_step: nocc not finite");
-  if (!valid_path(info->spgemm_path)) return fail(SP2E_ARG, "sp2_step: spgemm_path must be -1, 0..4, 7, 8 or 10..12");
+  if (!valid_path(info->spgemm_path)) return fail(SP2E_ARG, "sp2_step: spgemm_path must be -1, 0..4 or 7..12");
   const int n = X->n;
   Buffers b;
   b.s = as_stream(stream);

@@ -27,11 +27,10 @@
 
 #include <type_traits>
 
-#include "common.cuh"
+#include "spgemm_internal.cuh"
 
 namespace sp2 {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kEmpty = -1;
 // Rows of A with more entries than this skip the one-warp first pass (spgemm_super_kernel)
 // and go straight to the deferred-row bins, whose one CTA per row suits their work
@@ -40,16 +39,9 @@ constexpr int kEmpty = -1;
 // blocks finish faster than in the bins, several rows per SM at a time.
 constexpr int kHeavyRowA = 512;
 
-__device__ __forceinline__ unsigned lanemask_lt() {
-  unsigned m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
-}
 
 __device__ __forceinline__ double absval(double x) { return fabs(x); }
 __device__ __forceinline__ float absval(float x) { return fabsf(x); }
-__device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
 
 
 // Slot layout: columns are taken in groups of 32 (j >> 5).  A group g owns the aligned
@@ -113,12 +105,6 @@ __device__ __forceinline__ void load_brow(const EllView<T> &B, int k, int st, in
   }
 }
 
-// Drop rule |v| > tau evaluated on the bit patterns: for IEEE values with the sign bit
-// cleared the integer order is the numeric order, so the test runs on the integer pipe
-// (the FP64 pipe of this GPU is narrow).  A NaN compares above tau and is kept, so it
-// reaches the traces and is reported instead of vanishing.
-__device__ __forceinline__ long long mag_bits(double v) { return __double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFLL; }
-__device__ __forceinline__ int mag_bits(float v) { return __float_as_int(v) & 0x7FFFFFFF; }
 
 template <typename T>
 __device__ __forceinline__ bool keep_value(T v, T tau) {
@@ -177,11 +163,6 @@ __device__ __forceinline__ void sort_prefix(int *keys, T *vals, int nk, int lane
   }
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
 
 // Table geometry: 2^LOG2T slots of (int key, T value) per warp; a row is deferred to a
 // larger table once more than LIMIT = 7/8 of the slots hold keys.  As many warps per
@@ -431,13 +412,6 @@ struct BlockGeo {
   static constexpr unsigned MAX_GROUP = (1u << 24) - 1u;
 };
 
-__device__ __forceinline__ bool is_untouched(double v) {
-  return __double_as_longlong(v) == (long long)0xFFF4A5A5A5A5A5A5ULL;
-}
-__device__ __forceinline__ bool is_untouched(float v) { return __float_as_uint(v) == 0xFFA5A5A5u; }
-template <typename T> __device__ __forceinline__ T untouched();
-template <> __device__ __forceinline__ double untouched<double>() { return __longlong_as_double((long long)0xFFF4A5A5A5A5A5A5ULL); }
-template <> __device__ __forceinline__ float untouched<float>() { return __uint_as_float(0xFFA5A5A5u); }
 
 template <int LOG2G>
 __device__ __forceinline__ int ghash(unsigned g) { return (int)((g * 0x9E3779B1u) >> (32 - LOG2G)); }
@@ -804,9 +778,11 @@ __global__ void __launch_bounds__(BlockGeo<T, R, SZ>::WARPS * 32, 1)
         if (keep) {
           const int pos = nk + __popc(m & lt);
           if (pos < Out.w) { oi[pos] = j; ov[pos] = v; }
-          const double dv = (double)v;
-          if (j == r) dsum += dv;
-          fsum = fma(dv, dv, fsum);
+          if (!up.tp) {  // upper-triangle rows: the mirror pass takes the statistics of the full rows
+            const double dv = (double)v;
+            if (j == r) dsum += dv;
+            fsum = fma(dv, dv, fsum);
+          }
         }
         nk += __popc(m);
       }
@@ -1085,9 +1061,11 @@ __global__ void __launch_bounds__(BlockGeo<T, 1, SZ>::WARPS * 32, 1)
       if (keep) {
         const int pos = nk + __popc(m & lt);
         if (pos < Out.w) { oi[pos] = j; ov[pos] = v; }
-        const double dv = (double)v;
-        if (j == r) dsum += dv;
-        fsum = fma(dv, dv, fsum);
+        if (!up.tp) {  // upper-triangle rows: the mirror pass takes the statistics of the full rows
+          const double dv = (double)v;
+          if (j == r) dsum += dv;
+          fsum = fma(dv, dv, fsum);
+        }
       }
       nk += __popc(m);
     }
@@ -1143,7 +1121,7 @@ __global__ void __launch_bounds__(kDenseThreads)
                         int *__restrict__ mark_all) {
   __shared__ int s_warp[kDenseThreads / 32];
   __shared__ double s_d[kDenseThreads / 32], s_f[kDenseThreads / 32];
-  const int n = A.n;
+  const int n = Out.n;  // columns of the product
   const int nfb = *((volatile const int *)fb_count);
   T *acc = acc_all + (size_t)blockIdx.x * n;
   int *mark = mark_all + (size_t)blockIdx.x * n;
@@ -1767,6 +1745,7 @@ int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
     case 3: rc = launch_super_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 7: rc = launch_block_compact<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 8: rc = launch_super_compact<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
+    case 9: rc = launch_tile<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     default:  // automatic: the variant measured fastest on the 3D tight-binding products
               // (FP64: column blocks, 4 warps per row, 2 in the compact form; FP32: one warp
               // per row, two k steps per pass), in its compact form for the upper triangle
@@ -1869,7 +1848,7 @@ int multiply_t(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, cudaStre
     int *mark = nullptr;
     int slots = kFallbackSlots;
     if (slots > n) slots = n;
-    rc = fallback_scratch(n, a.A->dtype, slots, &acc, &mark, s);
+    rc = fallback_scratch(a.Out->n, a.A->dtype, slots, &acc, &mark, s);  // one dense row per slot
     if (rc == SP2_OK) {
       const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
       spgemm_dense_kernel<T><<<slots, kDenseThreads, 0, s>>>(
@@ -1989,6 +1968,64 @@ extern "C" int ellpack_multiply(const ellpack_t *A, const ellpack_t *B, ellpack_
   }
   dev_free(rowstat, s);
   dev_free(ctl, s);
+  return rc;
+}
+
+extern "C" int ellpack_multiply_block(const ellpack_t *A, int32_t row0, const ellpack_t *B, const ellpack_t *C,
+                                      ellpack_t *Out, double alpha, double beta, double tau, int32_t *required_width,
+                                      double *trace, double *frobenius2, void *stream) {
+  SP2_TRY(check_matrix(A, "ellpack_multiply_block: A"));
+  SP2_TRY(check_matrix(B, "ellpack_multiply_block: B"));
+  SP2_TRY(check_matrix(Out, "ellpack_multiply_block: Out"));
+  if (beta != 0.0) SP2_TRY(check_matrix(C, "ellpack_multiply_block: C"));
+  SP2_TRY(check_tau(tau, "ellpack_multiply_block"));
+  if (A->n != Out->n || (beta != 0.0 && C->n != A->n))
+    return fail(SP2E_ARG, "ellpack_multiply_block: A, C and Out must hold the same rows");
+  if (row0 < 0 || (long long)row0 + A->n > (long long)B->n)
+    return fail(SP2E_ARG, "ellpack_multiply_block: rows %d .. %lld are not rows of B (n = %d)", row0,
+                (long long)row0 + A->n - 1, B->n);
+  if (A->dtype != B->dtype || A->dtype != Out->dtype || (beta != 0.0 && C->dtype != A->dtype))
+    return fail(SP2E_ARG, "ellpack_multiply_block: dtypes differ");
+  if (same_arrays(Out, A) || same_arrays(Out, B) || (beta != 0.0 && same_arrays(Out, C)))
+    return fail(SP2E_ARG, "ellpack_multiply_block: Out aliases an input");
+  if (!isfinite(alpha) || !isfinite(beta)) return fail(SP2E_ARG, "ellpack_multiply_block: alpha/beta not finite");
+  cudaStream_t s = as_stream(stream);
+  const int nb = A->n;
+  double2 *rowstat = nullptr;
+  SpgemmCtl *ctl = nullptr;
+  StepResult *dres = nullptr;
+  SP2_TRY(dev_alloc((void **)&rowstat, sizeof(double2) * (size_t)nb, s));
+  int rc = dev_alloc((void **)&ctl, sizeof(SpgemmCtl), s);
+  if (rc == SP2_OK) rc = dev_alloc((void **)&dres, sizeof(StepResult), s);
+  if (rc == SP2_OK) {
+    // the product's columns are B's rows: the output view spans B->n columns, while the
+    // kernels write only A's rows
+    ellpack_t wide = *Out;
+    wide.n = B->n;
+    MultiplyArgs a{A, B, beta != 0.0 ? C : nullptr, &wide, alpha, beta, tau, 0};
+    rc = multiply_async(a, rowstat, ctl, s);
+    // statistics of the block's rows: the diagonal of local row r is column row0 + r
+    if (rc == SP2_OK) rc = rowstat_async(Out, rowstat, s, row0);
+    if (rc == SP2_OK) {
+      launch_reduce_rows(rowstat, Out->nnz, nb, ctl, dres, s);
+      StepResult h;
+      cudaError_t e = cudaMemcpyAsync(&h, dres, sizeof(h), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        rc = cuda_fail(e, "ellpack_multiply_block", __FILE__, __LINE__);
+      } else {
+        if (required_width) *required_width = h.max_count;
+        if (trace) *trace = h.tr;
+        if (frobenius2) *frobenius2 = h.fro;
+        if (h.overflow_rows > 0)
+          rc = fail(SP2E_OVERFLOW, "ellpack_multiply_block: %d row(s) need %d slots, output width is %d",
+                    h.overflow_rows, h.max_count, Out->width);
+      }
+    }
+  }
+  dev_free(rowstat, s);
+  dev_free(ctl, s);
+  dev_free(dres, s);
   return rc;
 }
 

@@ -1,8 +1,9 @@
 // tune.cu -- autotuner of the SpGEMM first pass.
 //
 // The first-pass variants (column blocks with 1, 2 or 4 warps per row, the one-warp
-// two-k-step variant, the compact forms of both for symmetric products, per-warp hash
-// tables of 2^10..2^12 slots) compute the same product;
+// two-k-step variant, the compact forms of both for symmetric products, the row tiles
+// with a shared column index, per-warp hash tables of 2^10..2^12 slots) compute the same
+// product;
 // which is fastest depends on the device, the element type, the matrix size and the row
 // lengths.  The tuner times every variant on a real product, keeps the fastest in a
 // table keyed by (SM count, dtype, floor(log2 n), floor(log2 mean row length of A)), and
@@ -22,7 +23,7 @@
 namespace sp2 {
 namespace {
 
-constexpr int kCandidates[] = {1, 2, 4, 7, 3, 8, 10, 11, 12};
+constexpr int kCandidates[] = {1, 2, 4, 7, 3, 8, 9, 10, 11, 12};
 constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
 static_assert(kNumCandidates == SP2_TUNE_CANDIDATES, "candidate count");
 

@@ -105,6 +105,10 @@ def _load():
         "ellpack_trace": ([E, P(D), V], ctypes.c_int),
         "ellpack_frobenius2": ([E, P(D), V], ctypes.c_int),
         "ellpack_gershgorin": ([E, P(D), P(D), V], ctypes.c_int),
+        "ellpack_multiply_block": ([E, I, E, E, E, D, D, D, P(I), P(D), P(D), V], ctypes.c_int),
+        "ellpack_gershgorin_block": ([E, I, P(D), P(D), V], ctypes.c_int),
+        "sp2_x0_block": ([E, I, D, D, D, E, V], ctypes.c_int),
+        "ellpack_stats_block": ([E, I, P(D), P(D), V], ctypes.c_int),
         "sp2_fma_peak": ([I, I, P(D), V], ctypes.c_int),
         "ellpack_trace_noalloc": ([E, P(D), P(D), V], ctypes.c_int),
         "sp2_options_default": ([P(sp2_options)], None),
@@ -292,6 +296,40 @@ def ellpack_multiply(A, B, C, alpha=1.0, beta=0.0, tau=0.0, stream=None, raise_o
         return rc, req.value
     _check(rc)
     return req.value
+
+
+def ellpack_multiply_block(A, row0, B, C, Out, alpha=1.0, beta=0.0, tau=0.0, stream=None, raise_on_overflow=True):
+    """Out <- drop_tau(alpha A B + beta C) for the row block held by A, C and Out (global
+    rows row0 .. row0 + A.n - 1, global column indices; B has the global row count and
+    holds every row A names).  Returns (status, required width, block trace, block
+    squared Frobenius norm)."""
+    req, tr, fro = ctypes.c_int32(0), ctypes.c_double(), ctypes.c_double()
+    rc = lib.ellpack_multiply_block(_d(A), int(row0), _d(B), _d(C) if C is not None else None, _d(Out),
+                                    float(alpha), float(beta), float(tau), ctypes.byref(req), ctypes.byref(tr),
+                                    ctypes.byref(fro), _stream(stream))
+    if rc == SP2E_OVERFLOW and not raise_on_overflow:
+        return rc, req.value, None, None
+    _check(rc)
+    return rc, req.value, tr.value, fro.value
+
+
+def ellpack_gershgorin_block(H, row0, stream=None):
+    """Gershgorin bounds (emin, emax) of the discs of a row block (global rows row0 ..)."""
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(lib.ellpack_gershgorin_block(_d(H), int(row0), ctypes.byref(lo), ctypes.byref(hi), _stream(stream)))
+    return lo.value, hi.value
+
+
+def sp2_x0_block(H, row0, emin, emax, tau, X0, stream=None):
+    """X0's rows of a row block from the global spectral bounds."""
+    _check(lib.sp2_x0_block(_d(H), int(row0), float(emin), float(emax), float(tau), _d(X0), _stream(stream)))
+
+
+def ellpack_stats_block(X, row0, stream=None):
+    """(block share of tr X, block share of ||X||_F^2)."""
+    tr, fro = ctypes.c_double(), ctypes.c_double()
+    _check(lib.ellpack_stats_block(_d(X), int(row0), ctypes.byref(tr), ctypes.byref(fro), _stream(stream)))
+    return tr.value, fro.value
 
 
 def ellpack_add(A, B, alpha=1.0, beta=1.0, tau=0.0, stream=None):
@@ -524,7 +562,7 @@ class NnzPredictor:
 
 
 # ---------------------------------------------------------------- autotuner
-TUNE_CANDIDATES = (1, 2, 4, 7, 3, 8, 10, 11, 12)
+TUNE_CANDIDATES = (1, 2, 4, 7, 3, 8, 9, 10, 11, 12)
 
 
 def sp2_tune_spgemm(A, B, C, Out, alpha=1.0, beta=0.0, tau=0.0, reps=3, stream=None):

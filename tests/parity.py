@@ -127,3 +127,43 @@ def sparse_of(idx, val, nnz, n):
 def sparse_fro(M):
     """Frobenius norm of a scipy sparse matrix."""
     return float(np.sqrt((M.multiply(M)).sum()))
+
+
+def compare_density(gpu, Do, tau, rows=None, rel=F64_REL):
+    """Per-entry check of an FP64 SP2 result against the oracle's D (Do, an oracle Ell).
+
+    The scale of entry (i, j) is S_ij = (|D| |D|)_ij + |D_ij| from the oracle's D: at
+    convergence D is close to the last iterate X, so S_ij is the error-bound scale of the
+    last update (X^2 or 2X - X^2) at that entry.  Values of entries stored on both sides
+    must agree within rel * S_ij; an entry may be stored on one side only if its magnitude
+    lies within rel * S_ij of tau (the drop decision there depends on rounding).
+    rows: compare only these rows (all if None).  Returns statistics."""
+    gidx, gval, gnnz = gpu
+    sel = np.arange(len(gnnz)) if rows is None else np.asarray(rows)
+    absD = _abs(Do)
+    scale = O.spgemm(absD, absD, absD, 1.0, 1.0, 0.0, rows=sel)
+    gk, gv = coo(gidx, gval, gnnz, sel)
+    rk, rv = coo(Do.idx, Do.val, Do.nnz, sel)
+    sk, sv = coo(scale.idx, scale.val, scale.nnz)
+    assert sorted_rows_ok(gidx[sel], gnnz[sel]), "GPU rows not strictly sorted"
+    bound_g = rel * _lookup(sk, sv, gk)[1] + 1e-300
+    found, _ = _lookup(sk, sv, gk)
+    assert found.all(), "GPU stores %d entries outside the pattern of D^2 + D" % int((~found).sum())
+    in_ref = np.isin(gk, rk, assume_unique=True)
+    cr = rv[np.searchsorted(rk, gk[in_ref])]
+    diff = np.abs(gv[in_ref] - cr)
+    bad = diff > bound_g[in_ref]
+    assert not bad.any(), "%d entries of D out of tolerance; worst ratio %.3g" % (
+        int(bad.sum()), float((diff / bound_g[in_ref]).max()))
+    g_only = ~in_ref
+    r_only = ~np.isin(rk, gk, assume_unique=True)
+    if tau == 0.0:
+        assert not g_only.any() and not r_only.any(), "column sets of D differ at tau = 0"
+    else:
+        if g_only.any():
+            assert np.all(np.abs(np.abs(gv[g_only]) - tau) <= bound_g[g_only]), "GPU kept an entry of D clearly below tau"
+        if r_only.any():
+            b = rel * _lookup(sk, sv, rk[r_only])[1] + 1e-300
+            assert np.all(np.abs(np.abs(rv[r_only]) - tau) <= b), "GPU dropped an entry of D clearly above tau"
+    return {"entries": int(len(gk)), "worst_ratio": float((diff / bound_g[in_ref]).max()) if len(diff) else 0.0,
+            "max_abs_diff": float(diff.max()) if len(diff) else 0.0, "flips": int(g_only.sum() + r_only.sum())}

@@ -5,7 +5,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2102_08505_gb300 import inputs as I
-from parity import dense_of
+from parity import compare_density, dense_of
 
 pytestmark = pytest.mark.gpu
 
@@ -41,6 +41,7 @@ def test_batched_f64_matches_oracle(gpu, graph):
         assert st["status"] == so["status"], m
         assert np.allclose(st["trX"], so["trX"], rtol=1e-11, atol=1e-9)
         assert np.linalg.norm(dense_D(D) - Do.to_dense()) / np.sqrt(H.n) < 1e-10, m
+        compare_density(D.to_numpy(), Do, tau)  # entry by entry
 
 
 def test_batched_mixed_within_1e5_of_oracle(gpu):

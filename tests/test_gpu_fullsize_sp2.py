@@ -10,7 +10,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2102_08505_gb300 import inputs as I
-from parity import sparse_fro, sparse_of
+from parity import compare_density, sparse_fro, sparse_of
 
 pytestmark = pytest.mark.gpu
 
@@ -34,6 +34,9 @@ def test_fullsize_sp2_f64_and_mixed_against_oracle(gpu):
     assert np.allclose(s64["trX"], so["trX"], rtol=1e-11, atol=0)
     d64 = sparse_fro(sparse_of(*D64.to_numpy(), N) - ref) / math.sqrt(N)
     assert d64 < 1e-10, d64
+    # entry by entry on 2000 sampled rows (and the first and last)
+    rows = np.unique(np.concatenate([[0, N - 1], np.random.default_rng(5).choice(N, 2000, replace=False)]))
+    print("full size fp64 per entry: %s" % compare_density(D64.to_numpy(), Do, TAU, rows=rows))
 
     Dm, sm = S.sp2_purify(dH, N // 2, TOL, S.sp2_options_default(tau=TAU, precision=S.SP2_PREC_MIXED),
                           allow_notconv=True)

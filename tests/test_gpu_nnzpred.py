@@ -113,6 +113,15 @@ def test_stats_grad_and_predict_match_oracle(gpu, trainset):
     assert loss == pytest.approx(lo, rel=1e-4)
     g = g.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go)
+    # block by block (W1, b1, W2, b2, w3, b3): each block's norm, and each element against its
+    # block's largest entry, so that one wrong block or element cannot hide in the whole
+    names = ("W1", "b1", "W2", "b2", "w3", "b3")
+    for name, gb, ob in zip(names, M.unpack(g), M.unpack(go)):
+        gb, ob = np.atleast_1d(gb).ravel(), np.atleast_1d(ob).ravel()
+        scale = np.abs(ob).max()
+        assert scale > 0, name
+        assert np.linalg.norm(gb - ob) <= 1e-4 * np.linalg.norm(ob) + 1e-7 * scale, name
+        assert np.abs(gb - ob).max() <= 1e-3 * scale, (name, float(np.abs(gb - ob).max() / scale))
     pred = p.predict(feat).cpu().numpy()
     ref = M.predict_counts(theta.astype(np.float64), stats.astype(np.float64), f64)
     np.testing.assert_allclose(pred, ref, rtol=2e-4, atol=1e-3)

@@ -4,7 +4,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2102_08505_gb300 import inputs as I
-from parity import compare_spgemm, dense_of
+from parity import compare_density, compare_spgemm, dense_of
 
 pytestmark = pytest.mark.gpu
 
@@ -50,6 +50,10 @@ def test_sp2_banded_f64_matches_oracle(gpu, delta):
     Dg, Dr = dense_D(D), Do.to_dense()
     assert np.linalg.norm(Dg - Dr) / np.sqrt(n) < 1e-10
     assert np.abs(Dg - Dr).max() < 1e-8
+    # entry by entry: each within 1e-12 of its error-bound scale, column sets equal except
+    # at entries within that bound of tau
+    rep = compare_density(D.to_numpy(), Do, tau)
+    print("banded delta %g: %s" % (delta, rep))
 
 
 def test_sp2_3d_gapped_f64_and_mixed(gpu):
@@ -68,6 +72,7 @@ def test_sp2_3d_gapped_f64_and_mixed(gpu):
     D64, s64 = S.sp2_purify(dev(S, H), n // 2, tol, S.sp2_options_default(tau=tau))
     assert s64["iterations"] == so["iterations"] and s64["branch"] == so["branch"]
     assert np.linalg.norm(dense_D(D64) - Dr) / np.sqrt(n) < 1e-10
+    print("3d gapped fp64: %s" % compare_density(D64.to_numpy(), Do, tau))
     Dm, sm = S.sp2_purify(dev(S, H), n // 2, tol, S.sp2_options_default(tau=tau, precision=S.SP2_PREC_MIXED),
                           allow_notconv=True)
     Dmd = dense_D(Dm)
@@ -142,6 +147,7 @@ def test_sp2_stall_arm_matches_oracle(gpu, arm, ratio):
                          allow_notconv=True)
     assert sg["iterations"] == so["iterations"] and sg["status"] == so["status"] and sg["branch"] == so["branch"]
     assert np.abs(dense_D(D) - Do.to_dense()).max() < 1e-8
+    compare_density(D.to_numpy(), Do, 1e-5)
     with pytest.raises(S.Sp2Error):
         S.sp2_purify(dev(S, H), n // 2, 1e-10, S.sp2_options_default(stall_arm=0.0))
     with pytest.raises(S.Sp2Error):

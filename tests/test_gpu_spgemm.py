@@ -264,7 +264,7 @@ def test_x0(gpu, tau):
         assert np.allclose(gv[i, :gn[i]], ref.row(i)[1], rtol=5e-16, atol=1e-300)
 
 
-@pytest.mark.parametrize("first_pass", [0, 1, 2, 3, 4, 7, 8, 11])
+@pytest.mark.parametrize("first_pass", [0, 1, 2, 3, 4, 7, 8, 9, 11])
 @pytest.mark.parametrize("fp32", [False, True])
 def test_first_pass_variants(gpu, first_pass, fp32):
     """Every first-pass variant (column blocks with 1, 2, 4 warps per row and the compact
@@ -325,7 +325,7 @@ def hub_matrix(n, hubs, hub_nnz, other_nnz, seed):
     return O.Ell(*I.coo_to_ellpack(n, rows, cols, vals))
 
 
-@pytest.mark.parametrize("first_pass", [0, 3])
+@pytest.mark.parametrize("first_pass", [0, 3, 9])
 def test_all_three_passes(gpu, first_pass):
     """Rows with more column groups than the block accumulator holds and a column span
     wider than the shared-memory window go to the 2^14-slot table; rows with more

@@ -43,7 +43,7 @@ BAD_OPTIONS = [
     (dict(tau=-1.0), "tau"),
     (dict(tau=float("inf")), "tau"),
     (dict(precision=7), "precision"),
-    (dict(spgemm_path=9), "spgemm_path"),
+    (dict(spgemm_path=13), "spgemm_path"),
     (dict(spgemm_path=5), "spgemm_path"),
     (dict(max_iter=-1), "max_iter"),
     (dict(max_iter=100000), "max_iter"),
@@ -144,3 +144,32 @@ def test_multiply_add_and_step_reject_bad_arguments(S):
     assert b"tau" in step(A, B, tau=float("nan"))
     assert b"nocc" in step(A, B, nocc=float("inf"))
     assert b"spgemm_path" in step(A, B, path=6)
+
+
+def test_multiply_block_rejects_bad_arguments(S):
+    """ellpack_multiply_block: a row block outside B, blocks of different lengths, a missing
+    addend, dtypes, aliasing and scalars come back as SP2E_ARG before any device call."""
+    keep = []
+    n = 16
+    Bfull = fake_matrix(S, n=n, keep=keep)
+    A, C, Out = fake_matrix(S, n=8, keep=keep), fake_matrix(S, n=8, keep=keep), fake_matrix(S, n=8, keep=keep)
+    short = fake_matrix(S, n=4, keep=keep)
+    f32 = fake_matrix(S, n=8, keep=keep)
+    f32.dtype = S.SP2_F32
+    w = ctypes.c_int32()
+
+    def blk(a, row0, b, c, out, al=1.0, be=0.0, tau=0.0):
+        rc = S.lib.ellpack_multiply_block(ctypes.byref(a), row0, ctypes.byref(b),
+                                          ctypes.byref(c) if c is not None else None, ctypes.byref(out),
+                                          al, be, tau, ctypes.byref(w), None, None, None)
+        return S.lib.sp2_last_error_string() if rc == S.SP2E_ARG else None
+    assert b"not rows of B" in blk(A, 9, Bfull, None, Out)
+    assert b"not rows of B" in blk(A, -1, Bfull, None, Out)
+    assert b"same rows" in blk(A, 0, Bfull, None, short)
+    assert b"same rows" in blk(A, 0, Bfull, short, Out, be=2.0)
+    assert b"NULL" in blk(A, 0, Bfull, None, Out, be=2.0)
+    assert b"dtypes differ" in blk(A, 0, Bfull, None, f32)
+    assert b"aliases" in blk(A, 0, Bfull, None, A)
+    assert b"aliases" in blk(A, 0, Bfull, C, C, be=2.0)
+    assert b"tau" in blk(A, 0, Bfull, None, Out, tau=-1.0)
+    assert b"not finite" in blk(A, 0, Bfull, None, Out, al=float("nan"))

@@ -52,7 +52,7 @@ def test_save_load_round_trip(S, tmp_path):
 def test_malformed_files_are_rejected(S, tmp_path):
     bad = [
         "152 0 18 7 4 34.3\n",                                          # no header
-        "# sp2ell spgemm tuning v1\n152 0 18 7 9 1.0\n",                # 9 is not a variant
+        "# sp2ell spgemm tuning v1\n152 0 18 7 13 1.0\n",               # 13 is not a variant
         "# sp2ell spgemm tuning v1\n152 2 18 7 4 1.0\n",                # unknown dtype
         "# sp2ell spgemm tuning v1\n152 0 18\n",                        # short line
     ]

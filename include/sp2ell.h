@@ -267,7 +267,8 @@ int ellpack_struct_count(const ellpack_t *A, const ellpack_t *B, const ellpack_t
                          int32_t *max_count, void *stream);
 
 #define NNZPRED_NPARAMS 5313  /* 16*64 + 64 + 64*64 + 64 + 64 + 1 */
-#define NNZPRED_NSTATS 34     /* feature means[16], feature stds[16], target mean, target std */
+#define NNZPRED_NSTATS 35     /* feature means[16], feature stds[16], target mean, target std,
+                                 margin added to the predicted log1p length (0 until calibrated) */
 
 /* A small MLP (16 -> 64 -> 64 -> 1, ReLU, FP32) predicting log1p of the post-threshold
  * length of each row of the next SP2 product from features of the current X. */
@@ -309,8 +310,17 @@ int nnzpred_grad(const nnzpred_t *p, const float *feat, const int32_t *count, in
 int nnzpred_train(nnzpred_t *p, const float *feat, const int32_t *count, int64_t n, int32_t steps, int32_t batch,
                   float lr, float *final_loss, void *stream);
 
-/* Predicted row lengths pred[n] (device float) from feat[n*16].  Asynchronous. */
+/* Predicted row lengths pred[n] (device float) from feat[n*16]: expm1(max(y + margin, 0))
+ * with y the network's log1p length.  Asynchronous. */
 int nnzpred_predict(const nnzpred_t *p, const float *feat, int64_t n, float *pred, void *stream);
+
+/* Calibration: sets the margin to the smallest m >= 0 such that at least a fraction
+ * `quantile` (in (0, 1]) of the n samples have log1p(count) <= y + m, so that the
+ * predictions err on the long side for that share of the rows (a network fitted to the
+ * mean under-predicts about half of them).  *margin (host, optional) receives it.
+ * Synchronises `stream`.  Errors: SP2E_ARG, SP2E_NOMEM, SP2E_CUDA. */
+int nnzpred_calibrate(nnzpred_t *p, const float *feat, const int32_t *count, int64_t n, float quantile,
+                      float *margin, void *stream);
 
 /* Output width for the product the SP2 step with `branch` and `tau` computes from X:
  * the features of X, the predicted row lengths (into pred, device float[n], optional),
@@ -366,7 +376,8 @@ int ellpack_from_dense(const void *dense, int64_t ld, double tau, ellpack_t *A, 
  * The SpGEMM first pass has several variants that compute the same product (spgemm_path
  * 1, 2, 4: column-block accumulator shared by that many warps per row (7: 2 warps, fewer
  * accumulator slots per row, for the upper triangles of symmetric products); 3: one warp
- * per row, two k steps per pass (8: compact, as 7); 10..12: per-warp hash table of 2^path
+ * per row, two k steps per pass (8: compact, as 7); 9: tiles of 8 consecutive rows sharing
+ * one sorted column index, one warp per row; 10..12: per-warp hash table of 2^path
  * slots).  The tuner
  * times them on a real product and keeps the fastest per class (SM count, dtype,
  * floor(log2 n), floor(log2 mean stored row length of A)) in a process-wide host table
@@ -416,13 +427,13 @@ typedef struct sp2_options {
                            err_n >= stall_ratio * err_{n-2} */
   int32_t n_fp64_tail;  /* MIXED: minimum FP64 iterations after the switch (default 2) */
   int32_t max_width;    /* cap on the working width (0 = n); SP2E_OVERFLOW beyond it */
-  int32_t spgemm_path;  /* SpGEMM first pass: 0 automatic (column blocks; F64: 4 warps
-                           per row, F32: path 3; their compact forms 7 and 8 for
-                           symmetric products); 1, 2, 4 = column-block accumulator
-                           shared by that many warps per row (7: 2, compact); 3 = column
+  int32_t spgemm_path;  /* SpGEMM first pass: 0 automatic (symmetric products, the
+                           default: F64 path 7, F32 path 8; full rows: F64 path 4, F32
+                           path 3); 1, 2, 4 = column-block accumulator shared by that
+                           many warps per row (7: 2 warps, compact blocks); 3 = column
                            blocks, one warp per row, two k steps per pass (8: compact);
-                           10..12 = per-warp hash table of 2^k slots; SP2_PATH_TUNED = the
-                           autotuner's choice */
+                           9 = row tiles sharing a column index; 10..12 = per-warp hash
+                           table of 2^k slots; SP2_PATH_TUNED = the autotuner's choice */
   double tau;           /* drop tolerance (default 1e-5) */
   double switch_tol;    /* MIXED: leave the FP32 loop once err_n < switch_tol (0 = automatic:
                            max(tol, 1e-4)); the FP32 stall rule also ends it */

@@ -69,9 +69,23 @@ def loss_and_grad(theta, x, t):
 
 
 def predict_counts(theta, stats, feat):
+    """Predicted row lengths: expm1 of the de-standardised output plus the calibration
+    margin stats[34] (when present), floored at 0."""
     x, _ = standardise(feat, np.zeros(len(feat)), stats)
     y, _ = forward(theta, x)
-    return np.expm1(np.maximum(y * stats[33] + stats[32], 0.0))
+    margin = stats[34] if len(stats) > 34 else 0.0
+    return np.expm1(np.maximum(y * stats[33] + stats[32] + margin, 0.0))
+
+
+def calibration_margin(theta, stats, feat, counts, quantile):
+    """The smallest m >= 0 with at least a share `quantile` of the samples satisfying
+    log1p(count) <= y + m (y the de-standardised network output): the k-th smallest
+    residual log1p(count) - y, k = ceil(quantile * n)."""
+    x, _ = standardise(feat, np.zeros(len(feat)), stats)
+    y, _ = forward(theta, x)
+    r = np.sort(np.log1p(np.asarray(counts, np.float64)) - (y * stats[33] + stats[32]))
+    k = min(len(r), max(1, int(np.ceil(quantile * len(r)))))
+    return max(float(r[k - 1]), 0.0)
 
 
 def features(idx, val, nnz, tau, branch):

@@ -10,6 +10,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -261,14 +262,14 @@ __global__ void __launch_bounds__(kMlpWarps * 32) mlp_predict_kernel(const float
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const float *mean = stats, *stdv = stats + 16;
-  const float tmean = stats[32], tstd = stats[33];
+  const float tmean = stats[32], tstd = stats[33], margin = stats[34];
   for (long long i = (long long)blockIdx.x * kMlpWarps + wid; i < n; i += (long long)gridDim.x * kMlpWarps) {
     float xin[kIn];
 #pragma unroll
     for (int c = 0; c < kIn; ++c) xin[c] = norm_in(feat, (size_t)i, c, mean, stdv);
     WarpAct act;
     mlp_forward_warp(sP, xin, h1s[wid], act, lane);
-    if (lane == 0) pred[i] = expm1f(fmaxf(act.y * tstd + tmean, 0.f));  // back to a row length
+    if (lane == 0) pred[i] = expm1f(fmaxf(act.y * tstd + tmean + margin, 0.f));  // back to a row length
     __syncwarp();
   }
 }
@@ -412,7 +413,31 @@ __global__ void feat_stats_kernel(const float *__restrict__ feat, const int *__r
     const double var = sq / (double)n - mean * mean;
     const double sd = var > 1e-12 ? sqrt(var) : 1.0;
     if (c < 16) { stats[c] = (float)mean; stats[16 + c] = (float)sd; }
-    else { stats[32] = (float)mean; stats[33] = (float)sd; }
+    else { stats[32] = (float)mean; stats[33] = (float)sd; stats[34] = 0.f; }
+  }
+}
+
+// Residuals log1p(count_i) - y_i of the network's log1p lengths (the margin left out).
+__global__ void __launch_bounds__(kMlpWarps * 32) mlp_residual_kernel(const float *__restrict__ P,
+                                                                     const float *__restrict__ stats,
+                                                                     const float *__restrict__ feat,
+                                                                     const int *__restrict__ count, long long n,
+                                                                     float *__restrict__ res) {
+  __shared__ float sP[kPN];
+  __shared__ float h1s[kMlpWarps][kH];
+  load_padded(P, sP);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const float *mean = stats, *stdv = stats + 16;
+  const float tmean = stats[32], tstd = stats[33];
+  for (long long i = (long long)blockIdx.x * kMlpWarps + wid; i < n; i += (long long)gridDim.x * kMlpWarps) {
+    float xin[kIn];
+#pragma unroll
+    for (int c = 0; c < kIn; ++c) xin[c] = norm_in(feat, (size_t)i, c, mean, stdv);
+    WarpAct act;
+    mlp_forward_warp(sP, xin, h1s[wid], act, lane);
+    if (lane == 0) res[i] = log1pf((float)count[i]) - (act.y * tstd + tmean);
+    __syncwarp();
   }
 }
 
@@ -698,6 +723,35 @@ extern "C" int nnzpred_predict(const nnzpred_t *p, const float *feat, int64_t n,
   SP2_TRY(check_pred(p, "nnzpred_predict"));
   if (!feat || !pred || n < 1) return fail(SP2E_ARG, "nnzpred_predict: bad arguments");
   return predict_async(p, feat, n, pred, as_stream(stream));
+}
+
+extern "C" int nnzpred_calibrate(nnzpred_t *p, const float *feat, const int32_t *count, int64_t n, float quantile,
+                                 float *margin, void *stream) {
+  SP2_TRY(check_pred(p, "nnzpred_calibrate"));
+  if (!feat || !count || n < 1) return fail(SP2E_ARG, "nnzpred_calibrate: bad arguments");
+  if (!(quantile > 0.f && quantile <= 1.f)) return fail(SP2E_ARG, "nnzpred_calibrate: quantile must be in (0, 1]");
+  cudaStream_t s = as_stream(stream);
+  float *res = nullptr;
+  SP2_TRY(dev_alloc((void **)&res, sizeof(float) * (size_t)n, s));
+  mlp_residual_kernel<<<grid_warps(n, kMlpWarps), kMlpWarps * 32, 0, s>>>(p->params, p->stats, feat, count, n, res);
+  note_launch();
+  std::vector<float> h((size_t)n);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), res, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dev_free(res, s);
+  if (e != cudaSuccess) return cuda_fail(e, "nnzpred_calibrate", __FILE__, __LINE__);
+  // the k-th smallest residual, k = ceil(quantile * n): at least that share lies at or below it
+  size_t k = (size_t)ceil((double)quantile * (double)n);
+  if (k < 1) k = 1;
+  if (k > (size_t)n) k = (size_t)n;
+  std::nth_element(h.begin(), h.begin() + (k - 1), h.end());
+  float m = h[k - 1];
+  if (!(m > 0.f)) m = 0.f;  // the margin only raises predictions (a NaN residual gives none)
+  SP2_CUDA(cudaMemcpyAsync(p->stats + 34, &m, sizeof(float), cudaMemcpyHostToDevice, s));
+  SP2_CUDA(cudaStreamSynchronize(s));
+  if (margin) *margin = m;
+  return SP2_OK;
 }
 
 extern "C" int nnzpred_width(const nnzpred_t *p, const ellpack_t *X, double tau, int32_t branch, int32_t *width,

@@ -443,7 +443,8 @@ struct TileCta {
 template <typename T, bool KEEPZ>
 __global__ void __launch_bounds__(TileCfg<T>::TT * 32, 2)
     spgemm_tile_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
-                       int use_add, BatchView bv, Upper up, int first_rows, double2 *__restrict__ rowstat,
+                       int use_add, BatchView bv, Upper up, int first_rows, const int *__restrict__ tile_list,
+                       const int *__restrict__ tile_count, double2 *__restrict__ rowstat,
                        SpgemmCtl *__restrict__ ctl, int *__restrict__ fb_list, int *__restrict__ fb_count) {
   using Cfg = TileCfg<T>;
   constexpr int TT = Cfg::TT;
@@ -472,8 +473,10 @@ __global__ void __launch_bounds__(TileCfg<T>::TT * 32, 2)
   for (int i = threadIdx.x; i < Cfg::SLOTS; i += blockDim.x) c.acc[i] = cl;
   __syncthreads();
 
-  const int ntiles = (A.n + TT - 1) / TT;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  // all tiles, or the tiles of a device-side list (those the split passes could not hold)
+  const int ntiles = tile_list ? *((volatile const int *)tile_count) : (A.n + TT - 1) / TT;
+  for (int q = blockIdx.x; q < ntiles; q += gridDim.x) {
+    const int tile = tile_list ? tile_list[q] : q;
     const int end = min(A.n, (tile + 1) * TT);
     int pos = tile * TT, size = first_rows;
     while (pos < end) {
@@ -500,37 +503,525 @@ __global__ void __launch_bounds__(TileCfg<T>::TT * 32, 2)
   }
 }
 
+
+// ------------------------------------------------------------------ split form
+// The same tiles in two kernels, so that neither waits on the other's phases: a build pass
+// (many small CTAs, latency hidden by occupancy) writes per tile the sorted column list U,
+// and for every source row the tile reads, its entries' positions in U (16-bit); the
+// product pass then needs no table at all: per entry one 16-bit load, the value, and the
+// read-modify-write of the row's accumulator.  Tiles are processed in waves so that the
+// per-tile records stay small; a tile whose records do not fit goes to the fused kernel.
+constexpr int kBuildWarps = 4;
+constexpr int kWaveTiles = 8192;
+constexpr long long kStagePerTile = 30000;  // mean staged entries a wave's buffer holds per tile
+
+// Records of one wave of tiles (device scratch).
+struct TileRecs {
+  int *nu;                      // [wave tiles] |U|, or -1: not built (the fused kernel takes the tile)
+  int *ucol;                    // [wave tiles][CU] U's columns in order
+  unsigned short *stage;        // positions in U of the staged entries of every tile
+  long long stage_cap;          // entries `stage` holds
+  unsigned long long *cursor;   // next free entry of `stage`
+  int *amap;                    // [wave tiles * TT][A.w]: staging index of entry t of a row's source row, minus
+                                // the entry's position in that source row
+  int *ovf;                     // tiles not built, by global index
+  int *ovf_count;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kBuildWarps * 32)
+    spgemm_tile_build_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, int use_add, BatchView bv, Upper up,
+                             int ncol, int tile0, int nwave, TileRecs rec) {
+  using Cfg = TileCfg<T>;
+  constexpr int TT = Cfg::TT, GT = Cfg::GT, KT = Cfg::KT;
+  __shared__ uint4 gent[GT];
+  __shared__ int kkey[KT], kst[KT], koff[KT];
+  __shared__ int klist[Cfg::MAXK];
+  __shared__ int gorder[Cfg::MAXG];
+  __shared__ unsigned long long sortbuf[Cfg::MAXG];
+  __shared__ int s_flag, s_nk, s_ng, s_nu, s_cnt, s_total;
+  __shared__ long long s_base;
+  TileCta<T, false> c;
+  c.A = A; c.B = B; c.Add = Add;
+  c.use_add = use_add; c.bv = bv; c.up = up;
+  c.gent = gent; c.kkey = kkey; c.kst = kst; c.gorder = gorder; c.sortbuf = sortbuf;
+  c.s_flag = &s_flag; c.s_nk = &s_nk; c.s_ng = &s_ng; c.s_nu = &s_nu;
+  c.lane = threadIdx.x & 31;
+  c.w = threadIdx.x >> 5;
+  c.ncol = ncol;
+  c.lt = lanemask_lt();
+  const int lane = c.lane, w = c.w;
+
+  for (int t = blockIdx.x; t < nwave; t += gridDim.x) {
+    const int tile = tile0 + t;
+    const int r0 = tile * TT, nr = min(TT, A.n - r0);
+    for (int e = threadIdx.x; e < GT; e += blockDim.x) gent[e] = make_uint4(kNoGroup, 0u, 0u, 0u);
+    for (int e = threadIdx.x; e < KT; e += blockDim.x) { kkey[e] = -1; kst[e] = INT_MAX; }
+    if (threadIdx.x == 0) { s_flag = 0; s_nk = 0; s_ng = 0; s_nu = 0; }
+    __syncthreads();
+    // 1. source rows of the tile, each with the first position any row reads
+    for (int lr = w; lr < nr; lr += kBuildWarps) {
+      const int r = r0 + lr;
+      if (bv.row_mat && !bv.active[bv.row_mat[r]]) continue;
+      const int na = min(A.nnz[r], A.w);
+      for (int s0 = 0; s0 < na; s0 += 32) {
+        const int sidx = s0 + lane;
+        if (sidx >= na) continue;
+        const int k = __ldg(A.idx + (size_t)r * A.w + sidx);
+        if ((unsigned)k >= (unsigned)B.n) continue;
+        int st = 0;
+        if (up.tp) st = min(max(__ldg(up.tp + (size_t)r * A.w + sidx), 0), min(__ldg(B.nnz + k), B.w));
+        int h = khash(k, Cfg::LOG2KT), slot = -1;
+#pragma unroll 1
+        for (int p = 0; p < KT; ++p) {
+          const int cur = *((volatile int *)&kkey[h]);
+          if (cur == k) { slot = h; break; }
+          if (cur == -1) {
+            const int old = atomicCAS(&kkey[h], -1, k);
+            if (old == -1) { atomicAdd(&s_nk, 1); slot = h; break; }
+            if (old == k) { slot = h; break; }
+          }
+          h = (h + 1) & (KT - 1);
+        }
+        if (slot >= 0) atomicMin(&kst[slot], st);
+        else s_flag = 1;
+      }
+    }
+    __syncthreads();
+    bool ok = !s_flag && s_nk <= Cfg::MAXK;
+    // 2. the source rows in slot order, their staged lengths and offsets (one warp)
+    if (ok && w == 0) {
+      int cnt = 0;
+      for (int c0 = 0; c0 < KT; c0 += 32) {
+        const bool used = kkey[c0 + lane] != -1;
+        const unsigned m = __ballot_sync(kFull, used);
+        if (used) klist[cnt + __popc(m & c.lt)] = c0 + lane;
+        cnt += __popc(m);
+      }
+      __syncwarp();
+      int run = 0;
+      for (int e0 = 0; e0 < cnt; e0 += 32) {
+        const int e = e0 + lane;
+        int len = 0, slot = 0;
+        if (e < cnt) {
+          slot = klist[e];
+          const int k = kkey[slot];
+          len = max(min(__ldg(B.nnz + k), B.w) - kst[slot], 0);
+        }
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
+        }
+        if (e < cnt) koff[slot] = run + incl - len;
+        run += __shfl_sync(kFull, incl, 31);
+      }
+      if (lane == 0) {
+        s_cnt = cnt;
+        s_total = run;
+        const unsigned long long b = run > 0 ? atomicAdd(rec.cursor, (unsigned long long)run) : 0ull;
+        s_base = (long long)b;
+        if ((long long)b + run > rec.stage_cap) s_flag = 1;
+      }
+    }
+    __syncthreads();
+    ok = ok && !s_flag;
+    const int cnt = s_cnt;
+    // 3. U: the staged entries' columns and the addend rows' columns
+    if (ok) {
+      for (int e = w; e < cnt; e += kBuildWarps) {
+        const int slot = klist[e], k = kkey[slot];
+        const int nb = min(__ldg(B.nnz + k), B.w);
+        const int *bi = B.idx + (size_t)k * B.w;
+        for (int q0 = kst[slot]; q0 < nb; q0 += 32) {
+          const int q = q0 + lane;
+          const int j = q < nb ? __ldg(bi + q) : -1;
+          c.insert_col((unsigned)j < (unsigned)ncol, j);
+        }
+      }
+      for (int lr = w; lr < nr; lr += kBuildWarps) {
+        const int r = r0 + lr;
+        bool add_r = use_add != 0;
+        if (bv.row_mat) {
+          const int m = bv.row_mat[r];
+          add_r = bv.active[m] && bv.beta[m] != 0.0;
+        }
+        if (!add_r) continue;
+        const int nc = min(Add.nnz[r], Add.w);
+        const int d0 = up.tpd ? min(max(up.tpd[r], 0), nc) : 0;
+        for (int q0 = d0; q0 < nc; q0 += 32) {
+          const int q = q0 + lane;
+          const int j = q < nc ? Add.idx[(size_t)r * Add.w + q] : -1;
+          c.insert_col((unsigned)j < (unsigned)ncol, j);
+        }
+      }
+    }
+    __syncthreads();
+    ok = ok && !s_flag && s_ng <= Cfg::MAXG;
+    // 4. sorted groups and their ranks (one warp)
+    if (ok && w == 0) {
+      int gc = 0;
+      for (int c0 = 0; c0 < GT; c0 += 32) {
+        const unsigned gk = gent[c0 + lane].x;
+        const bool used = gk != kNoGroup;
+        const unsigned m = __ballot_sync(kFull, used);
+        if (used) sortbuf[gc + __popc(m & c.lt)] = ((unsigned long long)gk << 32) | (unsigned)(c0 + lane);
+        gc += __popc(m);
+      }
+      __syncwarp();
+      if (gc <= 32) c.template rank_groups<1>(gc);
+      else if (gc <= 64) c.template rank_groups<2>(gc);
+      else if (gc <= 128) c.template rank_groups<4>(gc);
+      else c.template rank_groups<8>(gc);
+    }
+    __syncthreads();
+    ok = ok && s_nu <= Cfg::CU;
+    if (!ok) {
+      if (threadIdx.x == 0) {
+        rec.nu[t] = -1;
+        rec.ovf[atomicAdd(rec.ovf_count, 1)] = tile;
+      }
+      __syncthreads();
+      continue;
+    }
+    // 5. U's columns in order
+    int *ucol = rec.ucol + (size_t)t * Cfg::CU;
+    const int ng = s_ng;
+    for (int p = w; p < ng; p += kBuildWarps) {
+      const uint4 e = gent[gorder[p]];
+      if ((e.y >> lane) & 1u) ucol[(int)e.z + __popc(e.y & c.lt)] = (int)(e.x << 5) + lane;
+    }
+    // 6. positions in U of every staged entry
+    const long long base = s_base;
+    for (int e = w; e < cnt; e += kBuildWarps) {
+      const int slot = klist[e], k = kkey[slot];
+      const int nb = min(__ldg(B.nnz + k), B.w), k0 = kst[slot];
+      const int *bi = B.idx + (size_t)k * B.w;
+      unsigned short *dst = rec.stage + base + koff[slot] - k0;
+      for (int q = k0 + lane; q < nb; q += 32) {
+        const int j = __ldg(bi + q);
+        const int u = (unsigned)j < (unsigned)ncol ? c.lookup(j) : -1;
+        dst[q] = (unsigned short)(u >= 0 ? u : 0xFFFF);
+      }
+    }
+    // 7. per entry of the tile's rows: the staging index of its source row's entries
+    for (int lr = w; lr < nr; lr += kBuildWarps) {
+      const int r = r0 + lr;
+      const int na = min(A.nnz[r], A.w);
+      int *am = rec.amap + ((size_t)t * TT + lr) * A.w;
+      for (int sidx = lane; sidx < na; sidx += 32) {
+        const int k = __ldg(A.idx + (size_t)r * A.w + sidx);
+        int v = 0;
+        if ((unsigned)k < (unsigned)B.n) {
+          int h = khash(k, Cfg::LOG2KT);
+#pragma unroll 1
+          for (int p = 0; p < KT && kkey[h] != k; ++p) h = (h + 1) & (KT - 1);
+          if (kkey[h] == k) v = (int)(base + koff[h] - kst[h]);
+        }
+        am[sidx] = v;
+      }
+    }
+    if (threadIdx.x == 0) rec.nu[t] = s_nu;
+    __syncthreads();
+  }
+}
+
+template <typename T, bool KEEPZ>
+__global__ void __launch_bounds__(TileCfg<T>::TT * 32, 2)
+    spgemm_tile_apply_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
+                             int use_add, BatchView bv, Upper up, int tile0, int nwave, TileRecs rec,
+                             double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl) {
+  using Cfg = TileCfg<T>;
+  constexpr int TT = Cfg::TT, CU = Cfg::CU, QW = Cfg::QW;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *acc = reinterpret_cast<T *>(smem);
+  int *s_ucol = reinterpret_cast<int *>(smem + Cfg::ACC_BYTES);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = lanemask_lt();
+  const int ncol = Out.n;
+  const T clean = KEEPZ ? untouched<T>() : T(0);
+  const auto tb = mag_bits(tau);
+  int wmax = 0, wover = 0;
+  for (int i = threadIdx.x; i < TT * CU; i += blockDim.x) acc[i] = clean;
+  T *racc = acc + (size_t)w * CU;
+
+  for (int t = blockIdx.x; t < nwave; t += gridDim.x) {
+    const int nu = rec.nu[t];
+    if (nu < 0) continue;  // the fused kernel takes this tile
+    __syncthreads();       // the previous tile's rows are done with s_ucol
+    const int *ucol = rec.ucol + (size_t)t * CU;
+    for (int i = threadIdx.x; i < nu; i += blockDim.x) s_ucol[i] = ucol[i];
+    __syncthreads();
+    const int r = (tile0 + t) * TT + w;
+    if (r >= A.n) continue;
+    T alpha_r = alpha, beta_r = beta;
+    int add_r = use_add;
+    if (bv.row_mat) {
+      const int m = bv.row_mat[r];
+      if (!bv.active[m]) continue;
+      alpha_r = (T)bv.alpha[m];
+      beta_r = (T)bv.beta[m];
+      add_r = beta_r != T(0);
+    }
+    // the addend: positions by binary search in U
+    if (add_r) {
+      const int nc = min(Add.nnz[r], Add.w);
+      const int d0 = up.tpd ? min(max(up.tpd[r], 0), nc) : 0;
+      for (int q0 = d0; q0 < nc; q0 += 32) {
+        const int q = q0 + lane;
+        if (q < nc) {
+          const int j = Add.idx[(size_t)r * Add.w + q];
+          int lo = 0, hi = nu;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_ucol[mid] < j) lo = mid + 1; else hi = mid;
+          }
+          if (lo < nu && s_ucol[lo] == j) {
+            T o = racc[lo];
+            if (KEEPZ && is_untouched(o)) o = T(0);
+            racc[lo] = fmadd(beta_r, Add.val[(size_t)r * Add.w + q], o);
+          }
+        }
+      }
+      __syncwarp();
+    }
+    // the source rows in A's order: staged positions, values, read-modify-write
+    const int na = min(A.nnz[r], A.w);
+    const int *arow_i = A.idx + (size_t)r * A.w;
+    const T *arow_v = A.val + (size_t)r * A.w;
+    const int *am = rec.amap + ((size_t)t * TT + w) * A.w;
+    int ck = 0, cnb = 0, cst = 0, cam = 0, nk_ = 0, nnb = 0, nst = 0, nam = 0;
+    T ca = T(0), na_ = T(0);
+    auto load_chunk = [&](int cb, int &kk, int &nbk, T &av, int &st, int &amv) {
+      const int sidx = cb + lane;
+      kk = 0; nbk = 0; av = T(0); st = 0; amv = 0;
+      if (sidx < na) {
+        const int k = __ldg(arow_i + sidx);
+        if ((unsigned)k < (unsigned)B.n) {
+          kk = k;
+          av = alpha_r * __ldg(arow_v + sidx);
+          nbk = min(__ldg(B.nnz + k), B.w);
+          if (up.tp) st = min(max(__ldg(up.tp + (size_t)r * A.w + sidx), 0), nbk);
+          nbk -= st;
+          amv = __ldg(am + sidx) + st;
+        }
+      }
+    };
+    load_chunk(0, ck, cnb, ca, cst, cam);
+    load_chunk(32, nk_, nnb, na_, nst, nam);
+    int cbase = 0;
+    auto fetch_step = [&](int tt, int (&ur)[QW], T (&vr)[QW], int &nb, T &a) {
+      int k, st, amv;
+      if (tt < cbase + 32) {
+        k = __shfl_sync(kFull, ck, tt & 31);
+        nb = __shfl_sync(kFull, cnb, tt & 31);
+        a = __shfl_sync(kFull, ca, tt & 31);
+        st = __shfl_sync(kFull, cst, tt & 31);
+        amv = __shfl_sync(kFull, cam, tt & 31);
+      } else {
+        k = __shfl_sync(kFull, nk_, tt & 31);
+        nb = __shfl_sync(kFull, nnb, tt & 31);
+        a = __shfl_sync(kFull, na_, tt & 31);
+        st = __shfl_sync(kFull, nst, tt & 31);
+        amv = __shfl_sync(kFull, nam, tt & 31);
+      }
+      const T *bv_ = B.val + (size_t)k * B.w + st;
+      const unsigned short *us = rec.stage + amv;
+#pragma unroll
+      for (int u = 0; u < QW; ++u) {
+        const int q = 32 * u + lane;
+        ur[u] = q < nb ? (int)__ldg(us + q) : 0xFFFF;
+        vr[u] = q < nb ? __ldg(bv_ + q) : T(0);
+      }
+      // entries past the registers are read in the step itself
+      return 0;
+    };
+    int u0[QW], u1[QW], u2[QW];
+    T v0[QW], v1[QW], v2[QW];
+    int nb0 = 0, nb1 = 0, nb2 = 0, am0 = 0, am1 = 0, am2 = 0;
+    size_t bo0 = 0, bo1 = 0, bo2 = 0;
+    T a0 = T(0), a1 = T(0), a2 = T(0);
+    auto info_long = [&](int tt, int &amv, size_t &bo) {  // staging and value offsets of step tt
+      int k, st;
+      if (tt < cbase + 32) {
+        k = __shfl_sync(kFull, ck, tt & 31); st = __shfl_sync(kFull, cst, tt & 31);
+        amv = __shfl_sync(kFull, cam, tt & 31);
+      } else {
+        k = __shfl_sync(kFull, nk_, tt & 31); st = __shfl_sync(kFull, nst, tt & 31);
+        amv = __shfl_sync(kFull, nam, tt & 31);
+      }
+      bo = (size_t)k * B.w + st;
+    };
+    auto step = [&](const int (&ur)[QW], const T (&vr)[QW], int nb, T a, int amv, size_t bo) {
+      T old[QW];
+#pragma unroll
+      for (int u = 0; u < QW; ++u) old[u] = ur[u] < CU ? racc[ur[u]] : T(0);
+#pragma unroll
+      for (int u = 0; u < QW; ++u)
+        if (ur[u] < CU) {
+          const T o = (KEEPZ && is_untouched(old[u])) ? T(0) : old[u];
+          racc[ur[u]] = fmadd(a, vr[u], o);
+        }
+      for (int q = 32 * QW + lane; q < nb; q += 32) {  // source rows longer than the registers
+        const int uu = (int)__ldg(rec.stage + amv + q);
+        if (uu < CU) {
+          T o = racc[uu];
+          if (KEEPZ && is_untouched(o)) o = T(0);
+          racc[uu] = fmadd(a, __ldg(B.val + bo + q), o);
+        }
+      }
+      __syncwarp();
+    };
+    if (na > 0) { fetch_step(0, u0, v0, nb0, a0); info_long(0, am0, bo0); }
+    if (na > 1) { fetch_step(1, u1, v1, nb1, a1); info_long(1, am1, bo1); }
+    for (int tt = 0; tt < na; tt += 3) {
+      if (tt >= cbase + 32) {
+        ck = nk_; cnb = nnb; ca = na_; cst = nst; cam = nam;
+        cbase += 32;
+        load_chunk(cbase + 32, nk_, nnb, na_, nst, nam);
+      }
+      if (tt + 2 < na) { fetch_step(tt + 2, u2, v2, nb2, a2); info_long(tt + 2, am2, bo2); }
+      step(u0, v0, nb0, a0, am0, bo0);
+      if (tt + 1 >= na) break;
+      if (tt + 3 < na) { fetch_step(tt + 3, u0, v0, nb0, a0); info_long(tt + 3, am0, bo0); }
+      step(u1, v1, nb1, a1, am1, bo1);
+      if (tt + 2 >= na) break;
+      if (tt + 4 < na) { fetch_step(tt + 4, u1, v1, nb1, a1); info_long(tt + 4, am1, bo1); }
+      step(u2, v2, nb2, a2, am2, bo2);
+    }
+    // epilogue: U in column order
+    int nk = 0;
+    double dsum = 0.0, fsum = 0.0;
+    int *oi = Out.idx + (size_t)r * Out.w;
+    T *ov = Out.val + (size_t)r * Out.w;
+    for (int u00 = 0; u00 < nu; u00 += 32) {
+      const int u = u00 + lane;
+      bool keep = false;
+      T v = T(0);
+      int j = 0;
+      if (u < nu) {
+        v = racc[u];
+        keep = KEEPZ ? !is_untouched(v) : mag_bits(v) > tb;
+        racc[u] = clean;
+        j = s_ucol[u];
+      }
+      const unsigned m = __ballot_sync(kFull, keep);
+      if (keep) {
+        const int pos = nk + __popc(m & lt);
+        if (pos < Out.w) { oi[pos] = j; ov[pos] = v; }
+        if (!up.tp) {  // upper-triangle rows: the mirror pass takes the statistics of the full rows
+          const double dv = (double)v;
+          if (j == r) dsum += dv;
+          fsum = fma(dv, dv, fsum);
+        }
+      }
+      nk += __popc(m);
+    }
+    dsum = warp_sum(dsum);
+    fsum = warp_sum(fsum);
+    wmax = max(wmax, nk);
+    if (lane == 0) {
+      if (nk > Out.w) {
+        ++wover;
+        rowstat[r] = make_double2(0.0, 0.0);
+      } else {
+        Out.nnz[r] = nk;
+        rowstat[r] = make_double2(dsum, fsum);
+      }
+    }
+    (void)ncol;
+  }
+  if (lane == 0) {
+    if (wmax) atomicMax(&ctl->max_count, wmax);
+    if (wover) atomicAdd(&ctl->overflow_rows, wover);
+  }
+}
+
 }  // namespace
 
 template <typename T>
 int launch_tile(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
   using Cfg = TileCfg<T>;
+  constexpr int TT = Cfg::TT, CU = Cfg::CU;
+  constexpr int APPLY_SMEM = Cfg::ACC_BYTES + CU * 4;
   const bool keepz = a.tau == 0.0;
-  auto kern = keepz ? spgemm_tile_kernel<T, true> : spgemm_tile_kernel<T, false>;
-  static DeviceOnce once[2];
-  const int dev = current_device();
-  SP2_TRY(device_once(once[keepz ? 1 : 0], dev, [&](int &occ) {
-    SP2_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
+  auto fused = keepz ? spgemm_tile_kernel<T, true> : spgemm_tile_kernel<T, false>;
+  auto apply = keepz ? spgemm_tile_apply_kernel<T, true> : spgemm_tile_apply_kernel<T, false>;
+  static DeviceOnce once_f[2], once_a[2], once_b;
+  const int dev = current_device(), kz = keepz ? 1 : 0;
+  SP2_TRY(device_once(once_f[kz], dev, [&](int &occ) {
+    SP2_CUDA(cudaFuncSetAttribute(fused, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
     occ = 0;
-    SP2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, Cfg::TT * 32, Cfg::SMEM));
+    SP2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fused, TT * 32, Cfg::SMEM));
     if (occ < 1) occ = 1;
     return SP2_OK;
   }));
-  const long long cap = (long long)num_sms() * once[keepz ? 1 : 0].value[dev];
-  const long long tiles = ((long long)a.A->n + Cfg::TT - 1) / Cfg::TT;
-  int grid = (int)(tiles < cap ? tiles : cap);
-  if (grid < 1) grid = 1;
-  // full rows reach about twice the columns of upper-triangle rows: start at half tiles
-  const int first_rows = a.up.tp ? Cfg::TT : Cfg::TT / 2;
+  SP2_TRY(device_once(once_a[kz], dev, [&](int &occ) {
+    SP2_CUDA(cudaFuncSetAttribute(apply, cudaFuncAttributeMaxDynamicSharedMemorySize, APPLY_SMEM));
+    occ = 0;
+    SP2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, apply, TT * 32, APPLY_SMEM));
+    if (occ < 1) occ = 1;
+    return SP2_OK;
+  }));
+  SP2_TRY(device_once(once_b, dev, [&](int &occ) {
+    occ = 0;
+    SP2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spgemm_tile_build_kernel<T>, kBuildWarps * 32, 0));
+    if (occ < 1) occ = 1;
+    return SP2_OK;
+  }));
+  const int n = a.A->n, aw = a.A->width;
+  const int ntiles = (n + TT - 1) / TT;
+  const int wave = ntiles < kWaveTiles ? ntiles : kWaveTiles;
+  // records of one wave
+  auto a256 = [](size_t b) { return ((b + 255) / 256) * 256; };
+  const long long stage_cap = (long long)wave * kStagePerTile;
+  const size_t b_nu = a256(sizeof(int) * (size_t)wave), b_ucol = a256(sizeof(int) * (size_t)wave * CU);
+  const size_t b_stage = a256(sizeof(unsigned short) * (size_t)stage_cap), b_cur = 256;
+  const size_t b_amap = a256(sizeof(int) * (size_t)wave * TT * aw), b_ovf = a256(sizeof(int) * ((size_t)wave + 1));
+  unsigned char *scr = nullptr;
+  SP2_TRY(dev_alloc((void **)&scr, b_nu + b_ucol + b_stage + b_cur + b_amap + b_ovf, s));
+  TileRecs rec;
+  size_t off = 0;
+  rec.nu = reinterpret_cast<int *>(scr + off); off += b_nu;
+  rec.ucol = reinterpret_cast<int *>(scr + off); off += b_ucol;
+  rec.stage = reinterpret_cast<unsigned short *>(scr + off); off += b_stage;
+  rec.stage_cap = stage_cap;
+  rec.cursor = reinterpret_cast<unsigned long long *>(scr + off); off += b_cur;
+  rec.amap = reinterpret_cast<int *>(scr + off); off += b_amap;
+  rec.ovf = reinterpret_cast<int *>(scr + off);
+  rec.ovf_count = rec.ovf + wave;
   const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
+  const int use_add = a.Add != nullptr && a.beta != 0.0;
+  const int first_rows = a.up.tp ? TT : TT / 2;
+  const int sms = num_sms();
+  int rc = SP2_OK;
   prof_begin(SP2_PROF_SPGEMM, s);
-  kern<<<grid, Cfg::TT * 32, Cfg::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
-                                            (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv, a.up,
-                                            first_rows, rowstat, ctl, fb, fb_count);
-  note_launch();
+  for (int tile0 = 0; tile0 < ntiles && rc == SP2_OK; tile0 += wave) {
+    const int nw = ntiles - tile0 < wave ? ntiles - tile0 : wave;
+    cudaError_t e = cudaMemsetAsync(rec.cursor, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(rec.ovf_count, 0, sizeof(int), s);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "row-tile records", __FILE__, __LINE__); break; }
+    const int gb = nw < sms * once_b.value[dev] ? nw : sms * once_b.value[dev];
+    spgemm_tile_build_kernel<T><<<gb, kBuildWarps * 32, 0, s>>>(view<T>(a.A), view<T>(a.B), add, use_add, a.bv, a.up,
+                                                               a.Out->n, tile0, nw, rec);
+    note_launch();
+    const int ga = nw < sms * once_a[kz].value[dev] ? nw : sms * once_a[kz].value[dev];
+    apply<<<ga, TT * 32, APPLY_SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha, (T)a.beta,
+                                          (T)a.tau, use_add, a.bv, a.up, tile0, nw, rec, rowstat, ctl);
+    note_launch();
+    // tiles whose records did not fit: the fused kernel, which splits them as needed
+    const int gf = sms * once_f[kz].value[dev];
+    fused<<<gf, TT * 32, Cfg::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha, (T)a.beta,
+                                         (T)a.tau, use_add, a.bv, a.up, first_rows, rec.ovf, rec.ovf_count, rowstat,
+                                         ctl, fb, fb_count);
+    note_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) rc = cuda_fail(e, "row-tile kernels", __FILE__, __LINE__);
+  }
   prof_end(SP2_PROF_SPGEMM, s);
-  SP2_CUDA(cudaGetLastError());
-  return SP2_OK;
+  dev_free(scr, s);
+  return rc;
 }
 
 template int launch_tile<double>(const MultiplyArgs &, double2 *, SpgemmCtl *, int *, int *, cudaStream_t);

@@ -62,9 +62,13 @@ def default_training_set(seed=0, rows=50000, tau=1e-5, steps=10, dtype=S.SP2_F64
     return collect(hs, tau, steps, rows_per_product=per, dtype=dtype)
 
 
-def train(feat, counts, seed=0, steps=1500, batch=2048, lr=2e-3):
-    """A new predictor trained on (feat, counts); returns (predictor, final batch loss)."""
+def train(feat, counts, seed=0, steps=1500, batch=2048, lr=2e-3, quantile=0.9):
+    """A new predictor trained on (feat, counts) and calibrated so that a share `quantile`
+    of the training rows lie at or below their predicted lengths (None: no margin);
+    returns (predictor, final batch loss)."""
     p = S.NnzPredictor(seed)
     p.set_stats(feat, counts)
     loss = p.train(feat, counts, steps, batch, lr)
+    if quantile is not None:
+        p.calibrate(feat, counts, quantile)
     return p, loss

@@ -36,7 +36,7 @@ class ellpack_t(ctypes.Structure):
                 ("nnz", ctypes.c_void_p)]
 
 
-NNZPRED_NPARAMS, NNZPRED_NSTATS = 5313, 34
+NNZPRED_NPARAMS, NNZPRED_NSTATS = 5313, 35
 
 
 class nnzpred_t(ctypes.Structure):
@@ -123,6 +123,7 @@ def _load():
         "nnzpred_grad": ([P(nnzpred_t), V, V, ctypes.c_int64, V, P(ctypes.c_float), V], ctypes.c_int),
         "nnzpred_train": ([P(nnzpred_t), V, V, ctypes.c_int64, I, I, ctypes.c_float, P(ctypes.c_float), V],
                           ctypes.c_int),
+        "nnzpred_calibrate": ([P(nnzpred_t), V, V, ctypes.c_int64, ctypes.c_float, P(ctypes.c_float), V], ctypes.c_int),
         "nnzpred_predict": ([P(nnzpred_t), V, ctypes.c_int64, V, V], ctypes.c_int),
         "nnzpred_width": ([P(nnzpred_t), E, D, I, P(I), V, V], ctypes.c_int),
         "nnzpred_save": ([P(nnzpred_t), ctypes.c_char_p, V], ctypes.c_int),
@@ -515,6 +516,14 @@ class NnzPredictor:
         _check(lib.nnzpred_train(ctypes.byref(self.desc), feat.data_ptr(), counts.data_ptr(), feat.shape[0],
                                  int(steps), int(batch), float(lr), ctypes.byref(loss), _stream(stream)))
         return loss.value
+
+    def calibrate(self, feat, counts, quantile=0.9, stream=None):
+        """Sets the log-space margin so that a share `quantile` of the samples' lengths lie
+        at or below their predictions; returns the margin."""
+        m = ctypes.c_float()
+        _check(lib.nnzpred_calibrate(ctypes.byref(self.desc), feat.data_ptr(), counts.data_ptr(), feat.shape[0],
+                                     float(quantile), ctypes.byref(m), _stream(stream)))
+        return m.value
 
     def predict(self, feat, stream=None):
         import torch

@@ -216,3 +216,28 @@ def test_predicted_width_rule(gpu, trainset):
 def torch_equal(a, b):
     import torch
     return torch.equal(a, b)
+
+
+def test_calibration_margin_matches_oracle(gpu, trainset):
+    """The margin for quantile 0.9 is the oracle's (the 0.9 quantile of the residuals
+    log1p(count) - y, in FP32 on the GPU), and with it at least 90 % of the training rows
+    lie at or below their predicted length (about half do without it)."""
+    S = gpu
+    feat, counts = trainset
+    p = S.NnzPredictor(seed=5)
+    p.set_stats(feat, counts)
+    p.train(feat, counts, 400, 1024, 2e-3)
+    c = counts.cpu().numpy()
+    under0 = np.mean(c > p.predict(feat).cpu().numpy())
+    m = p.calibrate(feat, counts, 0.9)
+    theta, stats = p.params()
+    assert stats[34] == m and m > 0.0
+    mo = M.calibration_margin(theta.astype(np.float64), stats.astype(np.float64)[:34],
+                              feat.cpu().numpy().astype(np.float64), c, 0.9)
+    assert m == pytest.approx(mo, abs=2e-4)
+    pred = p.predict(feat).cpu().numpy()
+    ref = M.predict_counts(theta.astype(np.float64), stats.astype(np.float64), feat.cpu().numpy().astype(np.float64))
+    np.testing.assert_allclose(pred, ref, rtol=2e-4, atol=1e-3)
+    under = np.mean(c > pred)
+    print("rows above their prediction: %.3f uncalibrated, %.3f with margin %.4f" % (under0, under, m))
+    assert under <= 0.1 + 1e-3 and under < under0

@@ -79,5 +79,5 @@ def test_batched_tuned_matches_default(gpu):
             d0, d1 = dense_of(*D0[m].to_numpy(), n), dense_of(*D1[m].to_numpy(), n)
             assert np.linalg.norm(d1 - d0) / np.sqrt(n) < (1e-10 if prec == S.SP2_PREC_F64 else 1e-6)
     with pytest.raises(S.Sp2Error):
-        S.sp2_purify_batched(Hs, noccs, 1e-10, S.sp2_options_default(spgemm_path=9))
+        S.sp2_purify_batched(Hs, noccs, 1e-10, S.sp2_options_default(spgemm_path=13))
     S.sp2_tune_clear()

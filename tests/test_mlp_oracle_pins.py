@@ -69,6 +69,27 @@ def test_standardise_and_predict_round_trip():
     assert np.allclose(p, 99.0, rtol=1e-14)
     x, t = M.standardise(np.full((1, 16), 6.0), [99], stats)
     assert np.allclose(x, 1.0) and t[0] == pytest.approx(0.0, abs=1e-15)
+    # a margin m multiplies 1 + prediction by e^m
+    pm = M.predict_counts(th, np.concatenate([stats, [np.log(2.0)]]), np.zeros((2, 16)))
+    assert np.allclose(pm, 199.0, rtol=1e-13)
+
+
+def test_calibration_margin_is_the_residual_quantile():
+    """With a zero network every prediction is expm1(target mean): the margin for quantile
+    q is the ceil(q n)-th smallest log1p(count) minus that mean (never negative), and with
+    it at least a share q of the samples lie at or below their prediction."""
+    rng = np.random.default_rng(7)
+    counts = rng.integers(1, 500, 101)
+    stats = np.concatenate([np.zeros(16), np.ones(16), [np.log1p(120.0), 1.0]])
+    th = np.zeros(M.NPARAMS)
+    feat = np.zeros((len(counts), 16))
+    for q in (0.5, 0.9, 1.0):
+        m = M.calibration_margin(th, stats, feat, counts, q)
+        srt = np.sort(np.log1p(counts.astype(np.float64)))
+        assert m == pytest.approx(max(srt[int(np.ceil(q * len(counts))) - 1] - np.log1p(120.0), 0.0), abs=1e-14)
+        pred = M.predict_counts(th, np.concatenate([stats, [m]]), feat)
+        assert np.mean(counts <= pred * (1 + 1e-12)) >= q
+    assert M.calibration_margin(th, stats, feat[:5], np.ones(5, np.int64), 0.9) == 0.0  # over-predicted: no margin
 
 
 def test_features_hand_worked():

@@ -529,7 +529,7 @@ struct TileRecs {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kBuildWarps * 32)
+__global__ void __launch_bounds__(kBuildWarps * 32, 8)
     spgemm_tile_build_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, int use_add, BatchView bv, Upper up,
                              int ncol, int tile0, int nwave, TileRecs rec) {
   using Cfg = TileCfg<T>;
@@ -727,6 +727,22 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
   }
 }
 
+// The read-modify-writes of the NU occupied register slots of one source row (a
+// predicated-off FP64 instruction still takes its turn in the narrow FP64 pipe, so empty
+// slots are not issued at all); slot positions >= CU mark entries outside the product.
+template <typename T, bool KEEPZ, int NU, int QW, int CU>
+__device__ __forceinline__ void rmw_slots(T *racc, const int (&ur)[QW], const T (&vr)[QW], T a) {
+  T old[NU];
+#pragma unroll
+  for (int u = 0; u < NU; ++u) old[u] = ur[u] < CU ? racc[ur[u]] : T(0);
+#pragma unroll
+  for (int u = 0; u < NU; ++u)
+    if (ur[u] < CU) {
+      const T o = (KEEPZ && is_untouched(old[u])) ? T(0) : old[u];
+      racc[ur[u]] = fmadd(a, vr[u], o);
+    }
+}
+
 template <typename T, bool KEEPZ>
 __global__ void __launch_bounds__(TileCfg<T>::TT * 32, 2)
     spgemm_tile_apply_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
@@ -854,15 +870,13 @@ __global__ void __launch_bounds__(TileCfg<T>::TT * 32, 2)
       bo = (size_t)k * B.w + st;
     };
     auto step = [&](const int (&ur)[QW], const T (&vr)[QW], int nb, T a, int amv, size_t bo) {
-      T old[QW];
-#pragma unroll
-      for (int u = 0; u < QW; ++u) old[u] = ur[u] < CU ? racc[ur[u]] : T(0);
-#pragma unroll
-      for (int u = 0; u < QW; ++u)
-        if (ur[u] < CU) {
-          const T o = (KEEPZ && is_untouched(old[u])) ? T(0) : old[u];
-          racc[ur[u]] = fmadd(a, vr[u], o);
-        }
+      switch (min((nb + 31) >> 5, QW)) {
+        case 0: break;
+        case 1: rmw_slots<T, KEEPZ, 1, QW, CU>(racc, ur, vr, a); break;
+        case 2: rmw_slots<T, KEEPZ, 2, QW, CU>(racc, ur, vr, a); break;
+        case 3: rmw_slots<T, KEEPZ, 3, QW, CU>(racc, ur, vr, a); break;
+        default: rmw_slots<T, KEEPZ, QW, QW, CU>(racc, ur, vr, a); break;
+      }
       for (int q = 32 * QW + lane; q < nb; q += 32) {  // source rows longer than the registers
         const int uu = (int)__ldg(rec.stage + amv + q);
         if (uu < CU) {
@@ -1013,8 +1027,8 @@ int launch_tile(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
     // tiles whose records did not fit: the fused kernel, which splits them as needed
     const int gf = sms * once_f[kz].value[dev];
     fused<<<gf, TT * 32, Cfg::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha, (T)a.beta,
-                                         (T)a.tau, use_add, a.bv, a.up, first_rows, rec.ovf, rec.ovf_count, rowstat,
-                                         ctl, fb, fb_count);
+                                         (T)a.tau, use_add, a.bv, a.up, first_rows / 2, rec.ovf, rec.ovf_count,
+                                         rowstat, ctl, fb, fb_count);
     note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) rc = cuda_fail(e, "row-tile kernels", __FILE__, __LINE__);

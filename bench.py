@@ -42,7 +42,8 @@ def parse():
     p.add_argument("--tau", type=float, default=1e-6)
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--workload", default="spgemm", choices=["spgemm", "sp2", "batched", "sizing", "model", "schedule"],
+    p.add_argument("--workload", default="spgemm",
+                   choices=["spgemm", "sp2", "batched", "sizing", "model", "schedule", "rowblock"],
                    help="spgemm: one SP2 iteration at N=262144 (default); sp2: whole purifications, FP64 vs "
                         "mixed at N=131072; batched: 256 clusters in one graph launch vs one by one; sizing: "
                         "heuristic vs structural vs MLP output widths for mixed SP2 at N=1048576; model: the paper's "
@@ -681,6 +682,55 @@ def time_to_solution(a, dev_id, reps=3):
     return out
 
 
+def run_rowblock(a):
+    """The row-block split of one SP2 run (shard.row_block_sp2) with its ranks run as threads
+    of one process on one GPU (exchanges through host memory): the same 3D gapped
+    Hamiltonian as the sp2 workload, against the whole run (sp2_purify, FP64).  It shows
+    what the split itself costs (halo requests, exchanges, block products); it is not a
+    multi-GPU scaling figure."""
+    import threading
+    import torch
+    from paper_2102_08505_gb300 import inputs as I
+    from paper_2102_08505_gb300 import shard
+    from paper_2102_08505_gb300 import sp2ell as S
+    n = a.n
+    tau = a.tau if a.tau != 1e-6 else 1e-5
+    idx, val, nnz = I.tight_binding(n, seed=a.seed, delta=10.0)
+    H = S.Ellpack.from_numpy(idx, val, nnz)
+    t_whole, (Dw, sw), _ = _median_runs(lambda: S.sp2_purify(H, n / 2, 1e-10, S.sp2_options_default(tau=tau)), 3)
+    out = {"whole": {"time_s": t_whole, "iterations": sw["iterations"]}}
+    for world in (2, 4):
+        bounds = shard.block_bounds(n, world)
+        blocks = [S.Ellpack.from_numpy(idx[bounds[r]:bounds[r + 1]], val[bounds[r]:bounds[r + 1]],
+                                       nnz[bounds[r]:bounds[r + 1]]) for r in range(world)]
+
+        def run_once():
+            hub = shard.LocalComm.Hub(world)
+            res, errs = {}, []
+
+            def rank(r):
+                try:
+                    torch.cuda.set_device(0)
+                    res[r] = shard.row_block_sp2(shard.LocalComm(hub, r), bounds, blocks[r], n / 2, 1e-10, tau,
+                                                 shard.GPUBlockOps())
+                except Exception as e:
+                    errs.append(e)
+            ts = [threading.Thread(target=rank, args=(r,)) for r in range(world)]
+            for t in ts:
+                t.start()
+            for t in ts:
+                t.join()
+            if errs:
+                raise errs[0]
+            return res
+        t, res, _ = _median_runs(run_once, 1, warm=0)
+        st = res[0][1]
+        out["ranks_%d" % world] = {"time_s": t, "iterations": st["iterations"], "branches_match": st["branch"] == sw["branch"],
+                                   "halo_rows_per_iteration_rank0": float(np.mean(st["halo_rows"]))}
+    print(json.dumps({"workload": "row-block split of SP2, ranks as threads on one GPU, 3D tight-binding gapped "
+                                  "N=%d tau=%g tol=1e-10" % (n, tau), **out}), flush=True)
+
+
 def run_sp2(a):
     """Whole SP2 purifications of a gapped 3D tight-binding H (A/B onsite splitting 10):
     FP64 against mixed precision, time to solution and distance between the results."""
@@ -950,7 +1000,8 @@ def run_sizing(a):
 def main():
     a = parse()
     if a.n is None:
-        a.n = {"sp2": 131072, "sizing": 1048576, "model": 32000, "schedule": 131072}.get(a.workload, 262144)
+        a.n = {"sp2": 131072, "sizing": 1048576, "model": 32000, "schedule": 131072,
+               "rowblock": 131072}.get(a.workload, 262144)
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "sp2":
@@ -963,6 +1014,8 @@ def main():
         run_model(a)
     elif a.workload == "schedule":
         run_schedule(a)
+    elif a.workload == "rowblock":
+        run_rowblock(a)
     else:
         run_ours(a)
 

@@ -349,13 +349,23 @@ class GPUBlockOps:
         return [tr], [fro]
 
     def update(self, X, r0, B, up, tau):
+        """The block's product with the update, sized as sp2_purify sizes it (4x the longest row
+        of X, at least 64, grown to the exact length on overflow) and then cut to its longest
+        row, so that widths follow the rows and not the guesses."""
         S = self.S
         alpha, beta = (-1.0, 2.0) if up else (1.0, 0.0)
-        w = min(B.n, max(64, 4 * X.width))
+        longest = int(X.nnz.max().item()) if X.n else 0
+        w = min(B.n, max(64, ((4 * longest + 31) // 32) * 32))
         while True:
             Y = S.Ellpack.empty(X.n, w)
             rc, req, _, _ = S.ellpack_multiply_block(X, r0, B, X if up else None, Y, alpha, beta, tau,
                                                      stream=self.stream, raise_on_overflow=False)
             if rc == 0:
-                return Y
-            w = ((req + 31) // 32) * 32
+                break
+            w = min(B.n, ((req + 31) // 32) * 32)
+        tight = max(32, ((req + 31) // 32) * 32)
+        if tight < Y.width:
+            Z = S.Ellpack.empty(X.n, tight)
+            S.ellpack_copy(Y, Z, self.stream)
+            Y = Z
+        return Y

@@ -179,6 +179,13 @@ int sp2_x0_block(const ellpack_t *H, int32_t row0, double emin, double emax, dou
                  void *stream);
 int ellpack_stats_block(const ellpack_t *X, int32_t row0, double *trace, double *frobenius2, void *stream);
 
+/* The halo of a row block: the distinct columns k that X's stored entries name outside the
+ * block's rows row0 .. row0 + X->n - 1 (columns outside 0 .. ncols - 1 ignored), written
+ * in ascending order to rows (device int32[ncols], caller-owned); *count (host) receives
+ * how many.  These are the rows of X the block's product needs from other GPUs.
+ * Synchronises `stream`.  Errors: SP2E_ARG, SP2E_NOMEM, SP2E_CUDA. */
+int ellpack_halo_rows(const ellpack_t *X, int32_t row0, int32_t ncols, int32_t *rows, int32_t *count, void *stream);
+
 /*
  * A <- drop_tau(alpha * A + beta * B) (the "SP2 Loop Misc" update, Section "Performance
  * Evaluation using an ExaSP2 Application"): pattern is the union of the two rows, keep

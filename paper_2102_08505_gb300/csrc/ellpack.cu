@@ -608,6 +608,120 @@ extern "C" int ellpack_gershgorin(const ellpack_t *H, double *emin, double *emax
   return SP2_OK;
 }
 
+// ------------------------------------------------------------------ halo rows
+// The rows a block's entries name outside the block, ascending: a flag per column, then a
+// two-level stable compaction (per-CTA counts, one CTA's scan, per-CTA ordered writes).
+constexpr int kHaloPer = 4096;  // flags per CTA of the compaction
+template <typename T>
+__global__ void halo_mark_kernel(EllView<T> X, int row0, int ncols, unsigned char *__restrict__ flag) {
+  const int warps = (gridDim.x * blockDim.x) >> 5, lane = threadIdx.x & 31;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < X.n; r += warps) {
+    const int k = min(X.nnz[r], X.w);
+    for (int s = lane; s < k; s += 32) {
+      const int j = X.idx[(size_t)r * X.w + s];
+      if ((unsigned)j < (unsigned)ncols && (j < row0 || j >= row0 + X.n)) flag[j] = 1;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) halo_count_kernel(const unsigned char *__restrict__ flag, int ncols,
+                                                         int *__restrict__ part) {
+  __shared__ int s[256];
+  const int base = blockIdx.x * kHaloPer;
+  int c = 0;
+  for (int i = threadIdx.x; i < kHaloPer && base + i < ncols; i += 256) c += flag[base + i];
+  s[threadIdx.x] = c;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+// Exclusive scan of the m per-CTA counts in place; the total into part[m].
+__global__ void __launch_bounds__(1024) halo_scan_kernel(int *__restrict__ part, int m) {
+  __shared__ int s[1024];
+  int carry = 0;
+  for (int c0 = 0; c0 < m; c0 += 1024) {
+    const int i = c0 + (int)threadIdx.x;
+    const int v = i < m ? part[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan
+      const int y = (int)threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+      __syncthreads();
+      s[threadIdx.x] += y;
+      __syncthreads();
+    }
+    if (i < m) part[i] = carry + s[threadIdx.x] - v;
+    const int tot = s[1023];
+    __syncthreads();
+    carry += tot;
+  }
+  if (threadIdx.x == 0) part[m] = carry;
+}
+
+__global__ void __launch_bounds__(256) halo_write_kernel(const unsigned char *__restrict__ flag, int ncols,
+                                                         const int *__restrict__ part, int *__restrict__ rows) {
+  __shared__ int s_warp[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int base = blockIdx.x * kHaloPer;
+  int pos = part[blockIdx.x];
+  for (int c0 = 0; c0 < kHaloPer; c0 += 256) {
+    const int i = base + c0 + (int)threadIdx.x;
+    const bool on = c0 + (int)threadIdx.x < kHaloPer && i < ncols && flag[i];
+    const unsigned m = __ballot_sync(0xffffffffu, on);
+    if (lane == 0) s_warp[wid] = __popc(m);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < 8; ++w) {
+      if (w < wid) before += s_warp[w];
+      total += s_warp[w];
+    }
+    if (on) rows[pos + before + __popc(m & ((1u << lane) - 1u))] = i;
+    pos += total;
+    __syncthreads();
+  }
+}
+
+extern "C" int ellpack_halo_rows(const ellpack_t *X, int32_t row0, int32_t ncols, int32_t *rows, int32_t *count,
+                                 void *stream) {
+  SP2_TRY(check_matrix(X, "ellpack_halo_rows"));
+  if (!rows || !count) return fail(SP2E_ARG, "ellpack_halo_rows: null output");
+  if (row0 < 0 || ncols < 1 || (long long)row0 + X->n > (long long)ncols)
+    return fail(SP2E_ARG, "ellpack_halo_rows: rows %d .. %lld outside 0 .. %d", row0, (long long)row0 + X->n - 1,
+                ncols - 1);
+  cudaStream_t s = as_stream(stream);
+  const int ctas = (ncols + kHaloPer - 1) / kHaloPer;
+  unsigned char *flag = nullptr;
+  int *part = nullptr;
+  SP2_TRY(dev_alloc((void **)&flag, (size_t)ncols, s));
+  int rc = dev_alloc((void **)&part, sizeof(int) * ((size_t)ctas + 1), s);
+  int h = 0;
+  if (rc == SP2_OK) {
+    cudaError_t e = cudaMemsetAsync(flag, 0, (size_t)ncols, s);
+    if (e == cudaSuccess) {
+      const int grid = grid_for_rows(X->n, 8);
+      if (X->dtype == SP2_F64) halo_mark_kernel<double><<<grid, 256, 0, s>>>(view<double>(X), row0, ncols, flag);
+      else halo_mark_kernel<float><<<grid, 256, 0, s>>>(view<float>(X), row0, ncols, flag);
+      halo_count_kernel<<<ctas, 256, 0, s>>>(flag, ncols, part);
+      halo_scan_kernel<<<1, 1024, 0, s>>>(part, ctas);
+      halo_write_kernel<<<ctas, 256, 0, s>>>(flag, ncols, part, rows);
+      note_launch(); note_launch(); note_launch(); note_launch();
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, part + ctas, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "ellpack_halo_rows", __FILE__, __LINE__);
+  }
+  dev_free(flag, s);
+  dev_free(part, s);
+  SP2_TRY(rc);
+  *count = h;
+  return SP2_OK;
+}
+
 extern "C" int ellpack_gershgorin_block(const ellpack_t *H, int32_t row0, double *emin, double *emax, void *stream) {
   SP2_TRY(check_matrix(H, "ellpack_gershgorin_block"));
   if (!emin || !emax) return fail(SP2E_ARG, "ellpack_gershgorin_block: null output");

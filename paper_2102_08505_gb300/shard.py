@@ -216,7 +216,8 @@ def fetch_halo(comm, bounds, r0, idx, val, nnz, req):
     dev, w = idx.device, idx.shape[1]
     world, me = comm.world, comm.rank
     peers = [q for q in range(world) if q != me]
-    want = {q: torch.tensor(req.get(q, np.zeros(0, np.int64)), dtype=torch.int64, device=dev) for q in peers}
+    empty = torch.zeros(0, dtype=torch.int64, device=dev)
+    want = {q: torch.as_tensor(req[q], device=dev).to(torch.int64) if q in req else empty for q in peers}
     # 1. how many rows each peer wants from this rank
     cnt_out = {q: torch.tensor([want[q].numel()], dtype=torch.int64, device=dev) for q in peers}
     cnt_in = {q: torch.zeros(1, dtype=torch.int64, device=dev) for q in peers}
@@ -262,7 +263,7 @@ def row_block_sp2(comm, bounds, H_blk, nocc, tol, tau, backend, max_iter=100, st
         w = int(comm.reduce_scalar(backend.width(X), "max"))
         X = backend.widen(X, w)
         idx, val, nnz = backend.arrays(X)
-        req = halo_requests(*backend.host_pattern(X), r0, r1, bounds)
+        req = backend.halo_requests(X, r0, r1, bounds)
         halo = fetch_halo(comm, bounds, r0, idx, val, nnz, req)
         st["halo_rows"].append(int(halo[0].numel()))
         B = backend.extended(X, r0, n, halo)
@@ -324,8 +325,12 @@ class GPUBlockOps:
     def arrays(self, X):
         return X.idx, X.val, X.nnz
 
-    def host_pattern(self, X):
-        return X.idx.cpu().numpy(), X.nnz.cpu().numpy()
+    def halo_requests(self, X, r0, r1, bounds):
+        """{owner rank: device tensor of the rows it must send}, from the library's halo list."""
+        import torch
+        rows = self.S.ellpack_halo_rows(X, r0, bounds[-1], self.stream).to(torch.int64)
+        cut = torch.searchsorted(rows, torch.tensor(bounds, dtype=torch.int64, device=rows.device)).cpu().tolist()
+        return {q: rows[cut[q]:cut[q + 1]] for q in range(len(bounds) - 1) if cut[q + 1] > cut[q]}
 
     def extended(self, X, r0, n, halo):
         """A matrix of n rows holding the block's rows and the halo rows at their global

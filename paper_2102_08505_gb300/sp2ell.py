@@ -109,6 +109,7 @@ def _load():
         "ellpack_gershgorin_block": ([E, I, P(D), P(D), V], ctypes.c_int),
         "sp2_x0_block": ([E, I, D, D, D, E, V], ctypes.c_int),
         "ellpack_stats_block": ([E, I, P(D), P(D), V], ctypes.c_int),
+        "ellpack_halo_rows": ([E, I, I, V, P(I), V], ctypes.c_int),
         "sp2_fma_peak": ([I, I, P(D), V], ctypes.c_int),
         "ellpack_trace_noalloc": ([E, P(D), P(D), V], ctypes.c_int),
         "sp2_options_default": ([P(sp2_options)], None),
@@ -331,6 +332,16 @@ def ellpack_stats_block(X, row0, stream=None):
     tr, fro = ctypes.c_double(), ctypes.c_double()
     _check(lib.ellpack_stats_block(_d(X), int(row0), ctypes.byref(tr), ctypes.byref(fro), _stream(stream)))
     return tr.value, fro.value
+
+
+def ellpack_halo_rows(X, row0, ncols, stream=None):
+    """Ascending int32 device tensor of the rows outside the block (global rows row0 ..
+    row0 + X.n - 1) that X's entries name."""
+    import torch
+    rows = torch.empty(int(ncols), dtype=torch.int32, device="cuda")
+    cnt = ctypes.c_int32()
+    _check(lib.ellpack_halo_rows(_d(X), int(row0), int(ncols), rows.data_ptr(), ctypes.byref(cnt), _stream(stream)))
+    return rows[:cnt.value]
 
 
 def ellpack_add(A, B, alpha=1.0, beta=1.0, tau=0.0, stream=None):

@@ -121,3 +121,21 @@ def test_block_argument_checks(gpu):
     with pytest.raises(S.Sp2Error) as e:  # beta != 0 needs the addend rows
         S.ellpack_multiply_block(blk, 400, dX, None, out, -1.0, 2.0, 1e-5)
     assert e.value.code == S.SP2E_ARG
+
+
+def test_halo_rows_match_the_pattern(gpu):
+    """ellpack_halo_rows: the distinct columns a block's entries name outside the block,
+    ascending, against the same set taken from the pattern on the host."""
+    S = gpu
+    from paper_2102_08505_gb300 import shard
+    n = 6000
+    X = x_of_tight_binding(n, 10, 1e-5)
+    for r0, r1 in ((0, 1500), (1500, 1501), (2999, 6000)):
+        blk = rows_of(X, r0, r1)
+        got = S.ellpack_halo_rows(dev(S, blk, S.SP2_F64), r0, n).cpu().numpy()
+        want = np.concatenate(list(shard.halo_requests(blk.idx, blk.nnz, r0, r1, [0, r0, r1, n]).values()) or
+                              [np.zeros(0, np.int64)])
+        assert np.array_equal(got, np.sort(want)), (r0, r1)
+        assert len(got) > 0
+    with pytest.raises(S.Sp2Error):
+        S.ellpack_halo_rows(dev(S, rows_of(X, 0, 10), S.SP2_F64), n - 5, n)  # block outside 0 .. n-1

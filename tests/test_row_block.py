@@ -48,8 +48,8 @@ class OracleBlockOps:
     def arrays(self, X):
         return torch.from_numpy(X.idx), torch.from_numpy(X.val), torch.from_numpy(X.nnz)
 
-    def host_pattern(self, X):
-        return X.idx, X.nnz
+    def halo_requests(self, X, r0, r1, bounds):
+        return shard.halo_requests(X.idx, X.nnz, r0, r1, bounds)
 
     def extended(self, X, r0, n, halo):
         rows, hi, hv, hn = (t.numpy() for t in halo)

@@ -173,3 +173,24 @@ def test_multiply_block_rejects_bad_arguments(S):
     assert b"aliases" in blk(A, 0, Bfull, C, C, be=2.0)
     assert b"tau" in blk(A, 0, Bfull, None, Out, tau=-1.0)
     assert b"not finite" in blk(A, 0, Bfull, None, Out, al=float("nan"))
+
+
+def test_block_setup_calls_reject_bad_arguments(S):
+    """ellpack_halo_rows, ellpack_gershgorin_block, sp2_x0_block and ellpack_stats_block:
+    rows outside the matrix, missing outputs and bad bounds come back as SP2E_ARG before
+    any device call."""
+    keep = []
+    X = fake_matrix(S, n=8, keep=keep)
+    X0 = fake_matrix(S, n=8, w=64, keep=keep)
+    rows = np.zeros(16, np.int32)
+    cnt = ctypes.c_int32()
+    d1, d2 = ctypes.c_double(), ctypes.c_double()
+    err = lambda rc: S.lib.sp2_last_error_string() if rc == S.SP2E_ARG else None
+    assert b"outside" in err(S.lib.ellpack_halo_rows(ctypes.byref(X), 9, 16, rows.ctypes.data, ctypes.byref(cnt), None))
+    assert b"outside" in err(S.lib.ellpack_halo_rows(ctypes.byref(X), -1, 16, rows.ctypes.data, ctypes.byref(cnt), None))
+    assert b"null" in err(S.lib.ellpack_halo_rows(ctypes.byref(X), 0, 16, None, ctypes.byref(cnt), None))
+    assert b"row0" in err(S.lib.ellpack_gershgorin_block(ctypes.byref(X), -2, ctypes.byref(d1), ctypes.byref(d2), None))
+    assert b"row0" in err(S.lib.ellpack_stats_block(ctypes.byref(X), -2, ctypes.byref(d1), ctypes.byref(d2), None))
+    assert b"bounds" in err(S.lib.sp2_x0_block(ctypes.byref(X), 0, 1.0, 1.0, 1e-5, ctypes.byref(X0), None))
+    assert b"tau" in err(S.lib.sp2_x0_block(ctypes.byref(X), 0, -1.0, 1.0, -1.0, ctypes.byref(X0), None))
+    assert b"width" in err(S.lib.sp2_x0_block(ctypes.byref(X), 0, -1.0, 1.0, 1e-5, ctypes.byref(X), None))

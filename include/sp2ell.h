@@ -459,6 +459,18 @@ typedef struct sp2_options {
   double stall_ratio;   /* the armed stall rule fires once err_n >= stall_ratio * err_{n-2};
                            in (0, 1], default 1 (two updates brought no reduction); below 1
                            it also ends a slow monotone drift at the floor tau sets */
+  int32_t route_rows;   /* automatic first pass (spgemm_path 0) of a symmetric product: a
+                           cascade of passes, each over the rows that outgrew the previous
+                           one's accumulator blocks: tight compact, loose compact, full rows,
+                           then the deferred-row bins.  1 = each row keeps a flag (on the
+                           device) with the level it last needed, and later updates start it
+                           there (default); 0 = every row starts at the cascade's first level */
+  int32_t pad;
+  double level_up_frac; /* the cascade starts at the tight compact level (fewest blocks per
+                           row, most rows per SM); once its first pass passes on more than
+                           this fraction of the rows in an update, it starts one level higher
+                           (loose, then full rows) for the rest of the run.  > 0; default 1
+                           (>= 1 keeps the tight start) */
 } sp2_options;
 
 typedef struct sp2_stats {
@@ -479,6 +491,15 @@ typedef struct sp2_stats {
   int32_t branch[SP2_STATS_CAP];        /* per update: 1 = X^2, 2 = 2X - X^2 */
   int64_t nnz_total[SP2_STATS_CAP];     /* per visited X_n */
   int32_t max_row_nnz[SP2_STATS_CAP];   /* per visited X_n */
+  int32_t rows_level1[SP2_STATS_CAP];   /* per update: rows the tight compact pass passed
+                                           on to the loose one (cascade) */
+  int32_t rows_level2[SP2_STATS_CAP];   /* per update: rows passed on to the full-row pass */
+  int32_t rows_deferred[SP2_STATS_CAP]; /* per update: rows handed to the deferred-row bins */
+  int32_t rows_routed[SP2_STATS_CAP];   /* per update: rows whose route flag sent them past
+                                           the cascade's first pass unstarted */
+  int32_t level[SP2_STATS_CAP];         /* per update: the level the cascade of a symmetric
+                                           product started at (0 tight, 1 loose, 2 full
+                                           rows); -1 for other first passes */
 } sp2_stats;
 
 /*
@@ -504,16 +525,19 @@ typedef struct sp2_step_info {
   int32_t max_row_nnz;     /* out: longest row of X' */
   int32_t required_width;  /* out: longest post-threshold row (valid on overflow too) */
   int32_t spgemm_path;     /* in: SpGEMM first pass, as sp2_options.spgemm_path */
-  int32_t rows_deferred;   /* out: rows the first pass handed to the deferred-row bins (the
-                              shared-memory window, then the 2^14-slot table): rows that
-                              outgrew its accumulator, and with the one-warp pass rows of X
-                              longer than 512 entries */
+  int32_t rows_deferred;   /* out: rows the first pass (for spgemm_path 0 of a symmetric
+                              product: the last pass of the cascade) handed to the
+                              deferred-row bins (the shared-memory window, then the
+                              2^14-slot table): rows that outgrew its accumulator, and with
+                              the one-warp passes rows of X longer than 512 entries */
   int32_t rows_dense;      /* out: rows handed further to the dense global-row pass */
   int32_t spgemm_path_used; /* out: the first-pass variant that ran (the tuner's choice
                                for SP2_PATH_TUNED) */
   int32_t symmetric;       /* in: 1 = X is exactly symmetric (not checked): the product's
                               upper triangle is computed and mirrored */
-  int32_t pad;
+  int32_t compact_level;   /* in: symmetric product with spgemm_path 0: the level its
+                              cascade of first passes starts at, 0 tight (the default),
+                              1 loose, 2 full rows */
 } sp2_step_info;
 
 /*
@@ -527,7 +551,8 @@ typedef struct sp2_step_info {
  */
 int sp2_step(const ellpack_t *X, ellpack_t *Xn, double nocc, double tau, sp2_step_info *info, void *stream);
 
-/* Fills *opt with the defaults (F64, max_iter 100, stall rule on, tail 2, tau 1e-5). */
+/* Fills *opt with the defaults (F64, max_iter 100, stall rule on, tail 2, tau 1e-5,
+ * symmetric products, route flags on, the cascade kept at the tight start). */
 void sp2_options_default(sp2_options *opt);
 
 /*
@@ -563,6 +588,7 @@ int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2_options *o
  * ellpack_destroy) and stats[m] (optional) the per-iteration record of matrix m.
  * Returns SP2E_NOTCONV (D still set) if some matrix reached max_iter.  If a row
  * outgrows the working width the loop restarts wider (stats[m].regrows counts it).
+ * The products are shared by the batch: the per-update row counts of stats[m] stay 0.
  * Errors: SP2E_ARG, SP2E_NOMEM, SP2E_CUDA, SP2E_OVERFLOW, SP2E_NONFINITE.  Synchronises
  * `stream` (NULL: a private stream is used for the graph).
  */

@@ -393,6 +393,8 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
     return fail(SP2E_ARG, "sp2_purify_batched: stall_arm must be > 0");
   if (!(opt.stall_ratio > 0.0 && opt.stall_ratio <= 1.0))
     return fail(SP2E_ARG, "sp2_purify_batched: stall_ratio must be in (0, 1]");
+  if (opt.route_rows != 0 && opt.route_rows != 1)
+    return fail(SP2E_ARG, "sp2_purify_batched: route_rows must be 0 or 1");
   long long ntot_ll = 0;
   int wh = 1, nmax = 0;
   std::vector<int> off(count + 1, 0);
@@ -486,6 +488,16 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
     unsigned char *d_sym = nullptr;
     const size_t sym_bytes = opt.symmetric ? sym_scratch_bytes(ntot, width, width, SP2_F64) : 0;
     if (opt.symmetric) SP2_TRY(db.get(&d_sym, sym_bytes));
+    // The symmetric products run the cascade of first passes from the tight compact level:
+    // each row finds its level inside the captured loop, which takes no feedback from the
+    // host.  Route flags (route_rows 1), one set per precision, start a row at the level it
+    // needed last time.
+    unsigned char *d_route32 = nullptr, *d_route64 = nullptr;
+    if (opt.route_rows && use32) SP2_TRY(db.get(&d_route32, (size_t)ntot));
+    if (opt.route_rows && use64) SP2_TRY(db.get(&d_route64, (size_t)ntot));
+    if (d_route32) SP2_CUDA(cudaMemsetAsync(d_route32, 0, (size_t)ntot, s));
+    if (d_route64) SP2_CUDA(cudaMemsetAsync(d_route64, 0, (size_t)ntot, s));
+    const int level = 0;
     SP2_TRY(db.get(&sd.trX, sizeof(double) * (size_t)count * kCap));
     SP2_TRY(db.get(&sd.trX2, sizeof(double) * (size_t)count * kCap));
     SP2_TRY(db.get(&sd.err, sizeof(double) * (size_t)count * kCap));
@@ -570,7 +582,7 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
         if (tune_find(cur->dtype, ntot, mean, path)) return SP2_OK;
         MultiplyArgs a{cur, cur, nullptr, nxt, 1.0, 0.0, opt.tau, 0};
         a.sym = opt.symmetric != 0;
-        a.compact_level = 1;  // captured once, without feedback on deferred rows: the loose compact variants
+        a.compact_level = level;
         a.sym_prealloc = d_sym;
         a.sym_prealloc_bytes = sym_bytes;
         SP2_TRY(tune_multiply(a, mean, d_rowstat, c, 2, path, nullptr, s));
@@ -594,7 +606,8 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
         a.bv = bv32;
         a.fb_prealloc = d_fb;
         a.sym = opt.symmetric != 0;
-        a.compact_level = 1;  // captured once, without feedback on deferred rows: the loose compact variants
+        a.compact_level = level;
+        if (path32 == 0) a.route = d_route32;
         a.sym_prealloc = d_sym;
         a.sym_prealloc_bytes = sym_bytes;
         SP2_TRY(multiply_async(a, d_rowstat, d_c32, s));
@@ -604,7 +617,8 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
         a.bv = bv64;
         a.fb_prealloc = d_fb;
         a.sym = opt.symmetric != 0;
-        a.compact_level = 1;  // captured once, without feedback on deferred rows: the loose compact variants
+        a.compact_level = level;
+        if (path64 == 0) a.route = d_route64;
         a.sym_prealloc = d_sym;
         a.sym_prealloc_bytes = sym_bytes;
         SP2_TRY(multiply_async(a, d_rowstat, d_c64, s));
@@ -725,6 +739,8 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
           o.branch[t] = br[(size_t)m * kCap + t];
           o.nnz_total[t] = nz[(size_t)m * kCap + t];
           o.max_row_nnz[t] = mr[(size_t)m * kCap + t];
+          // the products of the batch are shared: no per-matrix deferral counts
+          o.level[t] = t < o.iterations ? (opt.symmetric && opt.spgemm_path == 0 ? level : -1) : 0;
         }
       }
     }

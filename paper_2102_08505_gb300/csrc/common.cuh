@@ -119,6 +119,9 @@ struct StepResult {
   int nonfinite;       // 1 if tr or fro is not finite
   int n_fallback2;     // rows deferred further to the dense global-row kernel
   int n_heavy;         // of n_fallback: rows sent on for the length of their row of A alone
+  int n_routed;        // rows whose route flag sent them past the first pass unstarted
+  int n_level1;        // rows the tight compact pass passed on to the loose one
+  int n_level2;        // rows passed on to the full-row pass
 };
 
 // Device control block of one multiply launch.
@@ -129,6 +132,9 @@ struct SpgemmCtl {
   int n_fallback2;  // count of the second deferred-row list
   int n_fallbackw;  // count of the rows the window bin passes on
   int n_heavy;      // rows of the first list deferred for the length of their row of A
+  int n_routed;     // rows the first pass of a cascade sent on unstarted (route flag)
+  int n_level1;     // count of the list of the loose compact pass of a cascade
+  int n_level2;     // count of the list of the full-row pass of a cascade
 };
 
 // Bitonic network over the 32*E keys a warp holds, E per lane in lane-major order
@@ -194,6 +200,15 @@ struct BatchView {
 // the columns j >= i.  tp[i*A.w + t] is the first position of row k = A.idx[i, t] of B
 // with a column >= i (that source row is read from there on); tpd[i] is the same
 // position in the addend row i.  Null pointers: full rows.
+// Rows of one first pass of a cascade: all rows (list null) or the rows of a device list
+// whose count a previous pass left at *count; level = the pass's compact level (0 tight,
+// 1 loose, 2 full rows), compared with the per-row route flags.
+struct PassRows {
+  const int *list = nullptr;
+  const int *count = nullptr;
+  int level = 0;
+};
+
 struct Upper {
   const int *tp = nullptr;
   const int *tpd = nullptr;
@@ -209,9 +224,15 @@ struct MultiplyArgs {
   // X*X (+ X) with X symmetric (A == B, Add null or A): compute the upper triangle and
   // mirror it (bitwise the same result as full rows, about half the products)
   bool sym = false;
-  // path 0 of a symmetric product: 0 the tight compact variant, 1 the loose one, 2 the
-  // full-row variants
+  // path 0 of a symmetric product: a cascade of first passes from this level on (0 the
+  // tight compact variant, 1 the loose one, 2 the full-row variants), each over the rows
+  // that outgrew the previous one; the rows that outgrow the full-row pass go to the bins
   int compact_level = 0;
+  // per-row route flags (n bytes, or null) of the automatic first passes: the level a row
+  // starts at.  A pass skips (passes on unstarted) a row flagged above its level, and
+  // flags a row that outgrows its blocks with the next level, so that later products
+  // start it there
+  unsigned char *route = nullptr;
   void *sym_prealloc = nullptr;  // scratch of the symmetric product (null: allocated per call)
   size_t sym_prealloc_bytes = 0;
   Upper up{};  // set internally for the upper-triangle pass

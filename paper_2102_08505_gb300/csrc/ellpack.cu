@@ -202,6 +202,9 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_rows_kernel(const doubl
     o.n_fallback = ctl ? ctl->n_fallback : 0;
     o.n_fallback2 = ctl ? ctl->n_fallback2 : 0;
     o.n_heavy = ctl ? ctl->n_heavy : 0;
+    o.n_routed = ctl ? ctl->n_routed : 0;
+    o.n_level1 = ctl ? ctl->n_level1 : 0;
+    o.n_level2 = ctl ? ctl->n_level2 : 0;
     o.nonfinite = (isfinite(o.tr) && isfinite(o.fro)) ? 0 : 1;
     *res = o;
   }

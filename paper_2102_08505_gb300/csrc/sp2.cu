@@ -25,6 +25,7 @@ struct Buffers {
   StepResult *dres = nullptr;
   double *bounds = nullptr;
   void *sizing = nullptr;  // counts, maxima, features, predictions (sizing modes 1 and 2)
+  unsigned char *route = nullptr;  // per-row route flags of the first pass (route_rows 1)
   ellpack_t X{}, Y{}, Hf{};
   bool hf_owned = false;
   ~Buffers() {
@@ -33,6 +34,7 @@ struct Buffers {
     dev_free(dres, s);
     dev_free(bounds, s);
     dev_free(sizing, s);
+    dev_free(route, s);
     if (X.owner) ellpack_destroy(&X, s);
     if (Y.owner) ellpack_destroy(&Y, s);
     if (hf_owned) ellpack_destroy(&Hf, s);
@@ -77,6 +79,8 @@ extern "C" void sp2_options_default(sp2_options *o) {
   o->stall_arm = 0.1;
   o->stall_ratio = 1.0;
   o->symmetric = 1;
+  o->route_rows = 1;
+  o->level_up_frac = 1.0;
 }
 
 extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2_options *opt_in, ellpack_t *D,
@@ -107,6 +111,9 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   if (!(opt.stall_arm > 0.0) || !isfinite(opt.stall_arm)) return fail(SP2E_ARG, "sp2_purify: stall_arm must be > 0");
   if (!(opt.stall_ratio > 0.0 && opt.stall_ratio <= 1.0))
     return fail(SP2E_ARG, "sp2_purify: stall_ratio must be in (0, 1]");
+  if (opt.route_rows != 0 && opt.route_rows != 1) return fail(SP2E_ARG, "sp2_purify: route_rows must be 0 or 1");
+  if (!(opt.level_up_frac > 0.0) || !isfinite(opt.level_up_frac))
+    return fail(SP2E_ARG, "sp2_purify: level_up_frac must be finite and > 0");
   if (opt.sizing == 2 && (!opt.predictor || !opt.predictor->params))
     return fail(SP2E_ARG, "sp2_purify: sizing 2 needs a created predictor");
   const double switch_tol = opt.switch_tol > 0.0 ? opt.switch_tol : (tol > 1e-4 ? tol : 1e-4);
@@ -122,6 +129,10 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   SP2_TRY(dev_alloc((void **)&b.ctl, sizeof(SpgemmCtl), s));
   SP2_TRY(dev_alloc((void **)&b.dres, sizeof(StepResult), s));
   SP2_TRY(dev_alloc((void **)&b.bounds, 2 * sizeof(double), s));
+  if (opt.route_rows) {
+    SP2_TRY(dev_alloc((void **)&b.route, (size_t)n, s));
+    SP2_CUDA(cudaMemsetAsync(b.route, 0, (size_t)n, s));
+  }
   // sizing scratch: max int, max float, counts int[n], rmax float[n], pred float[n],
   // features float[16n], then the prediction-error sums (kPredErrDoubles doubles)
   int *sz_counts = nullptr, *sz_dmax = nullptr;
@@ -214,6 +225,12 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   int status = 0;  // set when the loop stops: 0 err < tol, 1 stall rule, 2 max_iter
   int last_count = res.max_nnz;
   int compact_level = 0;
+  // the route flags (the level each row starts at) belong to one precision's passes:
+  // cleared when the precision changes
+  auto clear_route = [&]() -> int {
+    if (b.route) SP2_CUDA(cudaMemsetAsync(b.route, 0, (size_t)n, s));
+    return SP2_OK;
+  };
   for (;;) {
     if (res.nonfinite) return fail(SP2E_NONFINITE, "sp2_purify: non-finite trace at iteration %d", it);
     const double trX = res.tr, trX2 = res.fro;
@@ -250,6 +267,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
           ellpack_t t = b.X; b.X = b.Y; b.Y = t;
           fp32 = false;
           phase = TAIL;
+          SP2_TRY(clear_route());
           st.fp32_iterations = it;
         } else {
           if (fp32 && status != 2) status = err < tol ? 0 : 1;
@@ -306,6 +324,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
       MultiplyArgs a{&b.X, &b.X, beta != 0.0 ? &b.X : nullptr, &b.Y, alpha, beta, opt.tau, lg};
       a.sym = opt.symmetric != 0;
       a.compact_level = compact_level;
+      if (lg == 0) a.route = b.route;
       SP2_TRY(multiply_async(a, b.rowstat, b.ctl, s));
       launch_reduce_rows(b.rowstat, b.Y.nnz, n, b.ctl, b.dres, s);
       SP2_CUDA(cudaGetLastError());
@@ -344,11 +363,21 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
       rows_seen += (double)n;
     }
     last_count = res.max_count;
-    // the compact first passes (automatic for symmetric products) hold fewer blocks per row:
-    // once one defers more than 0.2 % of the rows, the next larger variant takes over for the
-    // rest of the run (tight -> loose -> full rows)
-    // rows deferred for their length alone take the bins at every level: not counted here
-    if (compact_level < 2 && opt.symmetric && lg == 0 && res.n_fallback - res.n_heavy > n / 500) ++compact_level;
+    if (it < SP2_STATS_CAP) {
+      st.rows_level1[it] = res.n_level1;
+      st.rows_level2[it] = res.n_level2;
+      st.rows_deferred[it] = res.n_fallback;
+      st.rows_routed[it] = res.n_routed;
+      st.level[it] = (opt.symmetric && lg == 0) ? compact_level : -1;
+    }
+    // the cascade of first passes (automatic for symmetric products) starts at the tight
+    // compact level; once its first pass passes on more than level_up_frac of the rows, the
+    // cascade starts one level higher for the rest of the run.  Rows passed on for their
+    // length alone (FP32, rows of X above 512 entries) are not counted
+    if (compact_level < 2 && opt.symmetric && lg == 0) {
+      const int passed = (compact_level == 0 ? res.n_level1 : res.n_level2) - res.n_heavy;
+      if ((double)passed > opt.level_up_frac * (double)n) ++compact_level;
+    }
     ellpack_t t = b.X; b.X = b.Y; b.Y = t;
     ++it;
   }
@@ -445,6 +474,7 @@ extern "C" int sp2_step(const ellpack_t *X, ellpack_t *Xn, double nocc, double t
   if (!(tau >= 0.0) || !isfinite(tau)) return fail(SP2E_ARG, "sp2_step: tau must be finite and >= 0");
   if (!isfinite(nocc)) return fail(SP2E_ARG, "sp2_step: nocc not finite");
   if (!valid_path(info->spgemm_path)) return fail(SP2E_ARG, "sp2_step: spgemm_path must be -1, 0..4 or 7..12");
+  if (info->compact_level < 0 || info->compact_level > 2) return fail(SP2E_ARG, "sp2_step: compact_level must be 0, 1 or 2");
   const int n = X->n;
   Buffers b;
   b.s = as_stream(stream);
@@ -468,6 +498,7 @@ extern "C" int sp2_step(const ellpack_t *X, ellpack_t *Xn, double nocc, double t
   info->branch = up ? 2 : 1;
   MultiplyArgs a{X, X, up ? X : nullptr, Xn, up ? -1.0 : 1.0, up ? 2.0 : 0.0, tau, info->spgemm_path};
   a.sym = info->symmetric != 0;
+  a.compact_level = info->compact_level;
   if (a.path == SP2_PATH_TUNED) {
     double mean = 0.0;
     SP2_TRY(mean_row_nnz(X, &mean, s));

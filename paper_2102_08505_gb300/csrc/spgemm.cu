@@ -514,7 +514,8 @@ template <typename T, int R, int QW, bool KEEPZ, int SZ>
 __global__ void __launch_bounds__(BlockGeo<T, R, SZ>::WARPS * 32, 1)
     spgemm_block_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
                         int use_add, BatchView bv, Upper up, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
-                        int *__restrict__ fb_list, int *__restrict__ fb_count) {
+                        int *__restrict__ fb_list, int *__restrict__ fb_count, unsigned char *__restrict__ route,
+                        PassRows rows) {
   using Geo = BlockGeo<T, R, SZ>;
   constexpr int GW = Geo::GW, GSH = Geo::GSH, G = Geo::G;
   constexpr int SPAN = 32 * R;  // entries of a B row covered by one register slot of the group
@@ -529,7 +530,9 @@ __global__ void __launch_bounds__(BlockGeo<T, R, SZ>::WARPS * 32, 1)
   const unsigned lt = lanemask_lt();
   int wmax = 0, wover = 0;
 
-  for (int r = blockIdx.x * Geo::GROUPS + grp; r < A.n; r += gridDim.x * Geo::GROUPS) {
+  const int nrows = rows.list ? *rows.count : A.n;
+  for (int q = blockIdx.x * Geo::GROUPS + grp; q < nrows; q += gridDim.x * Geo::GROUPS) {
+    const int r = rows.list ? rows.list[q] : q;
     T alpha_r = alpha, beta_r = beta;
     int add_r = use_add;
     if (bv.row_mat) {  // same row for the whole group: every warp takes the same branch
@@ -538,6 +541,17 @@ __global__ void __launch_bounds__(BlockGeo<T, R, SZ>::WARPS * 32, 1)
       alpha_r = (T)bv.alpha[m];
       beta_r = (T)bv.beta[m];
       add_r = beta_r != T(0);
+    }
+    // flagged by an earlier product above this pass's level (it outgrew these blocks
+    // there): passed on unstarted.  Every warp of the group reads the flag before the
+    // barrier below, and only this group writes it, after that barrier, so the group
+    // takes one branch.
+    if (route && route[r] > rows.level) {
+      if (gt == 0) {
+        fb_list[atomicAdd(fb_count, 1)] = r;
+        if (!rows.list) atomicAdd(&ctl->n_routed, 1);
+      }
+      continue;
     }
     {  // clear the blocks and the table
       const T c = KEEPZ ? untouched<T>() : T(0);
@@ -739,6 +753,7 @@ __global__ void __launch_bounds__(BlockGeo<T, R, SZ>::WARPS * 32, 1)
       if (gt == 0) {
         const int p = atomicAdd(fb_count, 1);
         fb_list[p] = r;
+        if (route) route[r] = (unsigned char)(rows.level + 1);
       }
       group_sync<R>(grp);
       continue;
@@ -817,7 +832,8 @@ template <typename T, int QM, int S, bool KEEPZ, int SZ>
 __global__ void __launch_bounds__(BlockGeo<T, 1, SZ>::WARPS * 32, 1)
     spgemm_super_kernel(EllView<T> A, EllView<T> B, EllView<T> Add, EllOut<T> Out, T alpha, T beta, T tau,
                         int use_add, BatchView bv, Upper up, double2 *__restrict__ rowstat, SpgemmCtl *__restrict__ ctl,
-                        int *__restrict__ fb_list, int *__restrict__ fb_count) {
+                        int *__restrict__ fb_list, int *__restrict__ fb_count, unsigned char *__restrict__ route,
+                        PassRows rows) {
   using Geo = BlockGeo<T, 1, SZ>;
   constexpr int GW = Geo::GW, GSH = Geo::GSH, G = Geo::G;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -830,7 +846,9 @@ __global__ void __launch_bounds__(BlockGeo<T, 1, SZ>::WARPS * 32, 1)
   const unsigned lt = lanemask_lt();
   int wmax = 0, wover = 0;
 
-  for (int r = blockIdx.x * Geo::GROUPS + wid; r < A.n; r += gridDim.x * Geo::GROUPS) {
+  const int nrows = rows.list ? *rows.count : A.n;
+  for (int q = blockIdx.x * Geo::GROUPS + wid; q < nrows; q += gridDim.x * Geo::GROUPS) {
+    const int r = rows.list ? rows.list[q] : q;
     T alpha_r = alpha, beta_r = beta;
     int add_r = use_add;
     if (bv.row_mat) {
@@ -843,7 +861,14 @@ __global__ void __launch_bounds__(BlockGeo<T, 1, SZ>::WARPS * 32, 1)
     if (A.nnz[r] > kHeavyRowA) {  // straight to the deferred-row bins (see kHeavyRowA)
       if (lane == 0) {
         fb_list[atomicAdd(fb_count, 1)] = r;
-        atomicAdd(&ctl->n_heavy, 1);
+        if (!rows.list) atomicAdd(&ctl->n_heavy, 1);
+      }
+      continue;
+    }
+    if (route && route[r] > rows.level) {  // flagged above this level: passed on unstarted
+      if (lane == 0) {
+        fb_list[atomicAdd(fb_count, 1)] = r;
+        if (!rows.list) atomicAdd(&ctl->n_routed, 1);
       }
       continue;
     }
@@ -1025,6 +1050,7 @@ __global__ void __launch_bounds__(BlockGeo<T, 1, SZ>::WARPS * 32, 1)
       if (lane == 0) {
         const int p = atomicAdd(fb_count, 1);
         fb_list[p] = r;
+        if (route) route[r] = (unsigned char)(rows.level + 1);
       }
       continue;
     }
@@ -1625,7 +1651,8 @@ int launch_hash(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, const i
 }
 
 template <typename T, int R, int QW, bool KEEPZ, int SZ = 0>
-int launch_block(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
+int launch_block(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s,
+                 PassRows rows = PassRows{}) {
   using Geo = BlockGeo<T, R, SZ>;
   auto kern = spgemm_block_kernel<T, R, QW, KEEPZ, SZ>;
   static DeviceOnce once;
@@ -1638,14 +1665,15 @@ int launch_block(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
     return SP2_OK;
   }));
   const long long cap = (long long)num_sms() * once.value[dev];
-  const long long blocks = ((long long)a.A->n + Geo::GROUPS - 1) / Geo::GROUPS;
+  // a row list's length is on the device: the whole resident grid, idle CTAs exit at once
+  const long long blocks = rows.list ? cap : ((long long)a.A->n + Geo::GROUPS - 1) / Geo::GROUPS;
   int grid = (int)(blocks < cap ? blocks : cap);
   if (grid < 1) grid = 1;
   const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
   prof_begin(SP2_PROF_SPGEMM, s);
   kern<<<grid, Geo::WARPS * 32, Geo::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
                                                (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv, a.up,
-                                               rowstat, ctl, fb, fb_count);
+                                               rowstat, ctl, fb, fb_count, a.route, rows);
   note_launch();
   prof_end(SP2_PROF_SPGEMM, s);
   SP2_CUDA(cudaGetLastError());
@@ -1653,7 +1681,8 @@ int launch_block(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
 }
 
 template <typename T, int QM, int S, bool KEEPZ, int SZ = 0>
-int launch_super(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
+int launch_super(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s,
+                 PassRows rows = PassRows{}) {
   using Geo = BlockGeo<T, 1, SZ>;
   auto kern = spgemm_super_kernel<T, QM, S, KEEPZ, SZ>;
   static DeviceOnce once;
@@ -1666,14 +1695,15 @@ int launch_super(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
     return SP2_OK;
   }));
   const long long cap = (long long)num_sms() * once.value[dev];
-  const long long blocks = ((long long)a.A->n + Geo::GROUPS - 1) / Geo::GROUPS;
+  // a row list's length is on the device: the whole resident grid, idle CTAs exit at once
+  const long long blocks = rows.list ? cap : ((long long)a.A->n + Geo::GROUPS - 1) / Geo::GROUPS;
   int grid = (int)(blocks < cap ? blocks : cap);
   if (grid < 1) grid = 1;
   const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
   prof_begin(SP2_PROF_SPGEMM, s);
   kern<<<grid, Geo::WARPS * 32, Geo::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
                                                (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv, a.up,
-                                               rowstat, ctl, fb, fb_count);
+                                               rowstat, ctl, fb, fb_count, a.route, rows);
   note_launch();
   prof_end(SP2_PROF_SPGEMM, s);
   SP2_CUDA(cudaGetLastError());
@@ -1681,33 +1711,35 @@ int launch_super(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
 }
 
 template <typename T>
-int launch_super_auto(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
+int launch_super_auto(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s,
+                      PassRows rows = PassRows{}) {
   constexpr int QM = sizeof(T) == 8 ? 6 : 6;
-  return a.tau == 0.0 ? launch_super<T, QM, 2, true>(a, rowstat, ctl, fb, fb_count, s)
-                      : launch_super<T, QM, 2, false>(a, rowstat, ctl, fb, fb_count, s);
+  return a.tau == 0.0 ? launch_super<T, QM, 2, true>(a, rowstat, ctl, fb, fb_count, s, rows)
+                      : launch_super<T, QM, 2, false>(a, rowstat, ctl, fb, fb_count, s, rows);
 }
 
 // Compact variants for the upper-triangle rows of symmetric products: fewer accumulator
 // slots per row and fewer warps per row (2 for the column blocks), more rows per SM.
 template <typename T, int SZ>
 int launch_block_compact(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count,
-                         cudaStream_t s) {
-  return a.tau == 0.0 ? launch_block<T, 2, 2, true, SZ>(a, rowstat, ctl, fb, fb_count, s)
-                      : launch_block<T, 2, 2, false, SZ>(a, rowstat, ctl, fb, fb_count, s);
+                         cudaStream_t s, PassRows rows = PassRows{}) {
+  return a.tau == 0.0 ? launch_block<T, 2, 2, true, SZ>(a, rowstat, ctl, fb, fb_count, s, rows)
+                      : launch_block<T, 2, 2, false, SZ>(a, rowstat, ctl, fb, fb_count, s, rows);
 }
 template <typename T, int SZ>
 int launch_super_compact(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count,
-                         cudaStream_t s) {
-  return a.tau == 0.0 ? launch_super<T, 3, 2, true, SZ>(a, rowstat, ctl, fb, fb_count, s)
-                      : launch_super<T, 3, 2, false, SZ>(a, rowstat, ctl, fb, fb_count, s);
+                         cudaStream_t s, PassRows rows = PassRows{}) {
+  return a.tau == 0.0 ? launch_super<T, 3, 2, true, SZ>(a, rowstat, ctl, fb, fb_count, s, rows)
+                      : launch_super<T, 3, 2, false, SZ>(a, rowstat, ctl, fb, fb_count, s, rows);
 }
 
 // Block first pass with R warps per row; the register slots per warp cover the width of B.
 template <typename T, int R>
-int launch_block_r(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s) {
+int launch_block_r(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb, int *fb_count, cudaStream_t s,
+                   PassRows rows = PassRows{}) {
   constexpr int QW = (R == 1) ? 8 : (R == 2 ? 4 : 2);
-  return a.tau == 0.0 ? launch_block<T, R, QW, true>(a, rowstat, ctl, fb, fb_count, s)
-                      : launch_block<T, R, QW, false>(a, rowstat, ctl, fb, fb_count, s);
+  return a.tau == 0.0 ? launch_block<T, R, QW, true>(a, rowstat, ctl, fb, fb_count, s, rows)
+                      : launch_block<T, R, QW, false>(a, rowstat, ctl, fb, fb_count, s, rows);
 }
 
 // First pass over every row (path: 0 automatic, 1/2/4 column blocks with that many
@@ -1734,7 +1766,7 @@ int launch_window(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, const
 template <typename T, int QM>
 int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb1, int *fbw, int *fb2, int path,
                 cudaStream_t s) {
-  int rc;
+  int rc = SP2_OK;
   switch (path) {
     case 1: rc = launch_block_r<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 4: rc = launch_block_r<T, 4>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
@@ -1746,20 +1778,42 @@ int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
     case 7: rc = launch_block_compact<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 8: rc = launch_super_compact<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
     case 9: rc = launch_tile<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s); break;
-    default:  // automatic: the variant measured fastest on the 3D tight-binding products
-              // (FP64: column blocks, 4 warps per row, 2 in the compact form; FP32: one warp
-              // per row, two k steps per pass), in its compact form for the upper triangle
-              // of a symmetric product
-      if (a.up.tp && a.compact_level == 0)
-        rc = sizeof(T) == 8 ? launch_block_compact<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
-                            : launch_super_compact<T, 1>(a, rowstat, ctl, fb1, &ctl->n_fallback, s);
-      else if (a.up.tp && a.compact_level == 1)
-        rc = sizeof(T) == 8 ? launch_block_compact<T, 2>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
-                            : launch_super_compact<T, 2>(a, rowstat, ctl, fb1, &ctl->n_fallback, s);
-      else
-        rc = sizeof(T) == 8 ? launch_block_r<T, 4>(a, rowstat, ctl, fb1, &ctl->n_fallback, s)
-                            : launch_super_auto<T>(a, rowstat, ctl, fb1, &ctl->n_fallback, s);
-      break;
+    default: {  // automatic: the variant measured fastest on the 3D tight-binding products
+                // (FP64: column blocks, 4 warps per row, 2 in the compact form; FP32: one warp
+                // per row, two k steps per pass)
+      // The upper triangle of a symmetric product runs a cascade from compact_level on:
+      // the tight compact pass over every row, the loose one over the rows that outgrew
+      // it, the full-row pass over the rows that outgrew that; each pass is a first pass
+      // over a device-side list (fb1 and fbw alternate), so a long row costs one pass of
+      // its level instead of a CTA of the window bin.  Full rows: the full-row pass alone.
+      const int first = a.up.tp ? (a.compact_level < 0 ? 0 : (a.compact_level > 2 ? 2 : a.compact_level)) : 2;
+      int *bufs[2] = {fb1, fbw};
+      int cur = 0;
+      PassRows rows{};
+      for (int lv = first; lv <= 2 && rc == SP2_OK; ++lv) {
+        rows.level = lv;
+        int *out = bufs[cur];
+        int *out_count = lv == 0 ? &ctl->n_level1 : (lv == 1 ? &ctl->n_level2 : &ctl->n_fallback);
+        if (lv == 0)
+          rc = sizeof(T) == 8 ? launch_block_compact<T, 1>(a, rowstat, ctl, out, out_count, s, rows)
+                              : launch_super_compact<T, 1>(a, rowstat, ctl, out, out_count, s, rows);
+        else if (lv == 1)
+          rc = sizeof(T) == 8 ? launch_block_compact<T, 2>(a, rowstat, ctl, out, out_count, s, rows)
+                              : launch_super_compact<T, 2>(a, rowstat, ctl, out, out_count, s, rows);
+        else
+          rc = sizeof(T) == 8 ? launch_block_r<T, 4>(a, rowstat, ctl, out, out_count, s, rows)
+                              : launch_super_auto<T>(a, rowstat, ctl, out, out_count, s, rows);
+        rows.list = out;
+        rows.count = out_count;
+        cur ^= 1;
+      }
+      // the rows the full-row pass passed on: bins as below, from the list it wrote
+      if (rc == SP2_OK)
+        rc = launch_window<T>(a, rowstat, ctl, rows.list, &ctl->n_fallback, bufs[cur], &ctl->n_fallbackw, s);
+      if (rc == SP2_OK)
+        rc = launch_hash<T, 14, QM>(a, rowstat, ctl, bufs[cur], &ctl->n_fallbackw, fb2, &ctl->n_fallback2, s);
+      return rc;
+    }
   }
   // deferred rows: a dense window per CTA when the row's span fits it, then the 2^14-slot
   // table, then dense global rows

@@ -49,7 +49,8 @@ class sp2_options(ctypes.Structure):
                 ("n_fp64_tail", ctypes.c_int32), ("max_width", ctypes.c_int32), ("spgemm_path", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("switch_tol", ctypes.c_double), ("graph", ctypes.c_int32),
                 ("sizing", ctypes.c_int32), ("predictor", ctypes.POINTER(nnzpred_t)), ("stall_arm", ctypes.c_double),
-                ("symmetric", ctypes.c_int32), ("stall_ratio", ctypes.c_double)]
+                ("symmetric", ctypes.c_int32), ("stall_ratio", ctypes.c_double), ("route_rows", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("level_up_frac", ctypes.c_double)]
 
 
 class sp2_stats(ctypes.Structure):
@@ -61,7 +62,10 @@ class sp2_stats(ctypes.Structure):
                 ("time_ms", ctypes.c_double),
                 ("trX", ctypes.c_double * SP2_STATS_CAP), ("trX2", ctypes.c_double * SP2_STATS_CAP),
                 ("err", ctypes.c_double * SP2_STATS_CAP), ("branch", ctypes.c_int32 * SP2_STATS_CAP),
-                ("nnz_total", ctypes.c_int64 * SP2_STATS_CAP), ("max_row_nnz", ctypes.c_int32 * SP2_STATS_CAP)]
+                ("nnz_total", ctypes.c_int64 * SP2_STATS_CAP), ("max_row_nnz", ctypes.c_int32 * SP2_STATS_CAP),
+                ("rows_level1", ctypes.c_int32 * SP2_STATS_CAP), ("rows_level2", ctypes.c_int32 * SP2_STATS_CAP),
+                ("rows_deferred", ctypes.c_int32 * SP2_STATS_CAP), ("rows_routed", ctypes.c_int32 * SP2_STATS_CAP),
+                ("level", ctypes.c_int32 * SP2_STATS_CAP)]
 
 
 class sp2_step_info(ctypes.Structure):
@@ -70,7 +74,8 @@ class sp2_step_info(ctypes.Structure):
                 ("trXn2", ctypes.c_double), ("nnz_total", ctypes.c_int64), ("max_row_nnz", ctypes.c_int32),
                 ("required_width", ctypes.c_int32), ("spgemm_path", ctypes.c_int32),
                 ("rows_deferred", ctypes.c_int32), ("rows_dense", ctypes.c_int32),
-                ("spgemm_path_used", ctypes.c_int32), ("symmetric", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("spgemm_path_used", ctypes.c_int32), ("symmetric", ctypes.c_int32),
+                ("compact_level", ctypes.c_int32)]
 
 
 SP2_PROF_CLASSES = 5
@@ -407,6 +412,11 @@ def stats_dict(st):
         "trX": np.array(st.trX[:m]), "trX2": np.array(st.trX2[:m]), "err": np.array(st.err[:m]),
         "branch": ["X2" if b == 1 else "2X-X2" for b in st.branch[:min(it, SP2_STATS_CAP)]],
         "nnz_total": np.array(st.nnz_total[:m]), "max_row_nnz": np.array(st.max_row_nnz[:m]),
+        "rows_level1": np.array(st.rows_level1[:min(it, SP2_STATS_CAP)]),
+        "rows_level2": np.array(st.rows_level2[:min(it, SP2_STATS_CAP)]),
+        "rows_deferred": np.array(st.rows_deferred[:min(it, SP2_STATS_CAP)]),
+        "rows_routed": np.array(st.rows_routed[:min(it, SP2_STATS_CAP)]),
+        "level": np.array(st.level[:min(it, SP2_STATS_CAP)]),
     }
 
 
@@ -435,12 +445,15 @@ def sp2_x0(H, X0, tau, stream=None):
     return lo.value, hi.value
 
 
-def sp2_step(X, Xn, nocc, tau, traces=None, spgemm_path=0, stream=None, raise_on_overflow=True, symmetric=False):
+def sp2_step(X, Xn, nocc, tau, traces=None, spgemm_path=0, stream=None, raise_on_overflow=True, symmetric=False,
+             compact_level=0):
     """One SP2 iteration X -> Xn.  traces = (trX, trX2) of X if known.  symmetric: X is
-    exactly symmetric (the product's upper triangle is computed and mirrored).  Returns
+    exactly symmetric (the product's upper triangle is computed and mirrored);
+    compact_level: its automatic first pass (0 tight, 1 loose, 2 full rows).  Returns
     the sp2_step_info record (and the status when raise_on_overflow=False)."""
     info = sp2_step_info()
     info.symmetric = 1 if symmetric else 0
+    info.compact_level = compact_level
     if traces is not None:
         info.trX, info.trX2 = traces
         info.have_traces = 1

@@ -180,3 +180,44 @@ def test_sp2_symmetric_mode_is_bitwise_the_full_product(gpu):
     assert e.value.code == S.SP2E_ARG
     S.sp2_purify(S.Ellpack.from_numpy(H.idx, bad, H.nnz), n // 2, 1e-10, S.sp2_options_default(symmetric=0),
                  allow_notconv=True)
+
+
+def _same_D(Da, Db):
+    ia, va, na = Da.to_numpy()
+    ib, vb, nb = Db.to_numpy()
+    if not np.array_equal(na, nb):
+        return False
+    w = min(ia.shape[1], ib.shape[1])
+    live = np.arange(w)[None, :] < na[:, None]
+    return (np.array_equal(np.where(live, ia[:, :w], 0), np.where(live, ib[:, :w], 0)) and
+            np.array_equal(np.where(live, va[:, :w], 0).view(np.int64), np.where(live, vb[:, :w], 0).view(np.int64)))
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_first_pass_cascade_policies_agree_bitwise(gpu, prec):
+    """The cascade of first passes (tight compact, loose compact, full rows, bins) of the
+    symmetric products: with and without per-row route flags, and whatever level it
+    starts at, every row of every product gets the same sums in the same order, so the
+    runs agree bit for bit.  The per-update counts nest (each pass takes the rows the
+    previous one passed on), and on this 3D tight-binding run the tight pass does pass
+    rows on, so the cascade and the route flags are exercised."""
+    S = gpu
+    n = 32768
+    H = ell(I.tight_binding(n, seed=0, delta=10.0))
+    p = S.SP2_PREC_F64 if prec == "f64" else S.SP2_PREC_MIXED
+    runs = {}
+    for route in (0, 1):
+        for up in (0.002, 10.0):
+            opt = S.sp2_options_default(precision=p, route_rows=route, level_up_frac=up)
+            runs[(route, up)] = S.sp2_purify(dev(S, H), n // 2, 1e-10, opt)
+    D0, s0 = runs[(0, 10.0)]
+    for key, (D, st) in runs.items():
+        assert st["iterations"] == s0["iterations"] and st["branch"] == s0["branch"], key
+        assert np.array_equal(st["trX"], s0["trX"]) and np.array_equal(st["nnz_total"], s0["nnz_total"]), key
+        assert _same_D(D, D0), key
+        start0 = st["level"] == 0
+        assert np.all(st["rows_level2"][start0] <= st["rows_level1"][start0]), key
+        assert np.all(st["rows_deferred"] <= np.where(st["level"] <= 1, st["rows_level2"], n)), key
+    assert np.all(s0["level"] == 0) and s0["rows_level1"].sum() > 0
+    assert runs[(1, 10.0)][1]["rows_routed"].sum() > 0
+    assert runs[(0, 10.0)][1]["rows_routed"].sum() == 0

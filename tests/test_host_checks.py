@@ -48,11 +48,14 @@ BAD_OPTIONS = [
     (dict(max_iter=-1), "max_iter"),
     (dict(max_iter=100000), "max_iter"),
     (dict(n_fp64_tail=-1), "n_fp64_tail"),
+    (dict(route_rows=2), "route_rows"),
 ]
 
 
 @pytest.mark.parametrize("bad,word", BAD_OPTIONS + [(dict(sizing=3), "sizing"), (dict(sizing=2), "predictor"),
-                                                    (dict(switch_tol=-1.0), "switch_tol")])
+                                                    (dict(switch_tol=-1.0), "switch_tol"),
+                                                    (dict(level_up_frac=0.0), "level_up_frac"),
+                                                    (dict(level_up_frac=float("nan")), "level_up_frac")])
 def test_purify_rejects_bad_options(S, bad, word):
     keep = []
     H = fake_matrix(S, keep=keep)
@@ -144,6 +147,11 @@ def test_multiply_add_and_step_reject_bad_arguments(S):
     assert b"tau" in step(A, B, tau=float("nan"))
     assert b"nocc" in step(A, B, nocc=float("inf"))
     assert b"spgemm_path" in step(A, B, path=6)
+    info.compact_level = 3
+    assert b"compact_level" in step(A, B)
+    info.compact_level = -1
+    assert b"compact_level" in step(A, B)
+    info.compact_level = 0
 
 
 def test_multiply_block_rejects_bad_arguments(S):

@@ -235,7 +235,9 @@ int ellpack_gershgorin(const ellpack_t *H, double *emin, double *emax, void *str
 #define SP2_PROF_REDUCE 2   /* ordered trace/norm reductions */
 #define SP2_PROF_OTHER 3    /* everything else (X0, conversions, add, Gershgorin) */
 #define SP2_PROF_SYMM 4     /* symmetric products: lower-bound starts and the mirror of U */
-#define SP2_PROF_CLASSES 5
+#define SP2_PROF_CASCADE 5  /* the later first passes of a cascade (loose compact, full rows),
+                               over the rows the earlier passes passed on */
+#define SP2_PROF_CLASSES 6
 
 typedef struct sp2_profile {
   int64_t launches;                   /* kernels launched by the library while enabled */

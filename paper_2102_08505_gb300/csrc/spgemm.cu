@@ -1670,12 +1670,13 @@ int launch_block(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
   int grid = (int)(blocks < cap ? blocks : cap);
   if (grid < 1) grid = 1;
   const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
-  prof_begin(SP2_PROF_SPGEMM, s);
+  const int cls = rows.list ? SP2_PROF_CASCADE : SP2_PROF_SPGEMM;
+  prof_begin(cls, s);
   kern<<<grid, Geo::WARPS * 32, Geo::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
                                                (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv, a.up,
                                                rowstat, ctl, fb, fb_count, a.route, rows);
   note_launch();
-  prof_end(SP2_PROF_SPGEMM, s);
+  prof_end(cls, s);
   SP2_CUDA(cudaGetLastError());
   return SP2_OK;
 }
@@ -1700,12 +1701,13 @@ int launch_super(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *f
   int grid = (int)(blocks < cap ? blocks : cap);
   if (grid < 1) grid = 1;
   const EllView<T> add = a.Add ? view<T>(a.Add) : view<T>(a.A);
-  prof_begin(SP2_PROF_SPGEMM, s);
+  const int cls = rows.list ? SP2_PROF_CASCADE : SP2_PROF_SPGEMM;
+  prof_begin(cls, s);
   kern<<<grid, Geo::WARPS * 32, Geo::SMEM, s>>>(view<T>(a.A), view<T>(a.B), add, outview<T>(a.Out), (T)a.alpha,
                                                (T)a.beta, (T)a.tau, a.Add != nullptr && a.beta != 0.0, a.bv, a.up,
                                                rowstat, ctl, fb, fb_count, a.route, rows);
   note_launch();
-  prof_end(SP2_PROF_SPGEMM, s);
+  prof_end(cls, s);
   SP2_CUDA(cudaGetLastError());
   return SP2_OK;
 }

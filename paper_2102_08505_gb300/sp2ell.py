@@ -78,8 +78,8 @@ class sp2_step_info(ctypes.Structure):
                 ("compact_level", ctypes.c_int32)]
 
 
-SP2_PROF_CLASSES = 5
-PROF_NAMES = ("spgemm", "large_rows", "reduce", "other", "symmetry")
+SP2_PROF_CLASSES = 6
+PROF_NAMES = ("spgemm", "large_rows", "reduce", "other", "symmetry", "cascade")
 
 
 class sp2_profile(ctypes.Structure):

@@ -464,7 +464,8 @@ typedef struct sp2_options {
   int32_t route_rows;   /* automatic first pass (spgemm_path 0) of a symmetric product: a
                            cascade of passes, each over the rows that outgrew the previous
                            one's accumulator blocks: tight compact, loose compact, full rows,
-                           then the deferred-row bins.  1 = each row keeps a flag (on the
+                           then the deferred-row bins (below 2048 rows the full-row pass
+                           alone, one launch instead of three).  1 = each row keeps a flag (on the
                            device) with the level it last needed, and later updates start it
                            there (default); 0 = every row starts at the cascade's first level */
   int32_t pad;

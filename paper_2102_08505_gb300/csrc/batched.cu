@@ -740,7 +740,8 @@ extern "C" int sp2_purify_batched(const ellpack_t *H, const double *nocc, int32_
           o.nnz_total[t] = nz[(size_t)m * kCap + t];
           o.max_row_nnz[t] = mr[(size_t)m * kCap + t];
           // the products of the batch are shared: no per-matrix deferral counts
-          o.level[t] = t < o.iterations ? (opt.symmetric && opt.spgemm_path == 0 ? level : -1) : 0;
+          o.level[t] = t < o.iterations ? (opt.symmetric && opt.spgemm_path == 0 ? cascade_start(ntot, true, level) : -1)
+                                        : 0;
         }
       }
     }

@@ -368,13 +368,13 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
       st.rows_level2[it] = res.n_level2;
       st.rows_deferred[it] = res.n_fallback;
       st.rows_routed[it] = res.n_routed;
-      st.level[it] = (opt.symmetric && lg == 0) ? compact_level : -1;
+      st.level[it] = (opt.symmetric && lg == 0) ? cascade_start(n, true, compact_level) : -1;
     }
     // the cascade of first passes (automatic for symmetric products) starts at the tight
     // compact level; once its first pass passes on more than level_up_frac of the rows, the
     // cascade starts one level higher for the rest of the run.  Rows passed on for their
     // length alone (FP32, rows of X above 512 entries) are not counted
-    if (compact_level < 2 && opt.symmetric && lg == 0) {
+    if (compact_level < 2 && opt.symmetric && lg == 0 && n >= kCascadeMinRows) {
       const int passed = (compact_level == 0 ? res.n_level1 : res.n_level2) - res.n_heavy;
       if ((double)passed > opt.level_up_frac * (double)n) ++compact_level;
     }

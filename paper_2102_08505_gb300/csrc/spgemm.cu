@@ -1788,7 +1788,7 @@ int launch_bins(const MultiplyArgs &a, double2 *rowstat, SpgemmCtl *ctl, int *fb
       // it, the full-row pass over the rows that outgrew that; each pass is a first pass
       // over a device-side list (fb1 and fbw alternate), so a long row costs one pass of
       // its level instead of a CTA of the window bin.  Full rows: the full-row pass alone.
-      const int first = a.up.tp ? (a.compact_level < 0 ? 0 : (a.compact_level > 2 ? 2 : a.compact_level)) : 2;
+      const int first = cascade_start(a.A->n, a.up.tp != nullptr, a.compact_level);
       int *bufs[2] = {fb1, fbw};
       int cur = 0;
       PassRows rows{};

@@ -212,8 +212,8 @@ struct PassRows {
 // Symmetric products of fewer rows than this run the full-row first pass alone (cascade
 // level 2, one launch): there a product takes tens of microseconds, and the two list passes
 // of the cascade, launched whether or not any row reaches them, would cost more than the
-// faster compact passes save.  (Measured on the N = 1024 banded SP2: 8052 iterations/s with
-// one first-pass launch, 7312 with the three-pass cascade.)
+// faster compact passes save.  (Measured on the N = 1024 banded SP2 as one graph: 7312
+// iterations/s with three first-pass launches per product, about 7500 with one.)
 constexpr int kCascadeMinRows = 2048;
 inline int cascade_start(int n, bool upper, int compact_level) {
   if (!upper || n < kCascadeMinRows) return 2;

@@ -132,31 +132,39 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 // Sorts the L <= 32*E entries at ri/rv by column (distinct columns): keys (column, old
-// position) sorted in registers, then the values gathered from their old positions.
-template <typename T, int E>
+// position) sorted in registers, then the values gathered from their old positions.  K =
+// unsigned: the key packs the column above the PB = log2(32*E) position bits (columns below
+// 2^(32-PB): half the shuffles of the 64-bit key); K = unsigned long long: column << 32.
+template <typename K, int E>
+struct SortKey {
+  static constexpr int PB = sizeof(K) == 8 ? 32 : (E == 1 ? 5 : E == 2 ? 6 : E == 4 ? 7 : E == 8 ? 8 : 9);
+  static_assert(sizeof(K) == 8 || E <= 16, "32-bit keys for up to 16 entries per lane");
+};
+template <typename T, int E, typename K>
 __device__ __forceinline__ void warp_sort_row(int *ri, T *rv, int L, int lane) {
-  unsigned long long a[E];
+  constexpr int PB = SortKey<K, E>::PB;
+  K a[E];
 #pragma unroll
   for (int t = 0; t < E; ++t) {
     const int s = lane * E + t;
-    a[t] = s < L ? ((unsigned long long)(unsigned)ri[s] << 32) | (unsigned)s : ~0ull;
+    a[t] = s < L ? ((K)(unsigned)ri[s] << PB) | (K)(unsigned)s : ~(K)0;
   }
-  warp_bitonic<unsigned long long, E>(a, lane);
+  warp_bitonic<K, E>(a, lane);
   T v[E];
 #pragma unroll
-  for (int t = 0; t < E; ++t) v[t] = lane * E + t < L ? rv[(unsigned)a[t]] : T(0);
+  for (int t = 0; t < E; ++t)
+    v[t] = lane * E + t < L ? rv[(unsigned)(a[t] & (((K)1 << PB) - 1))] : T(0);
   __syncwarp();  // every old value is read before any is overwritten
 #pragma unroll
   for (int t = 0; t < E; ++t) {
     const int s = lane * E + t;
     if (s < L) {
-      ri[s] = (int)(a[t] >> 32);
+      ri[s] = (int)(a[t] >> PB);
       rv[s] = v[t];
     }
   }
   __syncwarp();
 }
-
 // rowstat[i] = (diagonal, sum of squares) of the full row i, one warp.
 template <typename T>
 __device__ __forceinline__ void row_stat_warp(const int *ri, const T *rv, int total, int i, int lane,
@@ -176,7 +184,9 @@ __device__ __forceinline__ void row_stat_warp(const int *ri, const T *rv, int to
 // Sorts row i's lower part (positions 0 .. L-1) by column and records rowstat[i].  One
 // warp per row, in registers for L <= kSortWarpMax; longer lower parts are left for the
 // passes over the flagged rows (list `longs`).
-template <typename T>
+// K: the sort key (unsigned when every column is below 2^24, the 8 position bits of 256
+// entries leaving 24 for the column; else unsigned long long), chosen at launch.
+template <typename T, typename K>
 __global__ void __launch_bounds__(kSymThreads) mirror_sort_kernel(EllOut<T> Out, BatchView bv,
                                                                  const int *__restrict__ cnt,
                                                                  double2 *__restrict__ rowstat,
@@ -198,12 +208,12 @@ __global__ void __launch_bounds__(kSymThreads) mirror_sort_kernel(EllOut<T> Out,
       continue;
     }
     if (L > 128) {
-      warp_sort_row<T, 8>(ri, rv, L, lane);
+      warp_sort_row<T, 8, K>(ri, rv, L, lane);
     } else if (L > 32) {
-      if (L > 64) warp_sort_row<T, 4>(ri, rv, L, lane);
-      else warp_sort_row<T, 2>(ri, rv, L, lane);
+      if (L > 64) warp_sort_row<T, 4, K>(ri, rv, L, lane);
+      else warp_sort_row<T, 2, K>(ri, rv, L, lane);
     } else if (L > 1) {
-      warp_sort_row<T, 1>(ri, rv, L, lane);
+      warp_sort_row<T, 1, K>(ri, rv, L, lane);
     }
     row_stat_warp(ri, rv, total, i, lane, rowstat);
   }
@@ -225,7 +235,7 @@ __global__ void __launch_bounds__(kSymThreads) mirror_sort_mid_kernel(EllOut<T> 
     if (L > kSortMidMax) continue;
     int *ri = Out.idx + (size_t)i * Out.w;
     T *rv = Out.val + (size_t)i * Out.w;
-    warp_sort_row<T, 16>(ri, rv, L, lane);
+    warp_sort_row<T, 16, unsigned long long>(ri, rv, L, lane);
     row_stat_warp(ri, rv, Out.nnz[i], i, lane, rowstat);
   }
 }
@@ -339,7 +349,12 @@ static int mirror_t(const ellpack_t *U, ellpack_t *Out, const BatchView &bv, int
   const int g = grid_rows_sym(n);
   mirror_count_kernel<T><<<g, kSymThreads, 0, s>>>(view<T>(U), bv, cnt);
   mirror_place_kernel<T><<<g, kSymThreads, 0, s>>>(view<T>(U), outview<T>(Out), bv, cnt, cursor, ctl);
-  mirror_sort_kernel<T><<<g, kSymThreads, 0, s>>>(outview<T>(Out), bv, cnt, rowstat, longs, nlong);
+  static_assert(kSortWarpMax <= 256, "the 32-bit key holds 8 position bits");
+  if (Out->n < (1 << 24))
+    mirror_sort_kernel<T, unsigned><<<g, kSymThreads, 0, s>>>(outview<T>(Out), bv, cnt, rowstat, longs, nlong);
+  else
+    mirror_sort_kernel<T, unsigned long long>
+        <<<g, kSymThreads, 0, s>>>(outview<T>(Out), bv, cnt, rowstat, longs, nlong);
   note_launch();
   note_launch();
   note_launch();

@@ -137,3 +137,26 @@ def test_batched_symmetric_mode_is_bitwise_the_full_product(gpu):
             assert np.array_equal(na, nb)
             live = np.arange(ia.shape[1])[None, :] < na[:, None]
             assert np.array_equal(np.where(live, va, 0), np.where(live, vb[:, :ia.shape[1]], 0))
+
+
+def test_batched_route_flags_agree_bitwise(gpu):
+    """The captured loop runs the first-pass cascade from the tight compact level; with and
+    without per-row route flags every matrix gets the same iterations and the same D bit for
+    bit, and the stacked rows (above 2048) do start at the tight level."""
+    S = gpu
+    sizes = [4096, 700, 2600, 1500]
+    Hs = [S.Ellpack.from_numpy(*I.tight_binding(m, seed=80 + k, delta=10.0, periodic=False))
+          for k, m in enumerate(sizes)]
+    noccs = [(m + 1) // 2 for m in sizes]
+    for prec in (S.SP2_PREC_F64, S.SP2_PREC_MIXED):
+        Da, sa = S.sp2_purify_batched(Hs, noccs, 1e-10, S.sp2_options_default(precision=prec, route_rows=1))
+        Db, sb = S.sp2_purify_batched(Hs, noccs, 1e-10, S.sp2_options_default(precision=prec, route_rows=0))
+        for m in range(len(sizes)):
+            assert sa[m]["iterations"] == sb[m]["iterations"] and sa[m]["branch"] == sb[m]["branch"]
+            assert np.all(sa[m]["level"] == 0)
+            ia, va, na = Da[m].to_numpy()
+            ib, vb, nb = Db[m].to_numpy()
+            assert np.array_equal(na, nb)
+            live = np.arange(ia.shape[1])[None, :] < na[:, None]
+            assert np.array_equal(np.where(live, ia, 0), np.where(live, ib[:, :ia.shape[1]], 0))
+            assert np.array_equal(np.where(live, va, 0).view(np.int64), np.where(live, vb[:, :ia.shape[1]], 0).view(np.int64))

@@ -402,3 +402,29 @@ def test_window_bin_banded_long_rows(gpu, dtype):
     rows = np.unique(np.concatenate([[0, 1, band, n // 2, n - 1], np.random.default_rng(8).choice(n, 60, replace=False)]))
     compare_spgemm(full.to_numpy(), Hq, Hq, Hq, -1.0 if up else 1.0, 2.0 if up else 0.0, 1e-5, fp32=dt == S.SP2_F32,
                    rows=rows)
+
+
+def test_cascade_levels_of_the_symmetric_step(gpu):
+    """A banded X whose product rows span about 1920 columns above the diagonal: more 8-column
+    blocks than the tight compact pass holds, fewer than the loose one.  Started at each level
+    (sp2_step compact_level 0, 1, 2) the cascade gives the same bits as the full-row product,
+    no row reaches the deferred-row bins, and sampled rows match the oracle (tau = 0: every
+    structural entry kept)."""
+    S = gpu
+    n, band = 3000, 960
+    X = ell(I.banded(n, band=band, seed=21, delta=10.0))
+    dX = dev(S, X)
+    rc, info = S.sp2_step(dX, S.Ellpack.empty(n, 32), n / 2, 0.0, raise_on_overflow=False)
+    w = ((info.required_width + 31) // 32) * 32
+    full = S.Ellpack.empty(n, w)
+    info_f = S.sp2_step(dX, full, n / 2, 0.0)
+    ref = full.to_numpy()
+    for level in (0, 1, 2):
+        out = S.Ellpack.empty(n, w)
+        info_l = S.sp2_step(dX, out, n / 2, 0.0, symmetric=True, compact_level=level)
+        assert info_l.rows_deferred == 0, level
+        assert rows_equal(out.to_numpy(), ref), level
+        assert (info_l.trXn, info_l.nnz_total) == (info_f.trXn, info_f.nnz_total)
+    up = info_f.branch == 2
+    rows = np.array([0, 1, 959, 960, 1500, 2040, 2999])
+    compare_spgemm(ref, X, X, X, -1.0 if up else 1.0, 2.0 if up else 0.0, 0.0, rows=rows)

@@ -220,8 +220,9 @@ __global__ void __launch_bounds__(kSymThreads) mirror_sort_kernel(EllOut<T> Out,
 }
 
 // Flagged rows with kSortWarpMax < L <= kSortMidMax: one warp per row, 16 keys per lane
-// (a kernel of its own so that the registers this takes do not limit the common pass).
-template <typename T>
+// (a kernel of its own so that the registers this takes do not limit the common pass).  K as
+// in mirror_sort_kernel, with 9 position bits (columns below 2^23 for the 32-bit key).
+template <typename T, typename K>
 __global__ void __launch_bounds__(kSymThreads) mirror_sort_mid_kernel(EllOut<T> Out, const int *__restrict__ cnt,
                                                                      double2 *__restrict__ rowstat,
                                                                      const int *__restrict__ longs,
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(kSymThreads) mirror_sort_mid_kernel(EllOut<T> 
     if (L > kSortMidMax) continue;
     int *ri = Out.idx + (size_t)i * Out.w;
     T *rv = Out.val + (size_t)i * Out.w;
-    warp_sort_row<T, 16, unsigned long long>(ri, rv, L, lane);
+    warp_sort_row<T, 16, K>(ri, rv, L, lane);
     row_stat_warp(ri, rv, Out.nnz[i], i, lane, rowstat);
   }
 }
@@ -358,7 +359,13 @@ static int mirror_t(const ellpack_t *U, ellpack_t *Out, const BatchView &bv, int
   note_launch();
   note_launch();
   note_launch();
-  mirror_sort_mid_kernel<T><<<num_sms() * 2, kSymThreads, 0, s>>>(outview<T>(Out), cnt, rowstat, longs, nlong);
+  static_assert(kSortMidMax <= 512, "the 32-bit key holds 9 position bits");
+  if (Out->n < (1 << 23))
+    mirror_sort_mid_kernel<T, unsigned>
+        <<<num_sms() * 2, kSymThreads, 0, s>>>(outview<T>(Out), cnt, rowstat, longs, nlong);
+  else
+    mirror_sort_mid_kernel<T, unsigned long long>
+        <<<num_sms() * 2, kSymThreads, 0, s>>>(outview<T>(Out), cnt, rowstat, longs, nlong);
   note_launch();
   constexpr int smem = kSortCtaMax * (int)(sizeof(int) + sizeof(T));
   static DeviceOnce once;

@@ -551,8 +551,9 @@ def time_to_solution(a, dev_id, reps=3):
     warm-up, with the SM clocks sampled around it and the distance of every result to the
     FP64 GPU run of the same input (||D - D_FP64||_F / sqrt(N), same tau):
       C1: banded N = 1024, band 16 (the gapped variant: A/B onsite splitting 10), FP64,
-          iterations per second host-stepped (sp2_purify) and as one captured graph
-          (sp2_purify_batched of one matrix); the literal gapless configuration beside it;
+          iterations per second with the whole loop in one cooperative launch (sp2_purify),
+          host-stepped (small_path = 0) and as one captured graph (sp2_purify_batched of one
+          matrix); the literal gapless configuration beside it;
       C3: gapped 3D tight-binding N = 131072, FP64 against mixed precision;
       C4: 256 gapped open clusters, N log-uniform in [512, 8192]: one graph launch in mixed
           precision and in FP64, against FP64 purified one by one;
@@ -580,15 +581,20 @@ def time_to_solution(a, dev_id, reps=3):
         r = {}
         n, tau = 1024, 1e-5
         Hg = S.Ellpack.from_numpy(*I.banded(n, band=16, seed=1, delta=10.0, width=64))
-        opt = S.sp2_options_default(tau=tau)
-        t_host, (D, st), _ = _median_runs(lambda: S.sp2_purify(Hg, n / 2, tol, opt), reps * 3)
+        opt = S.sp2_options_default(tau=tau)  # n <= 2048: the whole loop in one cooperative launch
+        t_one, (D, st), _ = _median_runs(lambda: S.sp2_purify(Hg, n / 2, tol, opt), reps * 3)
+        opth = S.sp2_options_default(tau=tau, small_path=0)
+        t_host, (Dh, sh), _ = _median_runs(lambda: S.sp2_purify(Hg, n / 2, tol, opth), reps * 3)
         optg = S.sp2_options_default(tau=tau, graph=1)
         t_graph, (Dg, sg), _ = _median_runs(lambda: S.sp2_purify_batched([Hg], [n // 2], tol, optg), reps * 3)
         r["gapped_delta10"] = {
             "iterations": st["iterations"], "status": st["status"], "final_err": float(st["err"][-1]),
-            "host_stepped": {"time_s": t_host, "iters_per_s": st["iterations"] / t_host},
+            "one_launch": {"time_s": t_one, "iters_per_s": st["iterations"] / t_one,
+                           "api": "sp2_purify (the loop as one cooperative kernel)"},
+            "host_stepped": {"time_s": t_host, "iters_per_s": sh["iterations"] / t_host,
+                             "iterations": sh["iterations"], "dD_vs_one_launch": dD(Dh, D, n)},
             "graph": {"time_s": t_graph, "iters_per_s": sg[0]["iterations"] / t_graph,
-                      "iterations": sg[0]["iterations"], "dD_vs_host_stepped": dD(Dg[0], D, n)},
+                      "iterations": sg[0]["iterations"], "dD_vs_one_launch": dD(Dg[0], D, n)},
             "max_row_nnz": int(max(st["max_row_nnz"]))}
         H = S.Ellpack.from_numpy(*I.banded(n, band=16, seed=1, width=64))
         t_lit, (Dl, sl), _ = _median_runs(lambda: S.sp2_purify(H, n / 2, tol, opt, allow_notconv=True), reps)

@@ -468,7 +468,11 @@ typedef struct sp2_options {
                            alone, one launch instead of three).  1 = each row keeps a flag (on the
                            device) with the level it last needed, and later updates start it
                            there (default); 0 = every row starts at the cascade's first level */
-  int32_t pad;
+  int32_t small_path;   /* 1 (default): FP64 runs (precision F64, spgemm_path 0, sizing 0, no
+                           width cap below n) of at most 2048 rows take the whole loop in one
+                           cooperative launch, each row built in a dense shared-memory
+                           accumulator: the same rows bit for bit, traces added in another
+                           order; 0: always the host-stepped loop */
   double level_up_frac; /* the cascade starts at the tight compact level (fewest blocks per
                            row, most rows per SM); once its first pass passes on more than
                            this fraction of the rows in an update, it starts one level higher
@@ -502,7 +506,11 @@ typedef struct sp2_stats {
                                            the cascade's first pass unstarted */
   int32_t level[SP2_STATS_CAP];         /* per update: the level the cascade of a symmetric
                                            product started at (0 tight, 1 loose, 2 full
-                                           rows); -1 for other first passes */
+                                           rows); -1 for other first passes (and for the
+                                           updates of the one-launch loop) */
+  int32_t small_iterations;             /* updates made by the one-launch loop (small_path);
+                                           the host-stepped loop made the rest */
+  int32_t pad;
 } sp2_stats;
 
 /*

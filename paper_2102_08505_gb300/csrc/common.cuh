@@ -220,6 +220,17 @@ inline int cascade_start(int n, bool upper, int compact_level) {
   return compact_level < 0 ? 0 : (compact_level > 2 ? 2 : compact_level);
 }
 
+// The SP2 loop of a small FP64 matrix in one cooperative launch (small.cu): X0 (n rows,
+// width >= n) in, Y (n rows, width >= n) as the second buffer; the last iterate is in X0 or Y
+// (*final_buf 0 or 1).  Fills the per-iterate records of *stats up to *iterations.  *status
+// as sp2_stats.status, 3 for a non-finite trace, or 4 when an iterate grew a row too long for
+// the one-launch loop: the host-stepped loop then continues from iterate *iterations (whose
+// traces are recorded, its branch not yet taken) with the stall rule's *armed state.
+// Errors: SP2E_TIMEOUT (a grid barrier waited too long), SP2E_CUDA.
+constexpr int kSmallMaxN = 2048;
+int small_purify(ellpack_t *X0, ellpack_t *Y, double nocc, double tol, const sp2_options &opt, int *iterations,
+                 int *status, int *final_buf, int *final_maxr, int *armed, sp2_stats *stats, cudaStream_t s);
+
 struct Upper {
   const int *tp = nullptr;
   const int *tpd = nullptr;

@@ -80,6 +80,7 @@ extern "C" void sp2_options_default(sp2_options *o) {
   o->stall_ratio = 1.0;
   o->symmetric = 1;
   o->route_rows = 1;
+  o->small_path = 1;
   o->level_up_frac = 1.0;
 }
 
@@ -112,6 +113,7 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
   if (!(opt.stall_ratio > 0.0 && opt.stall_ratio <= 1.0))
     return fail(SP2E_ARG, "sp2_purify: stall_ratio must be in (0, 1]");
   if (opt.route_rows != 0 && opt.route_rows != 1) return fail(SP2E_ARG, "sp2_purify: route_rows must be 0 or 1");
+  if (opt.small_path != 0 && opt.small_path != 1) return fail(SP2E_ARG, "sp2_purify: small_path must be 0 or 1");
   if (!(opt.level_up_frac > 0.0) || !isfinite(opt.level_up_frac))
     return fail(SP2E_ARG, "sp2_purify: level_up_frac must be finite and > 0");
   if (opt.sizing == 2 && (!opt.predictor || !opt.predictor->params))
@@ -187,29 +189,86 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
                                        "use symmetric = 0", defects);
   }
 
-  // a2: X0 in FP64
-  SP2_TRY(ellpack_create(n, H64->width + 1, SP2_F64, s, &b.X));
-  SP2_TRY(x0_async(H64, b.bounds, opt.tau, &b.X, s));
-
-  const bool mixed = opt.precision == SP2_PREC_MIXED;
-  if (mixed) {
-    SP2_TRY(ellpack_create(n, b.X.width, SP2_F32, s, &b.Y));
-    SP2_TRY(convert_async(&b.X, &b.Y, s));
-    ellpack_t t = b.X; b.X = b.Y; b.Y = t;  // X <- F32 copy, Y <- spare F64 buffer
+  // a2..a7 for a small FP64 matrix: X0 here, then the loop in one cooperative launch, for as
+  // long as the iterates' rows stay short; the host-stepped loop below takes over after that
+  bool handed = false;
+  int it0 = 0;
+  bool armed0 = false;
+  StepResult res{};
+  if (opt.small_path && opt.precision == SP2_PREC_F64 && opt.spgemm_path == 0 && opt.sizing == 0 &&
+      n <= kSmallMaxN && max_w >= n) {
+    const int w = n > H64->width + 1 ? n : H64->width + 1;  // every product row fits
+    SP2_TRY(ellpack_create(n, w, SP2_F64, s, &b.X));
+    SP2_TRY(x0_async(H64, b.bounds, opt.tau, &b.X, s));
+    SP2_TRY(ellpack_create(n, w, SP2_F64, s, &b.Y));
+    int iters = 0, status = 0, fbuf = 0, fmax = 0, arm = 0;
+    const int rc = small_purify(&b.X, &b.Y, nocc, tol, opt, &iters, &status, &fbuf, &fmax, &arm, &st, s);
+    if (status == 4 && rc == SP2_OK) {  // the host-stepped loop continues from iterate iters
+      if (fbuf) { ellpack_t t = b.X; b.X = b.Y; b.Y = t; }
+      handed = true;
+      it0 = iters;
+      armed0 = arm != 0;
+      res.tr = st.trX[iters];
+      res.fro = st.trX2[iters];
+      res.nnz_total = st.nnz_total[iters];
+      res.max_nnz = st.max_row_nnz[iters];
+      res.max_count = res.max_nnz;
+      st.small_iterations = iters;
+    } else {
+      st.iterations = iters;
+      st.small_iterations = iters;
+      st.status = status == 3 ? 0 : status;
+      st.width_max = w;
+      st.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (stats) *stats = st;
+      if (rc != SP2_OK) return rc;
+      if (status == 3) return fail(SP2E_NONFINITE, "sp2_purify: non-finite trace at iteration %d", iters);
+      // result: a caller-owned F64 matrix as wide as its longest row
+      ellpack_t *R = fbuf ? &b.Y : &b.X;
+      int dw = round_up(fmax > 1 ? fmax : 1, 32);
+      if (dw > w) dw = w;
+      ellpack_t out{};
+      SP2_TRY(ellpack_create(n, dw, SP2_F64, s, &out));
+      int e = convert_async(R, &out, s);
+      if (e == SP2_OK) {
+        const cudaError_t ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) e = cuda_fail(ce, "sp2_purify", __FILE__, __LINE__);
+      }
+      if (e != SP2_OK) {
+        ellpack_destroy(&out, s);
+        return e;
+      }
+      *D = out;
+      st.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (stats) *stats = st;
+      if (status == 2) return fail(SP2E_NOTCONV, "sp2_purify: max_iter=%d reached (err %.3e)", opt.max_iter,
+                                   st.err[iters < SP2_STATS_CAP ? iters : SP2_STATS_CAP - 1]);
+      return SP2_OK;
+    }
   }
 
-  // a3 for X0: traces from a pass over the stored matrix
-  SP2_TRY(rowstat_async(&b.X, b.rowstat, s));
-  launch_reduce_rows(b.rowstat, b.X.nnz, n, nullptr, b.dres, s);
-  SP2_CUDA(cudaGetLastError());
-  StepResult res;
-  SP2_TRY(read_result(b, &res));
+  const bool mixed = opt.precision == SP2_PREC_MIXED;
+  if (!handed) {
+    // a2: X0 in FP64
+    SP2_TRY(ellpack_create(n, H64->width + 1, SP2_F64, s, &b.X));
+    SP2_TRY(x0_async(H64, b.bounds, opt.tau, &b.X, s));
+    if (mixed) {
+      SP2_TRY(ellpack_create(n, b.X.width, SP2_F32, s, &b.Y));
+      SP2_TRY(convert_async(&b.X, &b.Y, s));
+      ellpack_t t = b.X; b.X = b.Y; b.Y = t;  // X <- F32 copy, Y <- spare F64 buffer
+    }
+    // a3 for X0: traces from a pass over the stored matrix
+    SP2_TRY(rowstat_async(&b.X, b.rowstat, s));
+    launch_reduce_rows(b.rowstat, b.X.nnz, n, nullptr, b.dres, s);
+    SP2_CUDA(cudaGetLastError());
+    SP2_TRY(read_result(b, &res));
+  }
 
   enum Phase { MAIN, TAIL } phase = MAIN;
   bool fp32 = mixed;
   int tail_left = opt.n_fp64_tail;
-  bool armed = false;
-  int it = 0;
+  bool armed = armed0;
+  int it = it0;
   // the record so far reaches the caller on every return from here, errors included
   struct StatsOnExit {
     sp2_stats *dst;

@@ -50,7 +50,7 @@ class sp2_options(ctypes.Structure):
                 ("tau", ctypes.c_double), ("switch_tol", ctypes.c_double), ("graph", ctypes.c_int32),
                 ("sizing", ctypes.c_int32), ("predictor", ctypes.POINTER(nnzpred_t)), ("stall_arm", ctypes.c_double),
                 ("symmetric", ctypes.c_int32), ("stall_ratio", ctypes.c_double), ("route_rows", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("level_up_frac", ctypes.c_double)]
+                ("small_path", ctypes.c_int32), ("level_up_frac", ctypes.c_double)]
 
 
 class sp2_stats(ctypes.Structure):
@@ -65,7 +65,8 @@ class sp2_stats(ctypes.Structure):
                 ("nnz_total", ctypes.c_int64 * SP2_STATS_CAP), ("max_row_nnz", ctypes.c_int32 * SP2_STATS_CAP),
                 ("rows_level1", ctypes.c_int32 * SP2_STATS_CAP), ("rows_level2", ctypes.c_int32 * SP2_STATS_CAP),
                 ("rows_deferred", ctypes.c_int32 * SP2_STATS_CAP), ("rows_routed", ctypes.c_int32 * SP2_STATS_CAP),
-                ("level", ctypes.c_int32 * SP2_STATS_CAP)]
+                ("level", ctypes.c_int32 * SP2_STATS_CAP), ("small_iterations", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class sp2_step_info(ctypes.Structure):
@@ -417,6 +418,7 @@ def stats_dict(st):
         "rows_deferred": np.array(st.rows_deferred[:min(it, SP2_STATS_CAP)]),
         "rows_routed": np.array(st.rows_routed[:min(it, SP2_STATS_CAP)]),
         "level": np.array(st.level[:min(it, SP2_STATS_CAP)]),
+        "small_iterations": st.small_iterations,
     }
 
 

@@ -59,7 +59,7 @@ def test_options_defaults(libpath):
     o = sp2ell.sp2_options_default()
     assert (o.precision, o.max_iter, o.stall_rule, o.n_fp64_tail, o.tau) == (0, 100, 1, 2, 1e-5)
     assert (o.stall_arm, o.stall_ratio, o.symmetric) == (0.1, 1.0, 1)
-    assert (o.route_rows, o.level_up_frac) == (1, 1.0)
+    assert (o.route_rows, o.small_path, o.level_up_frac) == (1, 1, 1.0)
 
 
 def test_binding_structs_match_the_header(tmp_path):

@@ -221,3 +221,51 @@ def test_first_pass_cascade_policies_agree_bitwise(gpu, prec):
     assert np.all(s0["level"] == 0) and s0["rows_level1"].sum() > 0
     assert runs[(1, 10.0)][1]["rows_routed"].sum() > 0
     assert runs[(0, 10.0)][1]["rows_routed"].sum() == 0
+
+
+SMALL_CASES = [
+    # name, matrix, nocc, tau, tol
+    ("banded gapped n=1024", lambda: I.banded(1024, band=16, seed=1, delta=10.0, width=64), 512, 1e-5, 1e-10),
+    ("banded gapless n=1024 (stall rule)", lambda: I.banded(1024, band=16, seed=1, width=64), 512, 1e-5, 1e-10),
+    ("banded tau=0 n=300", lambda: I.banded(300, band=5, seed=3, delta=10.0), 150, 0.0, 1e-10),
+    ("open cluster n=1500", lambda: I.tight_binding(1500, seed=31, delta=10.0, periodic=False), 750, 1e-5, 1e-10),
+    ("3D gapped n=2048 (the largest)", lambda: I.tight_binding(2048, seed=32, delta=10.0), 1024, 1e-5, 1e-10),
+    ("n=3", lambda: I.banded(3, band=1, seed=4, delta=10.0), 1.5, 0.0, 1e-12),
+]
+
+
+@pytest.mark.parametrize("case", SMALL_CASES, ids=[c[0] for c in SMALL_CASES])
+def test_small_path_is_the_host_stepped_loop(gpu, case):
+    """sp2_purify of an FP64 matrix of at most 2048 rows runs the whole loop in one
+    cooperative launch (small_path, the default).  Against the host-stepped loop
+    (small_path = 0): the same iterations, branches and stop status, the same density
+    matrix bit for bit (every product row is the same sum in the same order), and traces
+    equal up to their summation order."""
+    S = gpu
+    name, make, nocc, tau, tol = case
+    H = dev(S, ell(make()))
+    Da, sa = S.sp2_purify(H, nocc, tol, S.sp2_options_default(tau=tau), allow_notconv=True)
+    Db, sb = S.sp2_purify(H, nocc, tol, S.sp2_options_default(tau=tau, small_path=0), allow_notconv=True)
+    assert sa["iterations"] == sb["iterations"] and sa["branch"] == sb["branch"] and sa["status"] == sb["status"]
+    assert np.array_equal(sa["nnz_total"], sb["nnz_total"]) and np.array_equal(sa["max_row_nnz"], sb["max_row_nnz"])
+    assert np.allclose(sa["trX"], sb["trX"], rtol=1e-13, atol=1e-12)
+    assert np.allclose(sa["trX2"], sb["trX2"], rtol=1e-13, atol=1e-12)
+    assert _same_D(Da, Db)
+    k = sa["small_iterations"]
+    assert k > 0 and np.all(sa["level"][:k] == -1)
+
+
+def test_small_path_hands_long_rows_to_the_host_stepped_loop(gpu):
+    """The gapless banded run grows rows past 64 entries: the one-launch loop hands the
+    iterate to the host-stepped loop, which finishes the run; the result is the host-stepped
+    loop's run bit for bit, with the iterations split between the two."""
+    S = gpu
+    n = 1024
+    H = dev(S, ell(I.banded(n, band=16, seed=1, width=64)))
+    Da, sa = S.sp2_purify(H, n / 2, 1e-10, S.sp2_options_default(tau=1e-5), allow_notconv=True)
+    Db, sb = S.sp2_purify(H, n / 2, 1e-10, S.sp2_options_default(tau=1e-5, small_path=0), allow_notconv=True)
+    assert 0 < sa["small_iterations"] < sa["iterations"] and sb["small_iterations"] == 0
+    assert sa["max_row_nnz"][sa["small_iterations"]] > 64 and max(sa["max_row_nnz"][:sa["small_iterations"]]) <= 64
+    assert sa["iterations"] == sb["iterations"] and sa["branch"] == sb["branch"] and sa["status"] == sb["status"]
+    assert np.allclose(sa["trX"], sb["trX"], rtol=1e-13, atol=1e-12)
+    assert _same_D(Da, Db)

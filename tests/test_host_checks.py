@@ -50,9 +50,10 @@ BAD_OPTIONS = [
     (dict(n_fp64_tail=-1), "n_fp64_tail"),
     (dict(route_rows=2), "route_rows"),
 ]
+PURIFY_ONLY_BAD = [(dict(small_path=2), "small_path")]
 
 
-@pytest.mark.parametrize("bad,word", BAD_OPTIONS + [(dict(sizing=3), "sizing"), (dict(sizing=2), "predictor"),
+@pytest.mark.parametrize("bad,word", BAD_OPTIONS + PURIFY_ONLY_BAD + [(dict(sizing=3), "sizing"), (dict(sizing=2), "predictor"),
                                                     (dict(switch_tol=-1.0), "switch_tol"),
                                                     (dict(level_up_frac=0.0), "level_up_frac"),
                                                     (dict(level_up_frac=float("nan")), "level_up_frac")])

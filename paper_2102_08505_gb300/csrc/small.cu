@@ -25,6 +25,7 @@ namespace {
 
 constexpr int kSmallWarps = 8;
 constexpr int kSmallThreads = kSmallWarps * 32;
+constexpr int kSmallMaxBlocks = (kSmallMaxN + kSmallWarps - 1) / kSmallWarps;  // the grid never exceeds it
 constexpr long long kBarrierSpins = 1ll << 24;  // with 64 ns pauses: about one second
 // Iterates with a row longer than this continue in the host-stepped loop: one warp per row
 // holds the first 64 entries of three source rows in registers, and longer rows run into
@@ -102,6 +103,9 @@ __global__ void __launch_bounds__(kSmallThreads) sp2_small_kernel(SmallArgs p) {
   __shared__ int s_max[kSmallWarps];
   __shared__ double s_trX, s_trX2;
   __shared__ int s_stop, s_up;
+  __shared__ double s_ptr[kSmallMaxBlocks], s_pfr[kSmallMaxBlocks];
+  __shared__ long long s_pnz[kSmallMaxBlocks];
+  __shared__ int s_pmx[kSmallMaxBlocks];
   const int gw = blockIdx.x * kSmallWarps + wid, tw = gridDim.x * kSmallWarps;
   const unsigned lt = lanemask_lt();
   const long long tb = mag_bits(p.tau);
@@ -129,16 +133,24 @@ __global__ void __launch_bounds__(kSmallThreads) sp2_small_kernel(SmallArgs p) {
       p.part[blockIdx.x] = q;
     }
     if (!grid_barrier(st)) return false;
+    // every block's partials into shared memory at once (L2 reads, the L1 may be stale),
+    // then added in block order by one thread
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+      s_ptr[b] = __ldcg(&p.part[b].tr);
+      s_pfr[b] = __ldcg(&p.part[b].fro);
+      s_pnz[b] = __ldcg(&p.part[b].nnz);
+      s_pmx[b] = __ldcg(&p.part[b].maxr);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
       double tr = 0.0, fro = 0.0;
       long long nz = 0;
       int mx = 0;
       for (int b = 0; b < (int)gridDim.x; ++b) {
-        const volatile SmallPart *q = p.part + b;
-        tr += q->tr;
-        fro += q->fro;
-        nz += q->nnz;
-        mx = max(mx, q->maxr);
+        tr += s_ptr[b];
+        fro += s_pfr[b];
+        nz += s_pnz[b];
+        mx = max(mx, s_pmx[b]);
       }
       s_trX = tr;
       s_trX2 = fro;

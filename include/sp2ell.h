@@ -581,8 +581,9 @@ void sp2_options_default(sp2_options *opt);
  * (release with ellpack_destroy) and *stats (optional) the per-iteration record.
  * Returns SP2_OK, or SP2E_NOTCONV with D still set when max_iter was reached.
  * Errors: SP2E_ARG, SP2E_NOMEM, SP2E_CUDA, SP2E_OVERFLOW (max_width too small),
- * SP2E_NONFINITE; after an error *stats holds the iterations recorded before it.
- * Synchronises `stream`.
+ * SP2E_NONFINITE, SP2E_TIMEOUT (small_path: a grid barrier of the one-launch loop saw no
+ * progress for about a second); after an error *stats holds the iterations recorded before
+ * it.  Synchronises `stream` (with small_path, `stream` must not be under graph capture).
  */
 int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2_options *opt, ellpack_t *D,
                sp2_stats *stats, void *stream);

@@ -26,7 +26,7 @@ namespace {
 constexpr int kSmallWarps = 8;
 constexpr int kSmallThreads = kSmallWarps * 32;
 constexpr int kSmallMaxBlocks = (kSmallMaxN + kSmallWarps - 1) / kSmallWarps;  // the grid never exceeds it
-constexpr long long kBarrierSpins = 1ll << 24;  // with 64 ns pauses: about one second
+constexpr long long kBarrierSpins = 1ll << 21;  // a pause and an L2 read each: about a second
 // Iterates with a row longer than this continue in the host-stepped loop: one warp per row
 // holds the first 64 entries of three source rows in registers, and longer rows run into
 // dependent loads and the narrow FP64 pipe of one SM, where the column-block passes over all

@@ -223,22 +223,12 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
       if (stats) *stats = st;
       if (rc != SP2_OK) return rc;
       if (status == 3) return fail(SP2E_NONFINITE, "sp2_purify: non-finite trace at iteration %d", iters);
-      // result: a caller-owned F64 matrix as wide as its longest row
+      // result: the buffer holding the last iterate (width max(n, width of H + 1)) goes to the
+      // caller as it is
       ellpack_t *R = fbuf ? &b.Y : &b.X;
-      int dw = round_up(fmax > 1 ? fmax : 1, 32);
-      if (dw > w) dw = w;
-      ellpack_t out{};
-      SP2_TRY(ellpack_create(n, dw, SP2_F64, s, &out));
-      int e = convert_async(R, &out, s);
-      if (e == SP2_OK) {
-        const cudaError_t ce = cudaStreamSynchronize(s);
-        if (ce != cudaSuccess) e = cuda_fail(ce, "sp2_purify", __FILE__, __LINE__);
-      }
-      if (e != SP2_OK) {
-        ellpack_destroy(&out, s);
-        return e;
-      }
-      *D = out;
+      *D = *R;
+      memset(R, 0, sizeof(*R));
+      (void)fmax;
       st.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
       if (stats) *stats = st;
       if (status == 2) return fail(SP2E_NOTCONV, "sp2_purify: max_iter=%d reached (err %.3e)", opt.max_iter,

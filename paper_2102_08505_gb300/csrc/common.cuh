@@ -225,7 +225,8 @@ inline int cascade_start(int n, bool upper, int compact_level) {
 // (*final_buf 0 or 1).  Fills the per-iterate records of *stats up to *iterations.  *status
 // as sp2_stats.status, 3 for a non-finite trace, or 4 when an iterate grew a row too long for
 // the one-launch loop: the host-stepped loop then continues from iterate *iterations (whose
-// traces are recorded, its branch not yet taken) with the stall rule's *armed state.
+// traces are recorded, its branch not yet taken) with the stall rule's *armed state; 5 when
+// the context cannot launch the grid cooperatively (nothing ran).
 // Errors: SP2E_TIMEOUT (a grid barrier waited too long), SP2E_CUDA.
 constexpr int kSmallMaxN = 2048;
 int small_purify(ellpack_t *X0, ellpack_t *Y, double nocc, double tol, const sp2_options &opt, int *iterations,

@@ -361,7 +361,10 @@ int small_purify(ellpack_t *X0, ellpack_t *Y, double nocc, double tol, const sp2
   }));
   int occ = 0;
   SP2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sp2_small_kernel, kSmallThreads, smem));
-  if (occ < 1) return fail(SP2E_ARG, "small_purify: the kernel does not fit an SM");
+  if (occ < 1) {  // nothing ran: the caller takes the host-stepped loop
+    *status = 5;
+    return SP2_OK;
+  }
   const long long need = ((long long)n + kSmallWarps - 1) / kSmallWarps;
   const long long cap = (long long)num_sms() * occ;
   const int grid = (int)(need < cap ? need : cap);
@@ -391,12 +394,29 @@ int small_purify(ellpack_t *X0, ellpack_t *Y, double nocc, double tol, const sp2
     a.part = part;
     a.st = dst;
     void *args[] = {&a};
-    if (e == cudaSuccess)
+    bool launched = false;
+    if (e == cudaSuccess) {
       e = cudaLaunchCooperativeKernel((const void *)sp2_small_kernel, dim3(grid), dim3(kSmallThreads), args, smem, s);
-    note_launch();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h, dst, sizeof(SmallState), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
+        // a context that cannot host the whole grid at once (shared SMs, no cooperative
+        // launch): nothing ran, the caller takes the host-stepped loop
+        (void)cudaGetLastError();
+        e = cudaSuccess;
+        *status = 5;
+      } else {
+        launched = true;
+        note_launch();
+      }
+    }
+    if (launched && e == cudaSuccess) e = cudaMemcpyAsync(h, dst, sizeof(SmallState), cudaMemcpyDeviceToHost, s);
+    if (launched && e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) rc = cuda_fail(e, "sp2_small_kernel", __FILE__, __LINE__);
+    if (!launched && rc == SP2_OK) {
+      free(h);
+      dev_free(part, s);
+      dev_free(dst, s);
+      return SP2_OK;
+    }
   }
   if (rc == SP2_OK) {
     if (h->error) {

@@ -203,7 +203,12 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
     SP2_TRY(ellpack_create(n, w, SP2_F64, s, &b.Y));
     int iters = 0, status = 0, fbuf = 0, fmax = 0, arm = 0;
     const int rc = small_purify(&b.X, &b.Y, nocc, tol, opt, &iters, &status, &fbuf, &fmax, &arm, &st, s);
-    if (status == 4 && rc == SP2_OK) {  // the host-stepped loop continues from iterate iters
+    if (status == 5 && rc == SP2_OK) {  // not launched: the host-stepped loop from X0
+      SP2_TRY(ellpack_destroy(&b.X, s));
+      SP2_TRY(ellpack_destroy(&b.Y, s));
+      memset(&b.X, 0, sizeof(b.X));
+      memset(&b.Y, 0, sizeof(b.Y));
+    } else if (status == 4 && rc == SP2_OK) {  // the host-stepped loop continues from iterate iters
       if (fbuf) { ellpack_t t = b.X; b.X = b.Y; b.Y = t; }
       handed = true;
       it0 = iters;

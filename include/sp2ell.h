@@ -437,8 +437,9 @@ typedef struct sp2_options {
   int32_t n_fp64_tail;  /* MIXED: minimum FP64 iterations after the switch (default 2) */
   int32_t max_width;    /* cap on the working width (0 = n); SP2E_OVERFLOW beyond it */
   int32_t spgemm_path;  /* SpGEMM first pass: 0 automatic (symmetric products, the
-                           default: F64 path 7, F32 path 8; full rows: F64 path 4, F32
-                           path 3); 1, 2, 4 = column-block accumulator shared by that
+                           default: the cascade of route_rows, whose tight pass is the F64
+                           path 7 / F32 path 8 form; full rows: F64 path 4, F32 path 3);
+                           1, 2, 4 = column-block accumulator shared by that
                            many warps per row (7: 2 warps, compact blocks); 3 = column
                            blocks, one warp per row, two k steps per pass (8: compact);
                            9 = row tiles sharing a column index; 10..12 = per-warp hash
@@ -469,10 +470,12 @@ typedef struct sp2_options {
                            device) with the level it last needed, and later updates start it
                            there (default); 0 = every row starts at the cascade's first level */
   int32_t small_path;   /* 1 (default): FP64 runs (precision F64, spgemm_path 0, sizing 0, no
-                           width cap below n) of at most 2048 rows take the whole loop in one
+                           width cap below n) of at most 2048 rows take the loop in one
                            cooperative launch, each row built in a dense shared-memory
-                           accumulator: the same rows bit for bit, traces added in another
-                           order; 0: always the host-stepped loop */
+                           accumulator, until an iterate has a row longer than 64 entries;
+                           the host-stepped loop continues from there.  The same rows bit
+                           for bit, traces added in another order.  0: always the
+                           host-stepped loop */
   double level_up_frac; /* the cascade starts at the tight compact level (fewest blocks per
                            row, most rows per SM); once its first pass passes on more than
                            this fraction of the rows in an update, it starts one level higher

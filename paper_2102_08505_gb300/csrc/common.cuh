@@ -230,7 +230,7 @@ inline int cascade_start(int n, bool upper, int compact_level) {
 // Errors: SP2E_TIMEOUT (a grid barrier waited too long), SP2E_CUDA.
 constexpr int kSmallMaxN = 2048;
 int small_purify(ellpack_t *X0, ellpack_t *Y, double nocc, double tol, const sp2_options &opt, int *iterations,
-                 int *status, int *final_buf, int *final_maxr, int *armed, sp2_stats *stats, cudaStream_t s);
+                 int *status, int *final_buf, int *armed, sp2_stats *stats, cudaStream_t s);
 
 struct Upper {
   const int *tp = nullptr;

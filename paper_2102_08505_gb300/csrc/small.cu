@@ -44,7 +44,7 @@ struct SmallState {
   int error;            // 1: a barrier timed out
   int it, status;       // status: 0 err < tol, 1 stall rule, 2 max_iter, 3 non-finite trace,
                         // 4 handed to the host-stepped loop (a row above kSmallRowMax entries)
-  int final_buf, final_maxr, armed;
+  int final_buf, armed;
   double trX[SP2_STATS_CAP], trX2[SP2_STATS_CAP], err[SP2_STATS_CAP];
   long long nnz[SP2_STATS_CAP];
   int maxr[SP2_STATS_CAP], branch[SP2_STATS_CAP];
@@ -214,7 +214,6 @@ __global__ void __launch_bounds__(kSmallThreads) sp2_small_kernel(SmallArgs p) {
           st->it = it;
           st->status = status;
           st->final_buf = cur;
-          st->final_maxr = s_max[0];
           st->armed = armed ? 1 : 0;
         }
       }
@@ -347,7 +346,7 @@ __global__ void __launch_bounds__(kSmallThreads) sp2_small_kernel(SmallArgs p) {
 }  // namespace
 
 int small_purify(ellpack_t *X0, ellpack_t *Y, double nocc, double tol, const sp2_options &opt, int *iterations,
-                 int *status, int *final_buf, int *final_maxr, int *armed, sp2_stats *stats, cudaStream_t s) {
+                 int *status, int *final_buf, int *armed, sp2_stats *stats, cudaStream_t s) {
   const int n = X0->n;
   if (n < 1 || n > kSmallMaxN || X0->dtype != SP2_F64 || Y->dtype != SP2_F64 || Y->n != n)
     return fail(SP2E_ARG, "small_purify: bad buffers");
@@ -425,7 +424,6 @@ int small_purify(ellpack_t *X0, ellpack_t *Y, double nocc, double tol, const sp2
       *iterations = h->it;
       *status = h->status;
       *final_buf = h->final_buf;
-      *final_maxr = h->final_maxr;
       *armed = h->armed;
       const int m = h->it + 1 < SP2_STATS_CAP ? h->it + 1 : SP2_STATS_CAP;
       for (int t = 0; t < m; ++t) {

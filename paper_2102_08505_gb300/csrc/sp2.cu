@@ -201,8 +201,8 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
     SP2_TRY(ellpack_create(n, w, SP2_F64, s, &b.X));
     SP2_TRY(x0_async(H64, b.bounds, opt.tau, &b.X, s));
     SP2_TRY(ellpack_create(n, w, SP2_F64, s, &b.Y));
-    int iters = 0, status = 0, fbuf = 0, fmax = 0, arm = 0;
-    const int rc = small_purify(&b.X, &b.Y, nocc, tol, opt, &iters, &status, &fbuf, &fmax, &arm, &st, s);
+    int iters = 0, status = 0, fbuf = 0, arm = 0;
+    const int rc = small_purify(&b.X, &b.Y, nocc, tol, opt, &iters, &status, &fbuf, &arm, &st, s);
     if (status == 5 && rc == SP2_OK) {  // not launched: the host-stepped loop from X0
       SP2_TRY(ellpack_destroy(&b.X, s));
       SP2_TRY(ellpack_destroy(&b.Y, s));
@@ -233,7 +233,6 @@ extern "C" int sp2_purify(const ellpack_t *H, double nocc, double tol, const sp2
       ellpack_t *R = fbuf ? &b.Y : &b.X;
       *D = *R;
       memset(R, 0, sizeof(*R));
-      (void)fmax;
       st.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
       if (stats) *stats = st;
       if (status == 2) return fail(SP2E_NOTCONV, "sp2_purify: max_iter=%d reached (err %.3e)", opt.max_iter,

@@ -47,11 +47,13 @@ def parse():
                    help="spgemm: one SP2 iteration at N=262144 (default); sp2: whole purifications, FP64 vs "
                         "mixed at N=131072; batched: 256 clusters in one graph launch vs one by one; sizing: "
                         "heuristic vs structural vs MLP output widths for mixed SP2 at N=1048576; model: the paper's "
-                        "model Hamiltonians at N=32000; schedule: stall-rule and precision-schedule variants")
+                        "model Hamiltonians at N=32000; schedule: stall-rule and precision-schedule variants; "
+                        "rowblock: the row-block split of one SP2 run with its ranks as threads on one GPU")
     p.add_argument("--count", type=int, default=256)
     p.add_argument("--path", type=int, default=0,
-                   help="SpGEMM first pass: 0 automatic, 1/2/4 column blocks with 1/2/4 warps per row, 3 two-step, "
-                        "7/8 compact forms of 4/3, 10-12 hash, -1 tuned")
+                   help="SpGEMM first pass: 0 automatic (for symmetric products the cascade of tight, loose "
+                        "and full-row passes), 1/2/4 column blocks with 1/2/4 warps per row, 3 two-step, "
+                        "7/8 compact forms of 2/3, 9 row tiles, 10-12 hash, -1 tuned")
     p.add_argument("--full-rows", dest="symmetric", action="store_false",
                    help="SP2 steps compute full product rows instead of the upper triangle of the "
                         "symmetric product mirrored (the default)")

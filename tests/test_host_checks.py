@@ -203,3 +203,24 @@ def test_block_setup_calls_reject_bad_arguments(S):
     assert b"bounds" in err(S.lib.sp2_x0_block(ctypes.byref(X), 0, 1.0, 1.0, 1e-5, ctypes.byref(X0), None))
     assert b"tau" in err(S.lib.sp2_x0_block(ctypes.byref(X), 0, -1.0, 1.0, -1.0, ctypes.byref(X0), None))
     assert b"width" in err(S.lib.sp2_x0_block(ctypes.byref(X), 0, -1.0, 1.0, 1e-5, ctypes.byref(X), None))
+
+
+def test_stats_record_conversion(S):
+    """stats_dict turns the C record into arrays of the visited iterates (traces, errors, entries,
+    longest rows: iterations + 1) and of the updates (branches, cascade counts, levels:
+    iterations), and carries the one-launch loop's share of the updates."""
+    st = S.sp2_stats()
+    st.iterations, st.status, st.small_iterations = 3, 1, 2
+    for t in range(4):
+        st.trX[t], st.trX2[t], st.err[t] = 10.0 + t, 9.0 + t, 0.1 / (t + 1)
+        st.nnz_total[t], st.max_row_nnz[t] = 100 + t, 7 + t
+    for t in range(3):
+        st.branch[t] = 1 + t % 2
+        st.rows_level1[t], st.rows_level2[t], st.rows_deferred[t], st.rows_routed[t] = 5 + t, 2, 1, t
+        st.level[t] = -1 if t < 2 else 0
+    d = S.stats_dict(st)
+    assert d["iterations"] == 3 and d["status"] == "stalled" and d["small_iterations"] == 2
+    assert list(d["trX"]) == [10.0, 11.0, 12.0, 13.0] and list(d["max_row_nnz"]) == [7, 8, 9, 10]
+    assert d["branch"] == ["X2", "2X-X2", "X2"]
+    assert list(d["rows_level1"]) == [5, 6, 7] and list(d["rows_routed"]) == [0, 1, 2]
+    assert list(d["level"]) == [-1, -1, 0]
